@@ -1,0 +1,107 @@
+"""Planted mistakes in the oracle (on the CPU) are caught by the pins.
+
+Each test swaps one oracle step for a plausible wrong version (a transposed operand, a
+dropped term, a flipped sign, a wrong index) and checks that a pin of
+test_oracle_pins fails.  This shows the pins constrain every step they cover.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from oracle import reach_oracle as R
+from tests import test_oracle_pins as pins
+
+
+def _patch(monkeypatch, name, fn):
+    monkeypatch.setattr(R, name, fn)
+    monkeypatch.setattr(O, name, fn)
+
+
+def test_transposed_a_is_caught(monkeypatch):
+    orig = R.extract_system
+
+    def bad(*a):
+        q, A, b = orig(*a)
+        return q, A.T.tocsr(), b
+    _patch(monkeypatch, "extract_system", bad)
+    with pytest.raises(AssertionError):
+        pins.test_worked_chain_partition_and_system()
+
+
+def test_dropped_b_term_is_caught(monkeypatch):
+    orig = R.extract_system
+
+    def bad(n, rowptr, col, val, cls):
+        q, A, b = orig(n, rowptr, col, val, cls)
+        return q, A, b * (np.arange(b.size) != b.size - 1)
+    _patch(monkeypatch, "extract_system", bad)
+    with pytest.raises(AssertionError):
+        pins.test_gamblers_ruin_closed_form(20, 0.4)
+
+
+def test_jacobi_sign_is_caught(monkeypatch):
+    def bad(m, b, eps, max_iter, x0=None, history=None):
+        m = sp.csr_matrix(m)
+        d = m.diagonal()
+        off = (m - sp.diags(d)).tocsr()
+        x = np.zeros(m.shape[0])
+        for it in range(1, max_iter + 1):
+            xp = x
+            x = (b + off @ xp) / d
+            if np.max(np.abs(x - xp)) < eps:
+                return x, it, 0.0, True
+        return x, max_iter, 1.0, False
+    _patch(monkeypatch, "jacobi", bad)
+    with pytest.raises(AssertionError):
+        pins.test_worked_chain_solution("jacobi")
+
+
+def test_bicgstab_beta_is_caught(monkeypatch):
+    orig_dot = np.ndarray.__matmul__
+
+    def bad(m, b, eps, max_iter, x0=None):
+        m = sp.csr_matrix(m)
+        x = np.zeros(m.shape[0]); r = b.copy(); q = r.copy()
+        y = a = w = 1.0; v = np.zeros_like(x); p = np.zeros_like(x)
+        for it in range(1, min(max_iter, 500) + 1):
+            yp, y = y, q @ r
+            p = r + y / yp * (p - w * v)      # drops the a / w factor of beta
+            v = m @ p
+            a = y / (q @ v)
+            s = r - a * v
+            t = m @ s
+            w = (t @ s) / (t @ t)
+            x = x + a * p + w * s
+            r = s - w * t
+            if np.max(np.abs(r)) < eps:
+                return x, it, 0.0, True
+        return x, max_iter, 1.0, False
+    del orig_dot
+    _patch(monkeypatch, "bicgstab", bad)
+    with pytest.raises(AssertionError):
+        pins.test_bicgstab_finite_termination(20, 0.45)
+
+
+def test_prob1_without_goal_barrier_is_caught(monkeypatch):
+    def bad(n, rowptr, col, val, goal, s0=None):
+        p = R.canonical_csr(n, rowptr, col, val)
+        if s0 is None:
+            s0 = R.prob0(n, rowptr, col, val, goal)
+        return ~R._backward_reach(p, s0, np.ones(n, bool))
+    _patch(monkeypatch, "prob1", bad)
+    with pytest.raises(AssertionError):
+        pins.test_prob1_literal_reading_differs_from_definition()
+
+
+def test_grad_wrong_index_is_caught(monkeypatch):
+    orig = R.grad_p
+
+    def bad(n, rowptr, col, val, goal, init, mode=O.PROB01, method="dense"):
+        g, x, cls = orig(n, rowptr, col, val, goal, init, mode, method)
+        row = np.repeat(np.arange(n), np.diff(rowptr))
+        scale = np.where(x[np.asarray(col)] > 0, x[row] / np.maximum(x[np.asarray(col)], 1e-300), 0)
+        return g * scale, x, cls
+    _patch(monkeypatch, "grad_p", bad)
+    with pytest.raises(AssertionError):
+        pins.test_grad_p_matches_central_differences()

@@ -1,0 +1,294 @@
+"""The oracle against what the paper and the mathematics fix (no GPU).
+
+Pins: the worked chain of §2 (partition §2.2, A and b §2.3), the CSR example of §4,
+the gambler's-ruin closed form, path sums on tiny acyclic chains (§2 cylinder sets),
+set parity against a boolean closure, and the invariants of the method (x in [0,1],
+monotone Jacobi from 0 and from 1, agreement of Jacobi / BiCGStab / LU, PROB01 vs
+PROB0_ONLY).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from paper_1210_6412_gb300 import synth
+from tests import brute
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def load(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def chain_arrays(c):
+    return c.n, c.rowptr, c.col, c.val, c.goal
+
+
+# ------------------------------------------------------------------ §4 CSR example
+
+def test_csr_example_section4():
+    g = load("csr_example.json")
+    rstart, col, nz = O.csr_from_dense(g["matrix"])
+    assert rstart.tolist() == g["rstart"]
+    assert col.tolist() == g["col"]
+    assert nz.tolist() == g["nonzero"]
+
+
+def test_canonical_csr_sorts_and_merges():
+    # row 0 stored out of order with a duplicate and a stored zero
+    rowptr = np.array([0, 4, 5])
+    col = np.array([1, 0, 1, 0, 1])
+    val = np.array([0.25, 0.5, 0.25, 0.0, 1.0])
+    p = O.canonical_csr(2, rowptr, col, val)
+    assert p.indptr.tolist() == [0, 2, 3]
+    assert p.indices.tolist() == [0, 1, 1]
+    assert p.data.tolist() == [0.5, 0.5, 1.0]
+
+
+# ------------------------------------------------------------------ §2 worked chain
+
+def test_worked_chain_partition_and_system():
+    g = load("worked_chain.json")
+    c = synth.worked_chain()
+    assert np.array_equal(sp.csr_matrix((c.val, c.col, c.rowptr)).toarray(), np.array(g["P"]))
+    cls = O.partition(*chain_arrays(c))
+    assert np.flatnonzero(cls == O.S0).tolist() == g["S0"]
+    assert np.flatnonzero(cls == O.S1).tolist() == g["S1"]
+    assert np.flatnonzero(cls == O.SQ).tolist() == g["Sq"]
+    q, a, b = O.extract_system(c.n, c.rowptr, c.col, c.val, cls)
+    assert q.tolist() == g["Sq"]
+    assert np.array_equal(a.toarray(), np.array(g["A"]))
+    assert np.array_equal(b, np.array(g["b"], float))
+
+
+@pytest.mark.parametrize("method", ["dense", "jacobi", "bicgstab"])
+def test_worked_chain_solution(method):
+    g = load("worked_chain.json")
+    c = synth.worked_chain()
+    x, cls, _ = O.reach_probabilities(*chain_arrays(c), method=method, eps=1e-15)
+    np.testing.assert_allclose(x[g["Sq"]], g["x_Sq"], rtol=0, atol=1e-14)
+    assert x[1] == 0.0 and x[3] == 1.0
+
+
+def test_worked_chain_path_sum_and_cylinder():
+    g = load("worked_chain.json")
+    p = np.array(g["P"], float)
+    # Pr(Cyl(0 3)) = P(0,3) (§2)
+    assert p[0, 3] == g["Pr_cyl_03"]
+    # path sum over (02)^n 0 3 truncated at depth 2k+1 equals 0.5 * sum_{j<=k} 0.2^j
+    tot = sum(0.5 * 0.2 ** j for j in range(60))
+    assert abs(tot - g["x_Sq"][0]) < 1e-15
+
+
+# ------------------------------------------------------------------ closed form
+
+@pytest.mark.parametrize("N,p", [(10, 0.5), (20, 0.4), (20, 0.6), (50, 0.49), (7, 0.9)])
+def test_gamblers_ruin_closed_form(N, p):
+    c = synth.gamblers_ruin(N, p)
+    want = np.array([brute.gambler_closed_form(N, p, i) for i in range(N + 1)])
+    for method, tol in (("dense", 1e-12), ("bicgstab", 1e-9), ("jacobi", 1e-8)):
+        x, cls, info = O.reach_probabilities(*chain_arrays(c), method=method, eps=1e-13,
+                                             max_iter=2_000_000)
+        np.testing.assert_allclose(x, want, rtol=0, atol=tol, err_msg=method)
+    assert cls[0] == O.S0 and cls[N] == O.S1 and np.all(cls[1:N] == O.SQ)
+
+
+# ------------------------------------------------------------------ brute force
+
+@pytest.mark.parametrize("seed", range(12))
+def test_path_sum_on_acyclic_chains(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(3, 12))
+    p, goal = brute.random_dag_chain(rng, n)
+    rowptr, col, val = brute.dense_to_csr(p)
+    x, cls, _ = O.reach_probabilities(n, rowptr, col, val, goal, method="dense")
+    for s in range(n):
+        assert abs(x[s] - brute.path_sum(p, goal, s)) < 1e-13
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_sets_match_boolean_closure(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 60))
+    dens = rng.uniform(0.02, 0.3)
+    p = (rng.random((n, n)) < dens) * rng.random((n, n))
+    for i in range(n):
+        if p[i].sum() == 0 or rng.random() < 0.1:
+            p[i] = 0
+            p[i, i] = 1.0
+    p = p / p.sum(axis=1, keepdims=True)
+    goal = (rng.random(n) < 0.1).astype(np.uint8)
+    rowptr, col, val = brute.dense_to_csr(p)
+    s0_ref, s1_ref = brute.sets_by_closure(p, goal)
+    cls = O.partition(n, rowptr, col, val, goal)
+    assert np.array_equal(cls == O.S0, s0_ref)
+    assert np.array_equal(cls == O.S1, s1_ref & ~s0_ref)
+    # S=1 and S=0 agree with the values themselves, computed on the PROB0_ONLY system
+    x, _, _ = O.reach_probabilities(n, rowptr, col, val, goal, mode=O.PROB0_ONLY, method="dense")
+    assert np.all(np.abs(x[cls == O.S1] - 1.0) < 1e-9)
+    assert np.all(x[cls == O.S0] == 0.0)
+    sq = cls == O.SQ
+    assert np.all((x[sq] > 1e-12) & (x[sq] < 1 - 1e-9))
+
+
+def test_prob1_literal_reading_differs_from_definition():
+    """A non-goal state whose only way to S=0 runs through a goal is in S=1 (definition)."""
+    # 0 -> 1 (goal) ; goal 1 -> 2 (sink) ; so state 0 reaches S=0 only through GS.
+    p = np.array([[0, 1.0, 0], [0, 0, 1.0], [0, 0, 1.0]])
+    goal = np.array([0, 1, 0], np.uint8)
+    rowptr, col, val = brute.dense_to_csr(p)
+    cls = O.partition(3, rowptr, col, val, goal)
+    assert cls.tolist() == [O.S1, O.S1, O.S0]
+
+
+# ------------------------------------------------------------------ invariants
+
+@pytest.fixture(scope="module")
+def c1_small():
+    return synth.random_chain(n=512, deg=8, goal_frac=0.03, sink_frac=0.03, seed=7)
+
+
+def test_methods_agree_and_invariants(c1_small):
+    c = c1_small
+    xd, cls, _ = O.reach_probabilities(*chain_arrays(c), method="dense")
+    xj, _, ij = O.reach_probabilities(*chain_arrays(c), method="jacobi", eps=1e-14)
+    xb, _, ib = O.reach_probabilities(*chain_arrays(c), method="bicgstab", eps=1e-14)
+    assert ij["converged"] and ib["converged"]
+    np.testing.assert_allclose(xj, xd, atol=1e-11, rtol=0)
+    np.testing.assert_allclose(xb, xd, atol=1e-11, rtol=0)
+    assert np.all((xd >= 0) & (xd <= 1))
+    assert np.all(xd[cls == O.S1] == 1) and np.all(xd[cls == O.S0] == 0)
+    sq = cls == O.SQ
+    assert np.all((xd[sq] > 0) & (xd[sq] < 1))
+    # PROB0_ONLY gives the same probabilities
+    x0, _, _ = O.reach_probabilities(*chain_arrays(c), mode=O.PROB0_ONLY, method="dense")
+    np.testing.assert_allclose(x0, xd, atol=1e-12, rtol=0)
+
+
+def test_jacobi_monotone_sandwich(c1_small):
+    c = c1_small
+    cls = O.partition(*chain_arrays(c))
+    q, a, b = O.extract_system(c.n, c.rowptr, c.col, c.val, cls)
+    m = O.system_matrix(a)
+    xs = O.dense_solve(m, b)
+    lo, hi = [], []
+    O.jacobi(m, b, 0.0, 60, history=lo)
+    O.jacobi(m, b, 0.0, 60, x0=np.ones(q.size), history=hi)
+    prev = np.zeros(q.size)
+    for x in lo:
+        assert np.all(x >= prev - 1e-15) and np.all(x <= xs + 1e-12)
+        prev = x
+    prev = np.ones(q.size)
+    for x in hi:
+        assert np.all(x <= prev + 1e-15) and np.all(x >= xs - 1e-12)
+        prev = x
+
+
+def test_error_bound_certifies(c1_small):
+    c = c1_small
+    cls = O.partition(*chain_arrays(c))
+    q, a, b = O.extract_system(c.n, c.rowptr, c.col, c.val, cls)
+    m = O.system_matrix(a)
+    xs = O.dense_solve(m, b)
+    xj, _, _, _ = O.jacobi(m, b, 1e-6, 100000)
+    bound = O.error_bound(m, b, xj)
+    assert np.max(np.abs(xj - xs)) <= bound * (1 + 1e-9) + 1e-15
+
+
+def test_check_chain_rejects_bad_inputs():
+    c = synth.worked_chain()
+    O.check_chain(*chain_arrays(c))
+    bad = c.val.copy(); bad[0] = -0.5
+    with pytest.raises(O.OracleInputError):
+        O.check_chain(c.n, c.rowptr, c.col, bad, c.goal)
+    bad = c.val.copy(); bad[0] = 0.6
+    with pytest.raises(O.OracleInputError):
+        O.check_chain(c.n, c.rowptr, c.col, bad, c.goal)
+    badc = c.col.copy(); badc[0] = 4
+    with pytest.raises(O.OracleInputError):
+        O.check_chain(c.n, c.rowptr, badc, c.val, c.goal)
+    bad = c.val.copy(); bad[0] = np.nan
+    with pytest.raises(O.OracleInputError):
+        O.check_chain(c.n, c.rowptr, c.col, bad, c.goal)
+
+
+def test_empty_goal_set_gives_zero():
+    c = synth.random_chain(n=64, deg=4, seed=3)
+    goal = np.zeros(c.n, np.uint8)
+    x, cls, _ = O.reach_probabilities(c.n, c.rowptr, c.col, c.val, goal)
+    assert np.all(cls == O.S0) and np.all(x == 0)
+
+
+@pytest.mark.parametrize("N,p", [(3, 0.5), (12, 0.4), (20, 0.45)])
+def test_bicgstab_finite_termination(N, p):
+    """§3: in exact arithmetic BiCGStab ends within n iterations for an n x n system."""
+    c = synth.gamblers_ruin(N, p)
+    cls = O.partition(*chain_arrays(c))
+    q, a, b = O.extract_system(c.n, c.rowptr, c.col, c.val, cls)
+    x, it, res, ok = O.bicgstab(O.system_matrix(a), b, 1e-11, q.size + 2)
+    assert ok and it <= q.size + 2
+    want = np.array([brute.gambler_closed_form(N, p, i) for i in q])
+    np.testing.assert_allclose(x, want, atol=1e-9, rtol=0)
+
+
+def test_bicgstab_iteration_cap():
+    c = synth.gamblers_ruin(200, 0.5)
+    cls = O.partition(*chain_arrays(c))
+    q, a, b = O.extract_system(c.n, c.rowptr, c.col, c.val, cls)
+    x, it, res, ok = O.bicgstab(O.system_matrix(a), b, 1e-30, 3)
+    assert not ok and it == 3
+
+
+# ------------------------------------------------------------------ gradients
+
+def _fd_on_sq_rows(c, init, entries, h=1e-6):
+    """Central differences of x_init in P entries of S? rows (linear system kept fixed)."""
+    cls = O.partition(*chain_arrays(c))
+    out = []
+    for k in entries:
+        vals = []
+        for sgn in (+1, -1):
+            v = c.val.copy()
+            v[k] += sgn * h
+            q, a, b = O.extract_system(c.n, c.rowptr, c.col, v, cls)
+            xq = O.dense_solve(O.system_matrix(a), b)
+            vals.append(O.full_vector(c.n, cls, q, xq)[init])
+        out.append((vals[0] - vals[1]) / (2 * h))
+    return np.array(out)
+
+
+def test_grad_p_matches_central_differences():
+    c = synth.random_chain(n=200, deg=5, goal_frac=0.05, sink_frac=0.05, seed=11)
+    g, x, cls = O.grad_p(*chain_arrays(c), init=c.init)
+    assert cls[c.init] == O.SQ
+    row = np.repeat(np.arange(c.n), np.diff(c.rowptr))
+    rng = np.random.default_rng(0)
+    cand = np.flatnonzero(cls[row] == O.SQ)
+    ks = rng.choice(cand, size=25, replace=False)
+    fd = _fd_on_sq_rows(c, c.init, ks)
+    np.testing.assert_allclose(g[ks], fd, rtol=1e-6, atol=1e-9)
+    assert np.all(g[cls[row] != O.SQ] == 0)
+
+
+def test_grad_theta_matches_central_differences():
+    pc = synth.parametric_chain(n=300, n_classes=8, goal_frac=0.03, sink_frac=0.03, seed=5)
+
+    def x_init(theta):
+        p = O.softmax_probs(pc.rowptr, pc.cls, pc.offset, theta)
+        x, _, _ = O.reach_probabilities(pc.n, pc.rowptr, pc.col, p, pc.goal, method="dense")
+        return x[pc.init]
+
+    p = O.softmax_probs(pc.rowptr, pc.cls, pc.offset, pc.theta)
+    np.testing.assert_allclose(np.add.reduceat(p, pc.rowptr[:-1]), 1.0, atol=1e-14)
+    g_p, x, cls = O.grad_p(pc.n, pc.rowptr, pc.col, p, pc.goal, pc.init)
+    assert cls[pc.init] == O.SQ
+    g_t = O.grad_theta(pc.rowptr, p, g_p, pc.cls, 8)
+    h = 1e-6
+    fd = np.array([(x_init(pc.theta + h * np.eye(8)[j]) - x_init(pc.theta - h * np.eye(8)[j])) / (2 * h)
+                   for j in range(8)])
+    np.testing.assert_allclose(g_t, fd, rtol=1e-5, atol=1e-9)
