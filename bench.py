@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Time-to-solution and SpMV HBM bandwidth of the reachability solver on one GB300.
+
+Workload: the paper-style dense random chain -- n = 32768 states, each entry present
+with probability 10% (about 107M stored transitions), U(0,1] weights normalised per
+row, 1% goal states.  Without absorbing sinks every state reaches GS almost surely,
+so the S=0/S=1 partition leaves nothing to solve (x = 1).  The step therefore solves
+the system of §2.3 as the paper writes it, with S=1 = GS (PROB0_ONLY): 32440 unknowns,
+about 105M entries, exact solution x* = 1 (certified by the S=0/S=1 partition).
+
+One step = ingest + validate P (a copy from HBM-resident inputs), the partition and
+extraction (§2.2-2.3), then FP64 Jacobi, mixed-precision Jacobi (FP32 sweeps, FP64
+refinement every 16 sweeps) and FP64 BiCGStab, each run until its max error against
+x* is at most 1e-9.  The matrix is 1.3 GB, far larger than the 129 MB L2, so no
+flush is needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solution @1e-6/1e-9 err & SpMV HBM GB/s vs FP64 plain Jacobi"
+WORKLOAD = ("dense random chain n=32768, 10% density (~107M nnz), U(0,1] normalised, 1% goals; "
+            "system of Sec. 2.3 with S=1=GS (32440 unknowns); FP64 Jacobi + mixed Jacobi + "
+            "BiCGStab, each to max error <= 1e-9")
+TARGET_ERR = 1e-9
+# stopping thresholds that give max error <= 1e-9 on this system (contraction ~0.99)
+EPS = {"jacobi": 5e-12, "mixed": 5e-12, "bicgstab": 5e-12}
+K_REFINE = 16
+# DRAM traffic per FP64 Jacobi sweep from an ncu capture of the same kernel
+# (profiles/jacobi64_dense32768.md); None until captured for the current kernel.
+NCU_TRAFFIC_BYTES = None
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def make_chain():
+    from paper_1210_6412_gb300 import synth
+    return synth.dense_random_chain(n=32768, density=0.10, goal_frac=0.01, sink_frac=0.0)
+
+
+def dist_init():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def cpu_oracle_sample(chain, sweeps=6):
+    """The oracle as it stands on a bounded sample of the step, scaled to one full step.
+
+    Runs the oracle's partition (PROB0_ONLY) and extraction on the full matrix, BiCGStab
+    to the same stopping rule, and `sweeps` Jacobi sweeps; the Jacobi time-to-solution is
+    extrapolated from the measured per-sweep time and the contraction of max|dx|.
+    """
+    import oracle as O
+    t0 = time.perf_counter()
+    cls = O.partition(chain.n, chain.rowptr, chain.col, chain.val, chain.goal, O.PROB0_ONLY)
+    q, a, b = O.extract_system(chain.n, chain.rowptr, chain.col, chain.val, cls)
+    m = O.system_matrix(a)
+    t_pre = time.perf_counter() - t0
+    hist = []
+    t0 = time.perf_counter()
+    O.jacobi(m, b, 0.0, sweeps, history=hist)
+    t_sweep = (time.perf_counter() - t0) / sweeps
+    d = [float(np.max(np.abs(hist[i + 1] - hist[i]))) for i in range(len(hist) - 1)]
+    rho = (d[-1] / d[1]) ** (1.0 / (len(d) - 2)) if len(d) > 2 and d[1] > 0 else 0.99
+    jac_iters = int(np.ceil(1 + np.log(EPS["jacobi"] / d[0]) / np.log(rho))) if d[0] > 0 else 1
+    t0 = time.perf_counter()
+    xb, bi_iters, _, ok = O.bicgstab(m, b, EPS["bicgstab"], 200)
+    t_bicg = time.perf_counter() - t0
+    total_s = t_pre + 2 * jac_iters * t_sweep + t_bicg   # the oracle has one FP64 Jacobi; counted twice
+    return {
+        "value_ms": total_s * 1e3,
+        "sample": (f"oracle partition+extraction of the full matrix ({t_pre:.1f} s), BiCGStab to "
+                   f"eps={EPS['bicgstab']:g} ({bi_iters} iters, {t_bicg:.1f} s), {sweeps} Jacobi sweeps "
+                   f"({t_sweep:.2f} s each) extrapolated to {jac_iters} sweeps at contraction {rho:.4f}; "
+                   "the Jacobi leg is counted for both Jacobi forms"),
+        "cpu_seconds_spent": t_pre + sweeps * t_sweep + t_bicg,
+        "bicgstab_max_err": float(np.max(np.abs(xb - 1.0))) if xb.size else 0.0,
+    }
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    chain = make_chain()
+    vals = []
+    samples = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(chain, sweeps=4)
+        if i >= args.warmup:
+            vals.append(r["value_ms"])
+            samples.append(r["sample"])
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": samples[-1]},
+        "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def launches_per_step(infos, k):
+    """Kernels of this library launched in one step (counted from the loop structure)."""
+    j, mx, b = infos["jacobi"], infos["mixed"], infos["bicgstab"]
+    create = 1
+    precompute = 5 + 2 + j.get("bfs_levels", 4) + 1 + 3 + 1 + 3 + 1 + 1
+    jac = j["iters"] + 2 * (j["iters"] // k) + 3
+    mix = mx["refinements"] * (2 + (k - 1) + 2) + 3 + 1
+    bic = 1 + 5 * b["iters"] + 3
+    return create + precompute + jac + mix + bic
+
+
+def run_ours(args):
+    import torch
+    import paper_1210_6412_gb300 as R
+
+    ws, rank, local = dist_init()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    chain = make_chain()
+    n, m = chain.n, chain.m
+    d_in = [torch.from_numpy(a).to(dev) for a in (chain.rowptr, chain.col, chain.val, chain.goal)]
+    h_in = [torch.from_numpy(a).pin_memory() for a in (chain.rowptr, chain.col, chain.val, chain.goal)]
+    outs = {k: torch.empty(n, dtype=torch.float64, device=dev) for k in EPS}
+    h_outs = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in EPS}
+    stream = torch.cuda.current_stream(dev)
+
+    def step(inputs, outputs):
+        infos = {}
+        ctx = R.reach_create(n, *inputs, stream=stream.cuda_stream)
+        try:
+            R.reach_precompute(ctx, R.REACH_PROB0_ONLY)
+            for meth in ("jacobi", "mixed", "bicgstab"):
+                _, infos[meth] = R.reach_solve(ctx, n, meth, eps=EPS[meth], max_iter=200_000,
+                                               refine_k=K_REFINE, out=outputs[meth])
+        finally:
+            R.reach_destroy(ctx)
+        return infos
+
+    for _ in range(args.warmup):
+        infos = step(d_in, outs)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    all_infos = []
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            all_infos.append(step(d_in, outs))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = clk.summary()
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    infos = all_infos[-1]
+    errs = {k: float(torch.max(torch.abs(outs[k] - 1.0)).item()) for k in outs}
+
+    # end to end through the public API: host (pinned) inputs copied in, x copied out
+    e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        step(h_in, h_outs)
+        e_ms.append((time.perf_counter() - t0) * 1e3)
+    h2d = sum(int(a.numel() * a.element_size()) for a in h_in)
+    d2h = 3 * n * 8
+
+    jac = infos["jacobi"]
+    sweep_ms = jac["ms_solve"] / max(jac["iters"], 1)
+    alg_bytes = jac["m_q"] * 12 + jac["n_q"] * 40
+    achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    methods = {}
+    for k, inf in infos.items():
+        methods[k] = {"ms": inf["ms_solve"], "iters": inf["iters"], "max_err": errs[k],
+                      "resid_inf": inf["resid_inf"], "alg_GBps": inf["bytes_moved"] / (inf["ms_solve"] * 1e6),
+                      "refinements": inf["refinements"]}
+    line = {
+        "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nnz": m, "n_q": jac["n_q"], "nnz_q": jac["m_q"],
+                   "refine_k": K_REFINE, "l2": "inputs (1.3 GB) larger than L2; no flush",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "methods": methods,
+        "precompute_ms": jac["ms_precompute"],
+        "max_err_all": max(errs.values()),
+        "roofline": {"bound": "hbm", "kernel": "k_jacobi64 (FP64 Jacobi sweep)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "traffic": NCU_TRAFFIC_BYTES, "alg_bytes_per_launch": alg_bytes,
+                     "avg_launch_ms": sweep_ms},
+        "e2e": {"value": statistics.median(e_ms), "unit": "ms", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step(infos, K_REFINE) * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb = cpu_oracle_sample(chain)
+        line["cpu_baseline"] = {"value": cb["value_ms"], "unit": "ms", "cores": 1, "kind": "oracle",
+                                "sample": cb["sample"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,148 @@
+/*
+ * reach.h -- C ABI of the GB300 (sm_103a) reachability-probability solver.
+ *
+ * Problem (Cormie-Bowins, "A Comparison of Sequential and GPU Implementations of
+ * Iterative Methods to Compute Reachability Probabilities", GRAPHITE 2012):
+ * given a discrete-time Markov chain (S, P, s0) with row-stochastic P (§2) and a
+ * set of goal states GS, compute x_s = Pr(s |= <> GS) for every state (§2.1).
+ * The states are split into S=0, S=1 and S? by graph search (§2.2); on S? the
+ * values solve (I - A) x = b with A = P restricted to S? and b_s the one-step
+ * probability of entering S=1 (§2.3), by Jacobi (§3.1) or BiCGStab (§3.2).
+ *
+ * Conventions shared by every entry point:
+ *   - Status is the return value; no exception crosses the ABI.  After a failure
+ *     reach_last_error() gives a one-line reason.
+ *   - The matrix is compressed row storage (§4): rowptr int64[n+1] (rowptr[0] = 0,
+ *     rowptr[n] = m), col int32[m] in [0, n), val float64[m].  Columns need not be
+ *     sorted; duplicate (s, s') entries are summed; an entry with value 0 is no
+ *     edge.  Every row must sum to 1 within 1e-9.
+ *   - `flags` says where caller pointers live: REACH_HOST or REACH_DEVICE (memory
+ *     of the current CUDA device).  Inputs are copied, so the caller keeps
+ *     ownership and may free them when the call returns; outputs are written
+ *     into caller-allocated buffers.
+ *   - All device work of a context runs on the stream given to reach_create
+ *     (NULL = the legacy default stream).  Calls that return data to the host
+ *     synchronise that stream; calls with REACH_DEVICE outputs do not, except where
+ *     stated.  A context is not thread-safe.
+ *   - Precision: FP64 unless a method says otherwise.
+ */
+#ifndef REACH_H_
+#define REACH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct reach_ctx reach_ctx;
+typedef struct reach_batch reach_batch;
+
+typedef enum {
+  REACH_OK = 0,
+  REACH_EINVAL = 1,      /* bad argument or input that is not a Markov chain */
+  REACH_ENOMEM = 2,      /* device allocation failed */
+  REACH_ECUDA = 3,       /* a CUDA runtime call failed */
+  REACH_ESTATE = 4,      /* call out of order (e.g. solve before precompute) */
+  REACH_ENOTCONV = 5,    /* max_iter reached before the stopping rule held */
+  REACH_EBREAKDOWN = 6,  /* BiCGStab breakdown that a restart did not cure */
+  REACH_ETIMEOUT = 7     /* a bounded device-side wait gave up */
+} reach_status;
+
+enum { REACH_HOST = 0, REACH_DEVICE = 1 };
+
+/* Partition modes (§2.2).  PROB01: S=0 = states that cannot reach GS; S=1 =
+ * states that cannot reach S=0 along a path avoiding GS (GS included); S? = rest.
+ * PROB0_ONLY: S=1 = GS, so S? = S \ (S=0 u GS) and b_s = P(s, GS), the system as
+ * written in §2.3.  Both give the same x. */
+typedef enum { REACH_PROB01 = 0, REACH_PROB0_ONLY = 1 } reach_precomp_mode;
+
+/* Solvers.  JACOBI_FP64: x_i <- (b_i + sum_{j != i} A_ij x_j) / (1 - A_ii), double
+ * buffered (§3.1), stop when max|x' - x| < eps.  JACOBI_MIXED: the same iteration run
+ * as defect correction -- every refine_k sweeps an FP64 residual r = b - (I - A) x
+ * (values as FP32 hi + lo pairs), then refine_k - 1 FP32 sweeps on (I - A) d = r,
+ * then x += d in FP64; stop when max|r_i / (1 - A_ii)| < eps (the FP64 Jacobi step).
+ * BICGSTAB_FP64: unpreconditioned BiCGStab (§3.2) with x = 0 and shadow q = b;
+ * stop when max|s| < eps after the a-step (then x += a p) or max|r| < eps. */
+typedef enum {
+  REACH_JACOBI_FP64 = 0,
+  REACH_JACOBI_MIXED = 1,
+  REACH_BICGSTAB_FP64 = 2
+} reach_method;
+
+typedef struct {
+  int64_t iters;          /* Jacobi sweeps or BiCGStab iterations performed */
+  int64_t n_q;            /* |S?| */
+  int64_t m_q;            /* stored off-diagonal entries of A */
+  double last_delta;      /* stopping quantity at exit (max|dx|, max|s| or max|r|) */
+  double resid_inf;       /* FP64 max_i |b - (I - A) x|_i at exit */
+  double ms_precompute;   /* device time of the last reach_precompute */
+  double ms_solve;        /* device time of this solve (CUDA events on the stream) */
+  double bytes_moved;     /* algorithmic HBM bytes of this solve */
+  int32_t status;         /* reach_status of the solve */
+  int32_t refinements;    /* JACOBI_MIXED: FP64 residual steps taken */
+} reach_info;
+
+/* Create a context holding a copy of P and the goal mask (§2, §4).
+ * goal: uint8[n], nonzero marks GS.  Validates the chain on the device (column
+ * range, finite values in [0, 1], row sums) and returns REACH_EINVAL with a reason
+ * when it fails.  stream: a cudaStream_t, or NULL.  *out is set on success only. */
+reach_status reach_create(reach_ctx** out, int64_t n, int64_t m, const int64_t* rowptr,
+                          const int32_t* col, const double* val, const uint8_t* goal,
+                          int32_t flags, void* stream);
+
+/* Partition S into S=0 / S=1 / S? by backward breadth-first search over the
+ * reversed underlying digraph (§2.2), then build A (off-diagonal, CSR over S? in
+ * ascending state order), d = 1 - diag(A) and b (§2.3).  mode: reach_precomp_mode. */
+reach_status reach_precompute(reach_ctx* ctx, int32_t mode);
+
+/* Class of every state after reach_precompute: 0 = S=0, 1 = S=1, 2 = S?.
+ * cls: uint8[n] in host or device memory per flags. */
+reach_status reach_get_classes(reach_ctx* ctx, uint8_t* cls, int32_t flags);
+
+/* Solve (I - A) x = b on S? (§2.3) with `method` and write the full vector
+ * x_out[n] = Pr(s |= <> GS) (1 on S=1, 0 on S=0).  eps > 0; max_iter >= 1;
+ * refine_k (JACOBI_MIXED) >= 2 and even, 0 = default 16; x0: optional float64[n]
+ * starting point (its S? entries are used; NULL = 0), same memory kind as x_out.
+ * info may be NULL.  Returns REACH_ENOTCONV when max_iter ran out (x_out still
+ * holds the last iterate).  Synchronises the stream. */
+reach_status reach_solve(reach_ctx* ctx, int32_t method, double eps, int64_t max_iter,
+                         int32_t refine_k, const double* x0, double* x_out, int32_t flags,
+                         reach_info* info);
+
+/* Gradient of x_init with respect to every stored entry of P, in input order:
+ * grad[k] = y_s * x_{col[k]} for an entry of row s in S?, else 0, where
+ * (I - A)^T y = e_init is solved by Jacobi on the transposed system (FP64, stop at
+ * max|y' - y| < eps).  Uses the x of the last successful reach_solve (REACH_ESTATE
+ * without one).  init in [0, n).  grad: float64[m] per flags. */
+reach_status reach_grad(reach_ctx* ctx, int64_t init, double eps, int64_t max_iter,
+                        double* grad, int32_t flags, reach_info* info);
+
+/* Parametric chains: P_e = softmax over the out-edges of each row of
+ * theta[cls_e] + offset_e.  All pointers are device memory; rows must be non-empty;
+ * cls_e in [0, n_classes).  p_out: float64[m].  Runs on `stream`, no sync. */
+reach_status reach_param_probs(int64_t n, int64_t m, const int64_t* rowptr, const int32_t* cls,
+                               const double* offset, const double* theta, int32_t n_classes,
+                               double* p_out, void* stream);
+
+/* Chain rule through the row softmax: dl_f = P_f (g_f - sum_e P_e g_e) per row and
+ * g_theta[c] = sum of dl_f over edges of class c.  Device pointers; g_theta:
+ * float64[n_classes], overwritten.  Runs on `stream`, no sync. */
+reach_status reach_param_grad_theta(int64_t n, int64_t m, const int64_t* rowptr,
+                                    const int32_t* cls, const double* p, const double* g_p,
+                                    int32_t n_classes, double* g_theta, void* stream);
+
+/* Last error message of ctx (NULL: of the calling thread's last context-free call). */
+const char* reach_last_error(const reach_ctx* ctx);
+
+/* Release every device buffer of the context.  NULL is a no-op. */
+void reach_destroy(reach_ctx* ctx);
+
+/* Library version string. */
+const char* reach_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* REACH_H_ */

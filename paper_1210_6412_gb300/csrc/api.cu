@@ -1,0 +1,439 @@
+// The C ABI of include/reach.h: context lifetime, argument checks, and the
+// orchestration of the precompute (§2.2-§2.3) and the solvers (§3).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace reach {
+
+static thread_local std::string g_tls_err;
+
+bool set_err(reach_ctx* c, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_tls_err = msg;
+  return false;
+}
+
+int pick_group(int64_t rows, int64_t nnz) {
+  const double mean = rows > 0 ? (double)nnz / (double)rows : 0.0;
+  if (mean <= 2.5) return 2;
+  if (mean <= 5.0) return 4;
+  if (mean <= 10.0) return 8;
+  if (mean <= 20.0) return 16;
+  return 32;
+}
+
+constexpr int MAX_GRID = 4096;
+
+int grid_for(reach_ctx* c, const void* kernel, int threads, int64_t work) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> occ;
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = occ.find(kernel);
+    if (it == occ.end()) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess)
+        per_sm = 1;
+      occ[kernel] = per_sm;
+    } else {
+      per_sm = it->second;
+    }
+  }
+  per_sm = std::max(per_sm, 1);
+  int64_t full = (int64_t)c->sm_count * per_sm;
+  int64_t need = std::max<int64_t>(1, (work + threads - 1) / threads);
+  return (int)std::min<int64_t>(std::min<int64_t>(full, need), MAX_GRID);
+}
+
+}  // namespace reach
+
+using namespace reach;
+
+namespace {
+
+const char* cuda_msg(cudaError_t e) { return cudaGetErrorString(e); }
+
+reach_status fail(reach_ctx* c, reach_status s, const std::string& msg) {
+  set_err(c, msg);
+  return s;
+}
+
+reach_status cuda_fail(reach_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cuda_msg(e);
+  set_err(c, m);
+  return e == cudaErrorMemoryAllocation ? REACH_ENOMEM : REACH_ECUDA;
+}
+
+bool inject_enomem() {
+  const char* v = std::getenv("REACH_FAULT_ENOMEM");
+  return v && v[0] == '1';
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, int64_t count) {
+  *p = nullptr;
+  if (inject_enomem()) return cudaErrorMemoryAllocation;
+  if (count <= 0) count = 1;
+  return cudaMalloc((void**)p, sizeof(T) * (size_t)count);
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_system(reach_ctx* c) {
+  dfree(c->a_rowptr); dfree(c->a_col); dfree(c->a_val); dfree(c->a_hi); dfree(c->a_lo);
+  dfree(c->d); dfree(c->b); dfree(c->d32); dfree(c->qstate);
+  dfree(c->at_rowptr); dfree(c->at_col); dfree(c->at_val);
+  dfree(c->x); dfree(c->x2); dfree(c->vr); dfree(c->vq); dfree(c->vp); dfree(c->vv);
+  dfree(c->vs); dfree(c->vt); dfree(c->r32); dfree(c->dl[0]); dfree(c->dl[1]);
+}
+
+void drop_graphs(reach_ctx* c) {
+  for (int i = 0; i < 4; ++i) {
+    if (c->g_exec[i]) cudaGraphExecDestroy(c->g_exec[i]);
+    c->g_exec[i] = nullptr;
+    c->g_key[i] = -1;
+  }
+}
+
+cudaMemcpyKind kind_to_dev(int32_t flags) {
+  return flags == REACH_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+cudaMemcpyKind kind_from_dev(int32_t flags) {
+  return flags == REACH_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* reach_version(void) { return "reach-gb300 0.1 (sm_103a)"; }
+
+const char* reach_last_error(const reach_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_tls_err.c_str();
+}
+
+void reach_destroy(reach_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  drop_graphs(c);
+  free_system(c);
+  dfree(c->rowptr); dfree(c->col); dfree(c->val); dfree(c->goal);
+  dfree(c->t_rowptr); dfree(c->t_col);
+  dfree(c->cls); dfree(c->qidx); dfree(c->vis); dfree(c->queue); dfree(c->bfs);
+  dfree(c->xfull); dfree(c->st); dfree(c->bi); dfree(c->part); dfree(c->ticket);
+  dfree(c->verr); dfree(c->vrow);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+reach_status reach_create(reach_ctx** out, int64_t n, int64_t m, const int64_t* rowptr,
+                          const int32_t* col, const double* val, const uint8_t* goal, int32_t flags,
+                          void* stream) {
+  if (!out) return fail(nullptr, REACH_EINVAL, "reach_create: out is NULL");
+  if (n < 1 || n > INT32_MAX - 1) return fail(nullptr, REACH_EINVAL, "reach_create: n must be in [1, 2^31-2]");
+  if (m < 0) return fail(nullptr, REACH_EINVAL, "reach_create: m < 0");
+  if (!rowptr || !goal || (m > 0 && (!col || !val)))
+    return fail(nullptr, REACH_EINVAL, "reach_create: NULL input pointer");
+  if (flags != REACH_HOST && flags != REACH_DEVICE)
+    return fail(nullptr, REACH_EINVAL, "reach_create: flags must be REACH_HOST or REACH_DEVICE");
+
+  reach_ctx* c = new reach_ctx();
+  c->stream = (cudaStream_t)stream;
+  c->n = n;
+  c->m = m;
+  const char* hl = std::getenv("REACH_HOST_LOOPS");
+  c->device_loops = !(hl && hl[0] == '1');
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+  if (e != cudaSuccess) {
+    reach_status s = cuda_fail(nullptr, e, "reach_create: device setup");
+    reach_destroy(c);
+    return s;
+  }
+  const int64_t words = (n + 31) >> 5;
+  const int64_t part_n = std::max<int64_t>(16 * 4096, n / 8192 + 64);
+  if ((e = dalloc(&c->rowptr, n + 1)) != cudaSuccess || (e = dalloc(&c->col, m + 8)) != cudaSuccess ||
+      (e = dalloc(&c->val, m + 8)) != cudaSuccess || (e = dalloc(&c->goal, n)) != cudaSuccess ||
+      (e = dalloc(&c->t_rowptr, n + 1)) != cudaSuccess || (e = dalloc(&c->t_col, m + 8)) != cudaSuccess ||
+      (e = dalloc(&c->cls, n)) != cudaSuccess || (e = dalloc(&c->qidx, n + 1)) != cudaSuccess ||
+      (e = dalloc(&c->vis, 2 * words)) != cudaSuccess || (e = dalloc(&c->queue, 2 * n)) != cudaSuccess ||
+      (e = dalloc(&c->bfs, 1)) != cudaSuccess || (e = dalloc(&c->xfull, n)) != cudaSuccess ||
+      (e = dalloc(&c->st, 1)) != cudaSuccess || (e = dalloc(&c->bi, 1)) != cudaSuccess ||
+      (e = dalloc(&c->part, part_n)) != cudaSuccess || (e = dalloc(&c->ticket, 1)) != cudaSuccess ||
+      (e = dalloc(&c->verr, 1)) != cudaSuccess || (e = dalloc(&c->vrow, 1)) != cudaSuccess) {
+    reach_status s = cuda_fail(nullptr, e, "reach_create: allocation");
+    reach_destroy(c);
+    return s;
+  }
+  cudaStream_t s = c->stream;
+  e = cudaMemcpyAsync(c->rowptr, rowptr, sizeof(int64_t) * (n + 1), kind_to_dev(flags), s);
+  if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(c->col, col, sizeof(int32_t) * m, kind_to_dev(flags), s);
+  if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(c->val, val, sizeof(double) * m, kind_to_dev(flags), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->goal, goal, n, kind_to_dev(flags), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->col + m, 0, 8 * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->val + m, 0, 8 * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ticket, 0, sizeof(unsigned), s);
+  int64_t ends[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[0], c->rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], c->rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    reach_status st = cuda_fail(nullptr, e, "reach_create: copying inputs");
+    reach_destroy(c);
+    return st;
+  }
+  if (ends[0] != 0 || ends[1] != m) {
+    reach_destroy(c);
+    return fail(nullptr, REACH_EINVAL, "reach_create: rowptr[0] must be 0 and rowptr[n] must equal m");
+  }
+  e = launch_validate(c);
+  unsigned verr = 0;
+  int64_t vrow = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&verr, c->verr, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&vrow, c->vrow, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    reach_status st = cuda_fail(nullptr, e, "reach_create: validation");
+    reach_destroy(c);
+    return st;
+  }
+  if (verr) {
+    std::string why = "reach_create: not a Markov chain (first bad row " + std::to_string(vrow) + ":";
+    if (verr & VERR_ROWPTR) why += " rowptr not non-decreasing within [0, m];";
+    if (verr & VERR_COL) why += " column outside [0, n);";
+    if (verr & VERR_VAL) why += " value not finite in [0, 1];";
+    if (verr & VERR_ROWSUM) why += " row does not sum to 1 within 1e-9;";
+    why += ")";
+    reach_destroy(c);
+    return fail(nullptr, REACH_EINVAL, why);
+  }
+  *out = c;
+  return REACH_OK;
+}
+
+reach_status reach_precompute(reach_ctx* c, int32_t mode) {
+  if (!c) return fail(nullptr, REACH_EINVAL, "reach_precompute: NULL context");
+  if (mode != REACH_PROB01 && mode != REACH_PROB0_ONLY)
+    return fail(c, REACH_EINVAL, "reach_precompute: unknown mode");
+  cudaStream_t s = c->stream;
+  drop_graphs(c);
+  free_system(c);
+  c->have_classes = false;
+  c->have_x = false;
+  cudaError_t e = cudaEventRecord(c->ev0, s);
+  if (e == cudaSuccess) e = build_reverse_pattern(c);
+  if (e == cudaSuccess) e = bfs_backward(c, 0, false);
+  if (e == cudaSuccess && mode == REACH_PROB01) e = bfs_backward(c, 1, true);
+  if (e == cudaSuccess) e = classify_and_extract(c, mode);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reach_precompute");
+  const int64_t nq = c->n_q;
+  if ((e = dalloc(&c->x, nq)) != cudaSuccess || (e = dalloc(&c->x2, nq)) != cudaSuccess ||
+      (e = dalloc(&c->vr, nq)) != cudaSuccess || (e = dalloc(&c->vq, nq)) != cudaSuccess ||
+      (e = dalloc(&c->vp, nq)) != cudaSuccess || (e = dalloc(&c->vv, nq)) != cudaSuccess ||
+      (e = dalloc(&c->vs, nq)) != cudaSuccess || (e = dalloc(&c->vt, nq)) != cudaSuccess ||
+      (e = dalloc(&c->r32, nq)) != cudaSuccess || (e = dalloc(&c->dl[0], nq)) != cudaSuccess ||
+      (e = dalloc(&c->dl[1], nq)) != cudaSuccess) {
+    free_system(c);
+    return cuda_fail(c, e, "reach_precompute: workspace");
+  }
+  e = cudaEventRecord(c->ev1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(c->ev1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reach_precompute");
+  c->ms_precompute = ms;
+  c->mode = mode;
+  c->have_classes = true;
+  return REACH_OK;
+}
+
+reach_status reach_get_classes(reach_ctx* c, uint8_t* cls, int32_t flags) {
+  if (!c) return fail(nullptr, REACH_EINVAL, "reach_get_classes: NULL context");
+  if (!c->have_classes) return fail(c, REACH_ESTATE, "reach_get_classes: call reach_precompute first");
+  if (!cls || (flags != REACH_HOST && flags != REACH_DEVICE))
+    return fail(c, REACH_EINVAL, "reach_get_classes: bad output");
+  cudaError_t e = cudaMemcpyAsync(cls, c->cls, c->n, kind_from_dev(flags), c->stream);
+  if (e == cudaSuccess && flags == REACH_HOST) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? REACH_OK : cuda_fail(c, e, "reach_get_classes");
+}
+
+static reach_status start_state(reach_ctx* c, double eps, int64_t max_iter, int64_t max_bodies) {
+  SolveState hs;
+  std::memset(&hs, 0, sizeof(hs));
+  hs.eps = eps;
+  hs.max_iter = max_iter;
+  hs.status = REACH_ENOTCONV;
+  hs.max_bodies = max_bodies;
+  cudaError_t e = cudaMemcpyAsync(c->st, &hs, sizeof(hs), cudaMemcpyHostToDevice, c->stream);
+  // hs lives on this stack frame: wait for the copy before returning
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? REACH_OK : cuda_fail(c, e, "solve state");
+}
+
+reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_iter, int32_t refine_k,
+                         const double* x0, double* x_out, int32_t flags, reach_info* info) {
+  if (!c) return fail(nullptr, REACH_EINVAL, "reach_solve: NULL context");
+  if (!c->have_classes) return fail(c, REACH_ESTATE, "reach_solve: call reach_precompute first");
+  if (method < REACH_JACOBI_FP64 || method > REACH_BICGSTAB_FP64)
+    return fail(c, REACH_EINVAL, "reach_solve: unknown method");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(c, REACH_EINVAL, "reach_solve: eps must be > 0");
+  if (max_iter < 1) return fail(c, REACH_EINVAL, "reach_solve: max_iter must be >= 1");
+  if (refine_k == 0) refine_k = 16;
+  if (refine_k < 2 || refine_k > 62 || (refine_k & 1))
+    return fail(c, REACH_EINVAL, "reach_solve: refine_k must be even in [2, 62]");
+  if (!x_out || (flags != REACH_HOST && flags != REACH_DEVICE))
+    return fail(c, REACH_EINVAL, "reach_solve: bad output");
+  cudaStream_t s = c->stream;
+  c->tune.k = refine_k;
+  const int64_t max_bodies = method == REACH_BICGSTAB_FP64 ? max_iter + 4 : max_iter / refine_k + 4;
+  reach_status rs = start_state(c, eps, max_iter, max_bodies);
+  if (rs != REACH_OK) return rs;
+  cudaError_t e = cudaSuccess;
+  const double* x0q = nullptr;
+  if (x0 && c->n_q > 0) {
+    e = cudaMemcpyAsync(c->xfull, x0, sizeof(double) * c->n, kind_to_dev(flags), s);
+    if (e == cudaSuccess) e = gather_q(c, c->xfull, c->vt);
+    x0q = c->vt;
+    if (e == cudaSuccess && method == REACH_BICGSTAB_FP64) {
+      // the BiCGStab workspace reuses vt: move the start vector out of it first
+      e = cudaMemcpyAsync(c->x2, c->vt, sizeof(double) * c->n_q, cudaMemcpyDeviceToDevice, s);
+      x0q = c->x2;
+    }
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev0, s);
+  if (e == cudaSuccess && c->n_q > 0) {
+    if (method == REACH_JACOBI_FP64) e = solve_jacobi64(c, x0q, false);
+    else if (method == REACH_JACOBI_MIXED) e = solve_mixed(c, x0q);
+    else e = solve_bicgstab(c, x0q);
+  }
+  if (e == cudaSuccess) e = scatter_full(c, c->x, c->xfull);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev1, s);
+  SolveState hs;
+  std::memset(&hs, 0, sizeof(hs));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, c->st, sizeof(hs), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(x_out, c->xfull, sizeof(double) * c->n, kind_from_dev(flags), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reach_solve");
+  if (c->n_q == 0) {
+    hs.status = REACH_OK;
+    hs.done = 1;
+  }
+  const double mq = (double)c->m_q, nq = (double)c->n_q;
+  double bytes = 0.0;
+  if (method == REACH_JACOBI_FP64) bytes = (double)hs.iter * (mq * 12.0 + nq * 40.0);
+  else if (method == REACH_JACOBI_MIXED)
+    bytes = (double)hs.refinements * (mq * 12.0 + nq * 40.0) +
+            (double)(hs.iter - hs.refinements) * (mq * 8.0 + nq * 24.0);
+  else bytes = (double)hs.iter * (2.0 * (mq * 12.0 + nq * 40.0) + nq * 8.0 * 10.0);
+  if (info) {
+    info->iters = hs.iter;
+    info->n_q = c->n_q;
+    info->m_q = c->m_q;
+    info->last_delta = hs.last;
+    info->resid_inf = hs.resid;
+    info->ms_precompute = c->ms_precompute;
+    info->ms_solve = ms;
+    info->bytes_moved = bytes;
+    info->status = hs.status;
+    info->refinements = hs.refinements;
+  }
+  c->have_x = hs.status == REACH_OK;
+  if (hs.status != REACH_OK) {
+    const char* why = hs.status == REACH_ENOTCONV ? "reach_solve: max_iter reached before the stopping rule held"
+                      : hs.status == REACH_EBREAKDOWN ? "reach_solve: BiCGStab breakdown"
+                      : hs.status == REACH_ETIMEOUT ? "reach_solve: loop bound reached"
+                                                    : "reach_solve: failed";
+    set_err(c, why);
+  }
+  return (reach_status)hs.status;
+}
+
+reach_status reach_grad(reach_ctx* c, int64_t init, double eps, int64_t max_iter, double* grad,
+                        int32_t flags, reach_info* info) {
+  if (!c) return fail(nullptr, REACH_EINVAL, "reach_grad: NULL context");
+  if (!c->have_x) return fail(c, REACH_ESTATE, "reach_grad: needs a successful reach_solve first");
+  if (init < 0 || init >= c->n) return fail(c, REACH_EINVAL, "reach_grad: init outside [0, n)");
+  if (!(eps > 0.0) || max_iter < 1) return fail(c, REACH_EINVAL, "reach_grad: bad eps or max_iter");
+  if (!grad || (flags != REACH_HOST && flags != REACH_DEVICE))
+    return fail(c, REACH_EINVAL, "reach_grad: bad output");
+  cudaStream_t s = c->stream;
+  double* gdev = grad;
+  cudaError_t e = cudaSuccess;
+  if (flags == REACH_HOST) {
+    if ((e = dalloc(&gdev, c->m + 1)) != cudaSuccess) return cuda_fail(c, e, "reach_grad: allocation");
+  }
+  uint8_t kind = 0;
+  int64_t row = -1;
+  e = cudaMemcpyAsync(&kind, c->cls + init, 1, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&row, c->qidx + init, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  reach_status status = REACH_OK;
+  SolveState hs;
+  std::memset(&hs, 0, sizeof(hs));
+  float ms = 0.f;
+  if (e == cudaSuccess && kind != CLS_SQ) {
+    e = cudaMemsetAsync(gdev, 0, sizeof(double) * c->m, s);
+    hs.status = REACH_OK;
+  } else if (e == cudaSuccess) {
+    e = build_transposed_system(c);
+    const int k = c->tune.k;
+    if (e == cudaSuccess) {
+      reach_status rs = start_state(c, eps, max_iter, max_iter / k + 4);
+      if (rs != REACH_OK) {
+        if (flags == REACH_HOST) cudaFree(gdev);
+        return rs;
+      }
+    }
+    const double one = 1.0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->vp, 0, sizeof(double) * c->n_q, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->vp + row, &one, sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev0, s);
+    if (e == cudaSuccess) e = solve_jacobi64(c, nullptr, true);
+    if (e == cudaSuccess) e = grad_entries(c, c->vr, gdev);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev1, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, c->st, sizeof(hs), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  }
+  if (e == cudaSuccess && flags == REACH_HOST)
+    e = cudaMemcpyAsync(grad, gdev, sizeof(double) * c->m, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (flags == REACH_HOST) cudaFree(gdev);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reach_grad");
+  status = (reach_status)hs.status;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = hs.iter;
+    info->n_q = c->n_q;
+    info->m_q = c->m_q;
+    info->last_delta = hs.last;
+    info->resid_inf = hs.resid;
+    info->ms_precompute = c->ms_precompute;
+    info->ms_solve = ms;
+    info->status = status;
+  }
+  if (status != REACH_OK) set_err(c, "reach_grad: adjoint solve did not converge");
+  return status;
+}
+
+}  // extern "C"

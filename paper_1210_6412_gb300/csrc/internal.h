@@ -1,0 +1,161 @@
+// Host-side declarations shared by the library's translation units: the
+// context layout, the device-state blocks read by the solver graphs, and the
+// kernel launchers.  Not part of the public ABI (include/reach.h is).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/reach.h"
+
+namespace reach {
+
+enum : uint8_t { CLS_S0 = 0, CLS_S1 = 1, CLS_SQ = 2 };
+
+// Validation error bits written by k_validate.
+enum : unsigned { VERR_ROWPTR = 1u, VERR_COL = 2u, VERR_VAL = 4u, VERR_ROWSUM = 8u };
+
+// Per-solve state in device memory.  Kernels of a captured solve graph read the
+// stopping parameters from here and write the outcome, so one instantiated graph
+// serves every later solve of the same shape.
+struct SolveState {
+  double eps;
+  int64_t max_iter;
+  int64_t iter;
+  double last;          // stopping quantity of the last check
+  double resid;         // FP64 max|b - (I - A) x| after the loop
+  int32_t status;       // reach_status
+  int32_t done;         // set once the stopping rule held or max_iter ran out
+  int32_t refinements;
+  int32_t pad;
+  int64_t bodies;       // loop bodies run (hard stop at max_bodies)
+  int64_t max_bodies;
+  unsigned long long slot[64];  // per-sweep max|dx| bit patterns (non-negative doubles)
+};
+
+// BiCGStab scalars (§3.2 names: y = rho, a = alpha, w = omega) in device memory.
+struct BiState {
+  double y, yprev, a, w, beta, qv, ts, tt, snorm, rnorm;
+  int32_t s_done;       // max|s| < eps after the a-step: finish with x += a p
+  int32_t restarted;
+};
+
+struct BfsState {
+  int32_t level;
+  uint32_t count[2];
+  uint32_t pad;
+};
+
+struct Tuning {
+  int g = 0;            // lanes per row for CSR kernels (0 = pick from mean degree)
+  int k = 16;           // sweeps between convergence checks / refinement period
+  int cta = 256;        // threads per CTA
+};
+
+struct DeviceBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace reach
+
+struct reach_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;       // user stream (may be the legacy default)
+  cudaStream_t cap = nullptr;          // private stream used for graph capture
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::string err;
+
+  int64_t n = 0, m = 0;
+  int64_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  uint8_t* goal = nullptr;
+
+  // reversed underlying digraph (pattern of P^T, entries with P > 0)
+  int64_t* t_rowptr = nullptr;
+  int32_t* t_col = nullptr;
+
+  // partition
+  bool have_classes = false;
+  int mode = 0;
+  uint8_t* cls = nullptr;
+  int64_t* qidx = nullptr;     // state -> S? row (valid on S?)
+  int64_t* qstate = nullptr;   // S? row -> state
+  uint32_t* vis = nullptr;     // BFS visited bitmask
+  int32_t* queue = nullptr;    // two BFS queues of n entries
+  reach::BfsState* bfs = nullptr;
+
+  // system over S? (§2.3): A off-diagonal CSR, d = 1 - A_ii, b
+  int64_t n_q = 0, m_q = 0;
+  int64_t* a_rowptr = nullptr;
+  int32_t* a_col = nullptr;
+  double* a_val = nullptr;
+  float* a_hi = nullptr;
+  float* a_lo = nullptr;
+  double* d = nullptr;
+  double* b = nullptr;
+  float* d32 = nullptr;
+
+  // transposed system for the adjoint
+  int64_t* at_rowptr = nullptr;
+  int32_t* at_col = nullptr;
+  double* at_val = nullptr;
+
+  // solve workspace (n_q each)
+  double* x = nullptr;
+  double* x2 = nullptr;
+  double* vr = nullptr;     // BiCGStab r
+  double* vq = nullptr;     // BiCGStab q
+  double* vp = nullptr;     // BiCGStab p
+  double* vv = nullptr;     // BiCGStab v
+  double* vs = nullptr;     // BiCGStab s
+  double* vt = nullptr;     // BiCGStab t
+  float* r32 = nullptr;     // mixed: residual
+  float* dl[2] = {nullptr, nullptr};  // mixed: correction ping-pong
+  double* xfull = nullptr;  // full-state x of the last successful solve
+  bool have_x = false;
+
+  reach::SolveState* st = nullptr;
+  reach::BiState* bi = nullptr;
+  double* part = nullptr;   // per-CTA partials (8 * max grid)
+  unsigned* ticket = nullptr;
+  unsigned* verr = nullptr;
+  int64_t* vrow = nullptr;
+
+  reach::Tuning tune;
+  bool device_loops = true;   // conditional-while graphs (false: host-driven loops)
+  double ms_precompute = 0.0;
+
+  // cached solve graphs, keyed by method and shape
+  cudaGraphExec_t g_exec[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t g_key[4] = {-1, -1, -1, -1};
+};
+
+namespace reach {
+
+// ---- graph.cu
+cudaError_t launch_validate(reach_ctx* c);
+cudaError_t build_reverse_pattern(reach_ctx* c);
+cudaError_t bfs_backward(reach_ctx* c, int source_kind, bool avoid_goal);
+cudaError_t classify_and_extract(reach_ctx* c, int mode);
+cudaError_t split_hilo(reach_ctx* c);
+cudaError_t build_transposed_system(reach_ctx* c);
+
+// ---- solve.cu
+cudaError_t solve_jacobi64(reach_ctx* c, const double* x0q, bool transposed);
+cudaError_t solve_mixed(reach_ctx* c, const double* x0q);
+cudaError_t solve_bicgstab(reach_ctx* c, const double* x0q);
+cudaError_t residual_inf(reach_ctx* c, const double* xq, double* out_host);
+cudaError_t scatter_full(reach_ctx* c, const double* xq, double* full);
+cudaError_t gather_q(reach_ctx* c, const double* full, double* xq);
+cudaError_t grad_entries(reach_ctx* c, const double* yq, double* grad);
+
+// ---- shared host helpers (api.cu)
+int pick_group(int64_t rows, int64_t nnz);
+int grid_for(reach_ctx* c, const void* kernel, int threads, int64_t work_items);
+bool set_err(reach_ctx* c, const std::string& msg);
+
+}  // namespace reach

@@ -1,0 +1,791 @@
+// Iterative solvers for (I - A) x = b on S? (§2.3): Jacobi (§3.1) in FP64 and as
+// FP32 sweeps with FP64 defect correction, and unpreconditioned BiCGStab (§3.2)
+// with FP64 scalars kept on the device.  Every loop runs inside one CUDA graph
+// with a conditional while node; the stopping rule is evaluated on the device.
+#include <cfloat>
+#include <functional>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace reach {
+
+constexpr int NT = 256;
+
+// ------------------------------------------------------------------ row dot products
+// G lanes per row, lane-strided over the row.  V (G == 32 only): 16-byte loads of
+// four column indices and the matching values, after a scalar head that aligns the
+// start to four entries; the tail is scalar again.  Matrix data is streamed with
+// evict-first loads; the gathered vector goes through the read-only cache.
+
+template <int G, bool V, typename XF>
+RDEV double dot64(int64_t lo, int64_t hi, int lane, const int32_t* __restrict__ ci,
+                  const double* __restrict__ av, XF xf) {
+  double s = 0.0;
+  if constexpr (V) {
+    int64_t a = (lo + 3) & ~int64_t(3);
+    if (a > hi) a = hi;
+    const int64_t e = a + ((hi - a) & ~int64_t(3));
+    if (lo + lane < a) s = fma(__ldcs(av + lo + lane), xf(__ldcs(ci + lo + lane)), s);
+    for (int64_t k = a + 4 * lane; k < e; k += 128) {
+      const int4 c4 = __ldcs(reinterpret_cast<const int4*>(ci + k));
+      const double2 v0 = __ldcs(reinterpret_cast<const double2*>(av + k));
+      const double2 v1 = __ldcs(reinterpret_cast<const double2*>(av + k + 2));
+      s = fma(v0.x, xf(c4.x), s);
+      s = fma(v0.y, xf(c4.y), s);
+      s = fma(v1.x, xf(c4.z), s);
+      s = fma(v1.y, xf(c4.w), s);
+    }
+    if (e + lane < hi) s = fma(__ldcs(av + e + lane), xf(__ldcs(ci + e + lane)), s);
+  } else {
+    for (int64_t k = lo + lane; k < hi; k += G) s = fma(__ldcs(av + k), xf(__ldcs(ci + k)), s);
+  }
+  return s;
+}
+
+// FP32 values, FP32 accumulation (inner sweeps of the mixed method).
+template <int G, bool V>
+RDEV float dot32(int64_t lo, int64_t hi, int lane, const int32_t* __restrict__ ci,
+                 const float* __restrict__ av, const float* __restrict__ x) {
+  float s = 0.0f;
+  if constexpr (V) {
+    int64_t a = (lo + 3) & ~int64_t(3);
+    if (a > hi) a = hi;
+    const int64_t e = a + ((hi - a) & ~int64_t(3));
+    if (lo + lane < a) s = fmaf(__ldcs(av + lo + lane), __ldg(x + __ldcs(ci + lo + lane)), s);
+    for (int64_t k = a + 4 * lane; k < e; k += 128) {
+      const int4 c4 = __ldcs(reinterpret_cast<const int4*>(ci + k));
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(av + k));
+      s = fmaf(v.x, __ldg(x + c4.x), s);
+      s = fmaf(v.y, __ldg(x + c4.y), s);
+      s = fmaf(v.z, __ldg(x + c4.z), s);
+      s = fmaf(v.w, __ldg(x + c4.w), s);
+    }
+    if (e + lane < hi) s = fmaf(__ldcs(av + e + lane), __ldg(x + __ldcs(ci + e + lane)), s);
+  } else {
+    for (int64_t k = lo + lane; k < hi; k += G) s = fmaf(__ldcs(av + k), __ldg(x + __ldcs(ci + k)), s);
+  }
+  return s;
+}
+
+// Values as FP32 hi + lo pairs widened to FP64, FP64 accumulation (residual step).
+template <int G, bool V>
+RDEV double dot_hilo(int64_t lo, int64_t hi, int lane, const int32_t* __restrict__ ci,
+                     const float* __restrict__ ah, const float* __restrict__ al,
+                     const double* __restrict__ x) {
+  double s = 0.0;
+  if constexpr (V) {
+    int64_t a = (lo + 3) & ~int64_t(3);
+    if (a > hi) a = hi;
+    const int64_t e = a + ((hi - a) & ~int64_t(3));
+    if (lo + lane < a) {
+      const int64_t k = lo + lane;
+      s = fma((double)__ldcs(ah + k) + (double)__ldcs(al + k), __ldg(x + __ldcs(ci + k)), s);
+    }
+    for (int64_t k = a + 4 * lane; k < e; k += 128) {
+      const int4 c4 = __ldcs(reinterpret_cast<const int4*>(ci + k));
+      const float4 h = __ldcs(reinterpret_cast<const float4*>(ah + k));
+      const float4 l = __ldcs(reinterpret_cast<const float4*>(al + k));
+      s = fma((double)h.x + (double)l.x, __ldg(x + c4.x), s);
+      s = fma((double)h.y + (double)l.y, __ldg(x + c4.y), s);
+      s = fma((double)h.z + (double)l.z, __ldg(x + c4.z), s);
+      s = fma((double)h.w + (double)l.w, __ldg(x + c4.w), s);
+    }
+    if (e + lane < hi) {
+      const int64_t k = e + lane;
+      s = fma((double)__ldcs(ah + k) + (double)__ldcs(al + k), __ldg(x + __ldcs(ci + k)), s);
+    }
+  } else {
+    for (int64_t k = lo + lane; k < hi; k += G)
+      s = fma((double)__ldcs(ah + k) + (double)__ldcs(al + k), __ldg(x + __ldcs(ci + k)), s);
+  }
+  return s;
+}
+
+RDEV double nan_to_inf(double v) { return v != v ? __longlong_as_double(0x7ff0000000000000LL) : v; }
+
+template <int NV, bool MAX>
+RDEV void cta_to_slot(double v, unsigned long long* slot) {
+  __shared__ double sh[32];
+  double a[1] = {v};
+  block_reduce<1, true>(a, sh);
+  if (threadIdx.x == 0) atomic_max_nonneg(slot, nan_to_inf(a[0]));
+}
+
+// Last CTA of the grid reduces NS sums followed by NM maxima.
+template <int NS, int NM>
+RDEV bool last_cta_reduce(double (&mine)[NS + NM], double* part, unsigned* ticket,
+                          double (&tot)[NS + NM]) {
+  constexpr int NV = NS + NM;
+  __shared__ double sh[NV * 32];
+  __shared__ bool is_last;
+  double bl[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) bl[j] = mine[j];
+  {
+    double s[NS > 0 ? NS : 1];
+    double mx[NM > 0 ? NM : 1];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) s[j] = bl[j];
+#pragma unroll
+    for (int j = 0; j < NM; ++j) mx[j] = bl[NS + j];
+    if constexpr (NS > 0) block_reduce<NS, false>(reinterpret_cast<double(&)[NS]>(s), sh);
+    if constexpr (NM > 0) block_reduce<NM, true>(reinterpret_cast<double(&)[NM]>(mx), sh);
+#pragma unroll
+    for (int j = 0; j < NS; ++j) bl[j] = s[j];
+#pragma unroll
+    for (int j = 0; j < NM; ++j) bl[NS + j] = mx[j];
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) part[j * gridDim.x + blockIdx.x] = bl[j];
+    __threadfence();
+    is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double s[NS > 0 ? NS : 1];
+  double mx[NM > 0 ? NM : 1];
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    s[j] = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s[j] += __ldcg(part + j * gridDim.x + b);
+  }
+#pragma unroll
+  for (int j = 0; j < NM; ++j) {
+    mx[j] = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+      mx[j] = fmax(mx[j], nan_to_inf(__ldcg(part + (NS + j) * gridDim.x + b)));
+  }
+  if constexpr (NS > 0) block_reduce<NS, false>(reinterpret_cast<double(&)[NS]>(s), sh);
+  if constexpr (NM > 0) block_reduce<NM, true>(reinterpret_cast<double(&)[NM]>(mx), sh);
+#pragma unroll
+  for (int j = 0; j < NS; ++j) tot[j] = s[j];
+#pragma unroll
+  for (int j = 0; j < NM; ++j) tot[NS + j] = mx[j];
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+// ------------------------------------------------------------------ Jacobi FP64 (§3.1)
+// x'_i = (b_i + sum_{j != i} A_ij x_j) / d_i with d_i = 1 - A_ii: the paper's row
+// update for M = I - A, double buffered; max|x' - x| is reduced into slot.
+
+template <int G, bool V>
+__global__ void __launch_bounds__(NT) k_jacobi64(int64_t nq, const int64_t* __restrict__ rp,
+                                                 const int32_t* __restrict__ ci,
+                                                 const double* __restrict__ av,
+                                                 const double* __restrict__ b,
+                                                 const double* __restrict__ d,
+                                                 const double* __restrict__ x,
+                                                 double* __restrict__ xn, unsigned long long* slot) {
+  RowGroups rg = RowGroups::make<G>();
+  double mx = 0.0;
+  auto xf = [x](int32_t j) { return __ldg(x + j); };
+  for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
+    double s = 0.0;
+    if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, av, xf);
+    s = group_sum<G>(s);
+    if (i < nq && rg.lane == 0) {
+      const double xv = (b[i] + s) / d[i];
+      mx = fmax(mx, nan_to_inf(fabs(xv - x[i])));
+      xn[i] = xv;
+    }
+  }
+  cta_to_slot<1, true>(mx, slot);
+}
+
+// FP64 residual r = b - (I - A) x, max|r| into slot (reported as resid_inf).
+template <int G, bool V>
+__global__ void __launch_bounds__(NT) k_resid64(int64_t nq, const int64_t* __restrict__ rp,
+                                                const int32_t* __restrict__ ci,
+                                                const double* __restrict__ av,
+                                                const double* __restrict__ b,
+                                                const double* __restrict__ d,
+                                                const double* __restrict__ x,
+                                                unsigned long long* slot) {
+  RowGroups rg = RowGroups::make<G>();
+  double mx = 0.0;
+  auto xf = [x](int32_t j) { return __ldg(x + j); };
+  for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
+    double s = 0.0;
+    if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, av, xf);
+    s = group_sum<G>(s);
+    if (i < nq && rg.lane == 0) mx = fmax(mx, nan_to_inf(fabs(b[i] + s - d[i] * x[i])));
+  }
+  cta_to_slot<1, true>(mx, slot);
+}
+
+__global__ void k_check(SolveState* st, int slot_idx, int sweeps, int reset_n) {
+  if (st->done) return;
+  const double dl = slot_value(&st->slot[slot_idx]);
+  st->iter += sweeps;
+  st->last = dl;
+  if (dl < st->eps) {
+    st->done = 1;
+    st->status = REACH_OK;
+  } else if (st->iter >= st->max_iter) {
+    st->done = 1;
+    st->status = REACH_ENOTCONV;
+  }
+  for (int j = 0; j < reset_n; ++j) st->slot[j] = 0ull;
+}
+
+__global__ void k_loop_ctl(SolveState* st, cudaGraphConditionalHandle h, int use_cond) {
+  st->bodies += 1;
+  if (!st->done && st->bodies >= st->max_bodies) {
+    st->done = 1;
+    st->status = REACH_ETIMEOUT;
+  }
+  if (use_cond) cudaGraphSetConditional(h, st->done ? 0u : 1u);
+}
+
+__global__ void k_finalize_resid(SolveState* st) {
+  st->resid = slot_value(&st->slot[63]);
+  st->slot[63] = 0ull;
+}
+
+// ------------------------------------------------------------------ mixed precision
+// Defect correction around the same Jacobi iteration: the FP64 residual step
+// writes r (FP32) and the first correction sweep d_0 = r / d; FP32 sweeps follow on
+// (I - A) delta = r; then x += delta in FP64.  max|r_i / d_i| is exactly the
+// max|x' - x| of an FP64 Jacobi sweep from x, so the stopping rule matches.
+
+template <int G, bool V>
+__global__ void __launch_bounds__(NT) k_resid_hilo(int64_t nq, const int64_t* __restrict__ rp,
+                                                   const int32_t* __restrict__ ci,
+                                                   const float* __restrict__ ah,
+                                                   const float* __restrict__ al,
+                                                   const double* __restrict__ b,
+                                                   const double* __restrict__ d,
+                                                   const double* __restrict__ x,
+                                                   float* __restrict__ r32, float* __restrict__ dl0,
+                                                   SolveState* st, int slot_idx) {
+  if (st->done) return;
+  RowGroups rg = RowGroups::make<G>();
+  double mx = 0.0;
+  for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
+    double s = 0.0;
+    if (i < nq) s = dot_hilo<G, V>(rp[i], rp[i + 1], rg.lane, ci, ah, al, x);
+    s = group_sum<G>(s);
+    if (i < nq && rg.lane == 0) {
+      const double di = d[i];
+      const double r = b[i] + s - di * x[i];
+      const double q = r / di;
+      r32[i] = __double2float_rn(r);
+      dl0[i] = __double2float_rn(q);
+      mx = fmax(mx, nan_to_inf(fabs(q)));
+    }
+  }
+  cta_to_slot<1, true>(mx, &st->slot[slot_idx]);
+}
+
+__global__ void k_check_mixed(SolveState* st, int slot_idx, int k) {
+  if (st->done) return;
+  const double dl = slot_value(&st->slot[slot_idx]);
+  st->slot[slot_idx] = 0ull;
+  st->refinements += 1;
+  st->iter += 1;
+  st->last = dl;
+  if (dl < st->eps) {
+    st->done = 1;
+    st->status = REACH_OK;
+  } else if (st->iter + (k - 1) > st->max_iter) {
+    st->done = 1;
+    st->status = REACH_ENOTCONV;
+  } else {
+    st->iter += k - 1;
+  }
+}
+
+template <int G, bool V>
+__global__ void __launch_bounds__(NT) k_sweep32(int64_t nq, const int64_t* __restrict__ rp,
+                                                const int32_t* __restrict__ ci,
+                                                const float* __restrict__ ah,
+                                                const float* __restrict__ r32,
+                                                const float* __restrict__ d32,
+                                                const float* __restrict__ din,
+                                                float* __restrict__ dout, const SolveState* st) {
+  if (st->done) return;
+  RowGroups rg = RowGroups::make<G>();
+  for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
+    float s = 0.0f;
+    if (i < nq) s = dot32<G, V>(rp[i], rp[i + 1], rg.lane, ci, ah, din);
+    s = group_sum<G>(s);
+    if (i < nq && rg.lane == 0) dout[i] = (r32[i] + s) / d32[i];
+  }
+}
+
+__global__ void k_apply(int64_t nq, double* __restrict__ x, const float* __restrict__ dl,
+                        const SolveState* st) {
+  if (st->done) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)dl[i];
+}
+
+// ------------------------------------------------------------------ BiCGStab (§3.2)
+// M = I - A, (M u)_i = d_i u_i - sum_{j != i} A_ij u_j.  Per iteration: p update;
+// v = M p with q.v fused (a = y / q.v in the last CTA); t = M s with s = r - a v
+// formed on the fly, t.s, t.t and max|s| fused (w = t.s / t.t); then x and r with
+// q.r and max|r| fused (next y and beta).  All sums are fixed-order two-stage.
+
+template <int G, bool V>
+__global__ void __launch_bounds__(NT) k_bi_init(int64_t nq, const int64_t* __restrict__ rp,
+                                                const int32_t* __restrict__ ci,
+                                                const double* __restrict__ av,
+                                                const double* __restrict__ b,
+                                                const double* __restrict__ d,
+                                                const double* __restrict__ x,
+                                                double* __restrict__ r, double* __restrict__ q,
+                                                double* __restrict__ p, double* __restrict__ v,
+                                                double* part, unsigned* ticket, BiState* bi,
+                                                SolveState* st) {
+  RowGroups rg = RowGroups::make<G>();
+  double acc[2] = {0.0, 0.0};
+  auto xf = [x](int32_t j) { return __ldg(x + j); };
+  for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
+    double s = 0.0;
+    if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, av, xf);
+    s = group_sum<G>(s);
+    if (i < nq && rg.lane == 0) {
+      const double ri = b[i] - (d[i] * x[i] - s);
+      r[i] = ri;
+      q[i] = ri;
+      p[i] = 0.0;
+      v[i] = 0.0;
+      acc[0] = fma(ri, ri, acc[0]);
+      acc[1] = fmax(acc[1], nan_to_inf(fabs(ri)));
+    }
+  }
+  double tot[2];
+  if (last_cta_reduce<1, 1>(acc, part, ticket, tot) && threadIdx.x == 0) {
+    bi->y = tot[0];
+    bi->yprev = 1.0;
+    bi->a = 1.0;
+    bi->w = 1.0;
+    bi->beta = 0.0;
+    bi->s_done = 0;
+    bi->restarted = 0;
+    bi->rnorm = tot[1];
+    st->last = tot[1];
+    if (tot[1] < st->eps) {
+      st->done = 1;
+      st->status = REACH_OK;
+    }
+  }
+}
+
+__global__ void k_bi_p(int64_t nq, const double* __restrict__ r, double* __restrict__ p,
+                       const double* __restrict__ v, const BiState* bi, const SolveState* st) {
+  if (st->done) return;
+  const double beta = bi->beta, w = bi->w;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = r[i] + beta * (p[i] - w * v[i]);
+}
+
+template <int G, bool V>
+__global__ void __launch_bounds__(NT) k_bi_v(int64_t nq, const int64_t* __restrict__ rp,
+                                             const int32_t* __restrict__ ci,
+                                             const double* __restrict__ av,
+                                             const double* __restrict__ d,
+                                             const double* __restrict__ p,
+                                             const double* __restrict__ q, double* __restrict__ v,
+                                             double* part, unsigned* ticket, BiState* bi,
+                                             SolveState* st) {
+  if (st->done) return;
+  RowGroups rg = RowGroups::make<G>();
+  double acc[1] = {0.0};
+  auto pf = [p](int32_t j) { return __ldg(p + j); };
+  for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
+    double s = 0.0;
+    if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, av, pf);
+    s = group_sum<G>(s);
+    if (i < nq && rg.lane == 0) {
+      const double vi = d[i] * p[i] - s;
+      v[i] = vi;
+      acc[0] = fma(q[i], vi, acc[0]);
+    }
+  }
+  double tot[1];
+  if (last_cta_reduce<1, 0>(acc, part, ticket, tot) && threadIdx.x == 0) {
+    bi->qv = tot[0];
+    if (tot[0] == 0.0 || !(fabs(tot[0]) <= DBL_MAX)) {
+      st->done = 1;
+      st->status = REACH_EBREAKDOWN;
+    } else {
+      bi->a = bi->y / tot[0];
+    }
+  }
+}
+
+template <int G, bool V>
+__global__ void __launch_bounds__(NT) k_bi_t(int64_t nq, const int64_t* __restrict__ rp,
+                                             const int32_t* __restrict__ ci,
+                                             const double* __restrict__ av,
+                                             const double* __restrict__ d,
+                                             const double* __restrict__ r,
+                                             const double* __restrict__ v,
+                                             double* __restrict__ s_out, double* __restrict__ t,
+                                             double* part, unsigned* ticket, BiState* bi,
+                                             SolveState* st) {
+  if (st->done) return;
+  const double a = bi->a;
+  RowGroups rg = RowGroups::make<G>();
+  double acc[3] = {0.0, 0.0, 0.0};
+  auto sf = [r, v, a](int32_t j) { return __ldg(r + j) - a * __ldg(v + j); };
+  for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
+    double s = 0.0;
+    if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, av, sf);
+    s = group_sum<G>(s);
+    if (i < nq && rg.lane == 0) {
+      const double si = r[i] - a * v[i];
+      const double ti = d[i] * si - s;
+      s_out[i] = si;
+      t[i] = ti;
+      acc[0] = fma(ti, si, acc[0]);
+      acc[1] = fma(ti, ti, acc[1]);
+      acc[2] = fmax(acc[2], nan_to_inf(fabs(si)));
+    }
+  }
+  double tot[3];
+  if (last_cta_reduce<2, 1>(acc, part, ticket, tot) && threadIdx.x == 0) {
+    bi->ts = tot[0];
+    bi->tt = tot[1];
+    bi->snorm = tot[2];
+    if (tot[2] < st->eps) {
+      bi->s_done = 1;
+    } else if (tot[1] == 0.0) {
+      st->done = 1;
+      st->status = REACH_EBREAKDOWN;
+    } else {
+      bi->w = tot[0] / tot[1];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_bi_x(int64_t nq, double* __restrict__ x,
+                                             const double* __restrict__ p,
+                                             const double* __restrict__ s,
+                                             const double* __restrict__ t, double* __restrict__ r,
+                                             const double* __restrict__ q, double* part,
+                                             unsigned* ticket, BiState* bi, SolveState* st) {
+  if (st->done) return;
+  const double a = bi->a, w = bi->w;
+  const int s_done = bi->s_done;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (s_done) {
+      x[i] += a * p[i];
+    } else {
+      x[i] += a * p[i] + w * s[i];
+      const double ri = s[i] - w * t[i];
+      r[i] = ri;
+      acc[0] = fma(q[i], ri, acc[0]);
+      acc[1] = fmax(acc[1], nan_to_inf(fabs(ri)));
+    }
+  }
+  double tot[2];
+  if (last_cta_reduce<1, 1>(acc, part, ticket, tot) && threadIdx.x == 0) {
+    st->iter += 1;
+    if (s_done) {
+      st->last = bi->snorm;
+      st->done = 1;
+      st->status = REACH_OK;
+      return;
+    }
+    bi->rnorm = tot[1];
+    st->last = tot[1];
+    bi->yprev = bi->y;
+    bi->y = tot[0];
+    if (tot[1] < st->eps) {
+      st->done = 1;
+      st->status = REACH_OK;
+    } else if (st->iter >= st->max_iter) {
+      st->done = 1;
+      st->status = REACH_ENOTCONV;
+    } else if (bi->y == 0.0 || w == 0.0) {
+      st->done = 1;
+      st->status = REACH_EBREAKDOWN;
+    } else {
+      bi->beta = (bi->y / bi->yprev) * (a / w);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+struct Lay {
+  int g;
+  bool vec;
+};
+
+static Lay layout(reach_ctx* c, int64_t rows, int64_t nnz) {
+  if (c->tune.g == 64) return {32, true};
+  if (c->tune.g > 0) return {c->tune.g, false};
+  const int g = pick_group(rows, nnz);
+  const bool vec = g == 32 && rows > 0 && nnz / rows >= 96;
+  return {g, vec};
+}
+
+#define LAY_DISPATCH(L, FN, ...)                          \
+  do {                                                    \
+    if ((L).vec) FN<32, true>(__VA_ARGS__);               \
+    else switch ((L).g) {                                 \
+        case 2: FN<2, false>(__VA_ARGS__); break;         \
+        case 4: FN<4, false>(__VA_ARGS__); break;         \
+        case 8: FN<8, false>(__VA_ARGS__); break;         \
+        case 16: FN<16, false>(__VA_ARGS__); break;       \
+        default: FN<32, false>(__VA_ARGS__); break;       \
+      }                                                   \
+  } while (0)
+
+struct Sys {
+  int64_t nq;
+  const int64_t* rp;
+  const int32_t* ci;
+  const double* av;
+  const double* b;
+};
+
+template <int G, bool V>
+static void l_jacobi(reach_ctx* c, const Sys& y, const double* x, double* xn, unsigned long long* slot,
+                     cudaStream_t s) {
+  const int grid = grid_for(c, (const void*)k_jacobi64<G, V>, NT, y.nq * G);
+  k_jacobi64<G, V><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, c->d, x, xn, slot);
+}
+
+template <int G, bool V>
+static void l_resid(reach_ctx* c, const Sys& y, const double* x, cudaStream_t s) {
+  const int grid = grid_for(c, (const void*)k_resid64<G, V>, NT, y.nq * G);
+  k_resid64<G, V><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, c->d, x, &c->st->slot[63]);
+}
+
+template <int G, bool V>
+static void l_resid_hilo(reach_ctx* c, int slot, cudaStream_t s) {
+  const int grid = grid_for(c, (const void*)k_resid_hilo<G, V>, NT, c->n_q * G);
+  k_resid_hilo<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->a_lo, c->b, c->d,
+                                         c->x, c->r32, c->dl[1], c->st, slot);
+}
+
+template <int G, bool V>
+static void l_sweep32(reach_ctx* c, const float* din, float* dout, cudaStream_t s) {
+  const int grid = grid_for(c, (const void*)k_sweep32<G, V>, NT, c->n_q * G);
+  k_sweep32<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->r32, c->d32, din, dout,
+                                      c->st);
+}
+
+template <int G, bool V>
+static void l_bi_init(reach_ctx* c, cudaStream_t s) {
+  const int grid = grid_for(c, (const void*)k_bi_init<G, V>, NT, c->n_q * G);
+  k_bi_init<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_val, c->b, c->d, c->x, c->vr,
+                                      c->vq, c->vp, c->vv, c->part, c->ticket, c->bi, c->st);
+}
+
+template <int G, bool V>
+static void l_bi_v(reach_ctx* c, cudaStream_t s) {
+  const int grid = grid_for(c, (const void*)k_bi_v<G, V>, NT, c->n_q * G);
+  k_bi_v<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_val, c->d, c->vp, c->vq, c->vv,
+                                   c->part, c->ticket, c->bi, c->st);
+}
+
+template <int G, bool V>
+static void l_bi_t(reach_ctx* c, cudaStream_t s) {
+  const int grid = grid_for(c, (const void*)k_bi_t<G, V>, NT, c->n_q * G);
+  k_bi_t<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_val, c->d, c->vr, c->vv, c->vs,
+                                   c->vt, c->part, c->ticket, c->bi, c->st);
+}
+
+static int ew_grid(reach_ctx* c, const void* k, int64_t n) { return grid_for(c, k, NT, n); }
+
+// Runs `body` inside a conditional while node until SolveState::done (device
+// loops), or relaunches it from the host and polls `done` (host loops).  Graphs
+// are cached in slot `gs` under `key`; the stopping parameters live in SolveState.
+static cudaError_t run_loop(reach_ctx* c, int gs, int64_t key,
+                            const std::function<void(cudaStream_t, cudaGraphConditionalHandle, int)>& body) {
+  cudaError_t e = cudaSuccess;
+  if (!c->device_loops) {
+    int32_t done = 0;
+    while (!done) {
+      body(c->stream, cudaGraphConditionalHandle(), 0);
+      k_loop_ctl<<<1, 1, 0, c->stream>>>(c->st, cudaGraphConditionalHandle(), 0);
+      e = cudaMemcpyAsync(&done, &c->st->done, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+  }
+  if (c->g_exec[gs] == nullptr || c->g_key[gs] != key) {
+    if (c->g_exec[gs]) cudaGraphExecDestroy(c->g_exec[gs]);
+    c->g_exec[gs] = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphConditionalHandle h;
+    e = cudaGraphCreate(&graph, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    if (e == cudaSuccess) {
+      cudaGraph_t bg = np.conditional.phGraph_out[0];
+      e = cudaStreamBeginCaptureToGraph(c->cap, bg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        body(c->cap, h, 1);
+        k_loop_ctl<<<1, 1, 0, c->cap>>>(c->st, h, 1);
+        e = cudaStreamEndCapture(c->cap, &bg);
+      }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->g_exec[gs], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c->g_exec[gs] = nullptr;
+      return e;
+    }
+    c->g_key[gs] = key;
+  }
+  return cudaGraphLaunch(c->g_exec[gs], c->stream);
+}
+
+static int64_t shape_key(reach_ctx* c, const Lay& L, int k) {
+  return (c->n_q * 1000003LL + c->m_q) * 131 + L.g * 7 + (L.vec ? 1 : 0) + 1000LL * k;
+}
+
+cudaError_t solve_jacobi64(reach_ctx* c, const double* x0q, bool transposed) {
+  cudaStream_t s = c->stream;
+  const int64_t nq = c->n_q;
+  double* xa = transposed ? c->vr : c->x;
+  double* xb = transposed ? c->vq : c->x2;
+  if (x0q) cudaMemcpyAsync(xa, x0q, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
+  else cudaMemsetAsync(xa, 0, sizeof(double) * nq, s);
+  Sys y = transposed ? Sys{nq, c->at_rowptr, c->at_col, c->at_val, c->vp}
+                     : Sys{nq, c->a_rowptr, c->a_col, c->a_val, c->b};
+  const Lay L = layout(c, nq, c->m_q);
+  const int k = c->tune.k;
+  cudaError_t e = run_loop(c, transposed ? 3 : 0, shape_key(c, L, k),
+                           [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
+                             for (int j = 0; j < k; ++j) {
+                               const double* xi = (j & 1) ? xb : xa;
+                               double* xo = (j & 1) ? xa : xb;
+                               LAY_DISPATCH(L, l_jacobi, c, y, xi, xo, &c->st->slot[j], cs);
+                             }
+                             k_check<<<1, 1, 0, cs>>>(c->st, k - 1, k, k);
+                           });
+  if (e != cudaSuccess) return e;
+  LAY_DISPATCH(L, l_resid, c, y, xa, s);
+  k_finalize_resid<<<1, 1, 0, s>>>(c->st);
+  return cudaGetLastError();
+}
+
+cudaError_t solve_mixed(reach_ctx* c, const double* x0q) {
+  cudaStream_t s = c->stream;
+  const int64_t nq = c->n_q;
+  cudaError_t e = split_hilo(c);
+  if (e != cudaSuccess) return e;
+  if (x0q) cudaMemcpyAsync(c->x, x0q, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
+  else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
+  const Lay L = layout(c, nq, c->m_q);
+  const int k = c->tune.k;
+  e = run_loop(c, 1, shape_key(c, L, k), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
+    LAY_DISPATCH(L, l_resid_hilo, c, 0, cs);
+    k_check_mixed<<<1, 1, 0, cs>>>(c->st, 0, k);
+    // k - 1 FP32 sweeps: dl[1] -> dl[0] -> dl[1] ... ; k even, so the last lands in dl[0]
+    for (int j = 1; j < k; ++j) {
+      const float* din = (j & 1) ? c->dl[1] : c->dl[0];
+      float* dout = (j & 1) ? c->dl[0] : c->dl[1];
+      LAY_DISPATCH(L, l_sweep32, c, din, dout, cs);
+    }
+    k_apply<<<ew_grid(c, (const void*)k_apply, nq), NT, 0, cs>>>(nq, c->x, c->dl[0], c->st);
+  });
+  if (e != cudaSuccess) return e;
+  Sys y{nq, c->a_rowptr, c->a_col, c->a_val, c->b};
+  LAY_DISPATCH(L, l_resid, c, y, c->x, s);
+  k_finalize_resid<<<1, 1, 0, s>>>(c->st);
+  return cudaGetLastError();
+}
+
+cudaError_t solve_bicgstab(reach_ctx* c, const double* x0q) {
+  cudaStream_t s = c->stream;
+  const int64_t nq = c->n_q;
+  if (x0q) cudaMemcpyAsync(c->x, x0q, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
+  else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
+  const Lay L = layout(c, nq, c->m_q);
+  LAY_DISPATCH(L, l_bi_init, c, s);
+  cudaError_t e = run_loop(c, 2, shape_key(c, L, 1), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
+    k_bi_p<<<ew_grid(c, (const void*)k_bi_p, nq), NT, 0, cs>>>(nq, c->vr, c->vp, c->vv, c->bi, c->st);
+    LAY_DISPATCH(L, l_bi_v, c, cs);
+    LAY_DISPATCH(L, l_bi_t, c, cs);
+    k_bi_x<<<ew_grid(c, (const void*)k_bi_x, nq), NT, 0, cs>>>(nq, c->x, c->vp, c->vs, c->vt, c->vr, c->vq,
+                                                               c->part, c->ticket, c->bi, c->st);
+  });
+  if (e != cudaSuccess) return e;
+  Sys y{nq, c->a_rowptr, c->a_col, c->a_val, c->b};
+  LAY_DISPATCH(L, l_resid, c, y, c->x, s);
+  k_finalize_resid<<<1, 1, 0, s>>>(c->st);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ full-state vectors
+
+__global__ void k_scatter(int64_t n, const uint8_t* __restrict__ cls, const int64_t* __restrict__ qidx,
+                          const double* __restrict__ xq, double* __restrict__ full) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t k = cls[s];
+    full[s] = k == CLS_S1 ? 1.0 : (k == CLS_S0 ? 0.0 : xq[qidx[s]]);
+  }
+}
+
+__global__ void k_gather(int64_t nq, const int64_t* __restrict__ qstate, const double* __restrict__ full,
+                         double* __restrict__ xq) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+       i += (int64_t)gridDim.x * blockDim.x)
+    xq[i] = full[qstate[i]];
+}
+
+cudaError_t scatter_full(reach_ctx* c, const double* xq, double* full) {
+  k_scatter<<<ew_grid(c, (const void*)k_scatter, c->n), NT, 0, c->stream>>>(c->n, c->cls, c->qidx, xq, full);
+  return cudaGetLastError();
+}
+
+cudaError_t gather_q(reach_ctx* c, const double* full, double* xq) {
+  if (c->n_q == 0) return cudaSuccess;
+  k_gather<<<ew_grid(c, (const void*)k_gather, c->n_q), NT, 0, c->stream>>>(c->n_q, c->qstate, full, xq);
+  return cudaGetLastError();
+}
+
+// d x_init / d P(s, s') = y_s * x_s' for rows s in S?, 0 elsewhere (input order).
+template <int G>
+__global__ void k_grad(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                       const uint8_t* __restrict__ cls, const int64_t* __restrict__ qidx,
+                       const double* __restrict__ y, const double* __restrict__ xfull,
+                       double* __restrict__ g) {
+  RowGroups rg = RowGroups::make<G>();
+  for (int64_t s = rg.first; s < n; s += rg.stride) {
+    const bool q = cls[s] == CLS_SQ;
+    const double ys = q ? y[qidx[s]] : 0.0;
+    for (int64_t k = rp[s] + rg.lane; k < rp[s + 1]; k += G) g[k] = q ? ys * xfull[col[k]] : 0.0;
+  }
+}
+
+cudaError_t grad_entries(reach_ctx* c, const double* yq, double* grad) {
+  const int g = pick_group(c->n, c->m);
+#define KG(G) k_grad<G><<<grid_for(c, (const void*)k_grad<G>, NT, c->n * G), NT, 0, c->stream>>>( \
+      c->n, c->rowptr, c->col, c->cls, c->qidx, yq, c->xfull, grad)
+  switch (g) {
+    case 2: KG(2); break;
+    case 4: KG(4); break;
+    case 8: KG(8); break;
+    case 16: KG(16); break;
+    default: KG(32); break;
+  }
+#undef KG
+  return cudaGetLastError();
+}
+
+}  // namespace reach

@@ -1,0 +1,244 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Classes (S=0 / S=1 / S?) must match bit for bit; x within 1e-9 absolute for the FP64
+methods and 1e-6 for the mixed-precision form.  Sizes span several CTAs and leave
+ragged tails; the edge cases of the method (empty S?, empty goal set, single state,
+duplicate / unsorted / zero entries, invalid chains) are covered too.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1210_6412_gb300 as R
+from paper_1210_6412_gb300 import synth
+from tests import brute
+from tests.gpu_util import TOL_FP64, TOL_MIXED, gpu_solve, need_gpu, oracle_solution
+
+pytestmark = pytest.mark.gpu
+
+METHODS = [("jacobi", TOL_FP64), ("mixed", TOL_MIXED), ("bicgstab", TOL_FP64)]
+MODES = [O.PROB01, O.PROB0_ONLY]
+
+
+def _eps(method):
+    return 1e-13 if method != "mixed" else 1e-10
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return synth.random_chain(n=4096, deg=16, goal_frac=0.02, sink_frac=0.02)
+
+
+@pytest.mark.parametrize("method,tol", METHODS)
+def test_worked_chain(method, tol):
+    with open(os.path.join(os.path.dirname(__file__), "golden", "worked_chain.json")) as f:
+        g = json.load(f)
+    c = synth.worked_chain()
+    cls, x, info = gpu_solve(c, O.PROB01, method, _eps(method))
+    assert np.flatnonzero(cls == 0).tolist() == g["S0"]
+    assert np.flatnonzero(cls == 1).tolist() == g["S1"]
+    assert np.flatnonzero(cls == 2).tolist() == g["Sq"]
+    np.testing.assert_allclose(x[g["Sq"]], g["x_Sq"], atol=tol, rtol=0)
+    assert x[1] == 0.0 and x[3] == 1.0
+    assert info["n_q"] == 2 and info["m_q"] == 2
+
+
+@pytest.mark.parametrize("method,tol", METHODS)
+@pytest.mark.parametrize("mode", MODES)
+def test_config_small_random_chain(c1, method, tol, mode):
+    """4096 states, 16 successors, 2% goals, 2% sinks (the small random-chain workload)."""
+    cls_o, x_o = oracle_solution(c1, mode)
+    cls, x, info = gpu_solve(c1, mode, method, _eps(method))
+    assert np.array_equal(cls, cls_o)
+    assert np.max(np.abs(x - x_o)) <= tol
+    assert info["status"] == R.REACH_OK and info["iters"] > 0
+    assert info["resid_inf"] < 1e-9
+
+
+@pytest.mark.parametrize("N,p", [(20, 0.4), (60, 0.5), (33, 0.55)])
+@pytest.mark.parametrize("method,tol", METHODS)
+def test_gamblers_ruin(N, p, method, tol):
+    c = synth.gamblers_ruin(N, p)
+    want = np.array([brute.gambler_closed_form(N, p, i) for i in range(N + 1)])
+    cls, x, info = gpu_solve(c, O.PROB01, method, 1e-14 if method != "mixed" else 1e-12)
+    assert cls[0] == 0 and cls[N] == 1 and np.all(cls[1:N] == 2)
+    assert np.max(np.abs(x - want)) <= tol
+
+
+@pytest.mark.parametrize("n,m", synth.TABLE1_QUICKSORT[::4] + synth.TABLE1_BIASED_DIE[::4])
+@pytest.mark.parametrize("method,tol", METHODS)
+def test_table1_shapes(n, m, method, tol):
+    c = synth.table1_chain(n, m)
+    cls_o, x_o = oracle_solution(c)
+    cls, x, _ = gpu_solve(c, O.PROB01, method, _eps(method))
+    assert np.array_equal(cls, cls_o)
+    assert np.max(np.abs(x - x_o)) <= tol
+
+
+@pytest.mark.parametrize("method,tol", METHODS)
+def test_layered_chain(method, tol):
+    c = synth.layered_chain(layers=60, width=300, seed=11)
+    cls_o, x_o = oracle_solution(c)
+    cls, x, _ = gpu_solve(c, O.PROB01, method, _eps(method))
+    assert np.array_equal(cls, cls_o)
+    assert np.max(np.abs(x - x_o)) <= tol
+
+
+@pytest.mark.parametrize("method,tol", METHODS)
+def test_dense_chain_with_sinks(method, tol):
+    """Long rows (about 200 entries): the vector-load row kernels."""
+    c = synth.dense_random_chain(n=2000, density=0.1, goal_frac=0.01, sink_frac=0.02, seed=5)
+    cls_o, x_o = oracle_solution(c)
+    cls, x, _ = gpu_solve(c, O.PROB01, method, _eps(method))
+    assert np.array_equal(cls, cls_o)
+    assert np.max(np.abs(x - x_o)) <= tol
+
+
+def test_dense_chain_without_sinks_is_degenerate():
+    """No sinks: every state reaches GS almost surely, so S=1 = S and x = 1."""
+    c = synth.dense_random_chain(n=3000, density=0.1, goal_frac=0.01, seed=6)
+    cls, x, info = gpu_solve(c, O.PROB01, "jacobi", 1e-12)
+    assert np.all(cls == 1) and np.all(x == 1.0) and info["n_q"] == 0
+    cls_o = O.partition(c.n, c.rowptr, c.col, c.val, c.goal)
+    assert np.array_equal(cls, cls_o)
+    # the same matrix in PROB0_ONLY mode iterates to x -> 1
+    for method, tol in METHODS:
+        cls0, x0, info0 = gpu_solve(c, O.PROB0_ONLY, method, 1e-13 if method != "mixed" else 1e-11)
+        assert info0["n_q"] == c.n - int(c.goal.sum())
+        assert np.max(np.abs(x0 - 1.0)) <= tol, method
+
+
+@pytest.mark.parametrize("method,tol", METHODS)
+def test_device_pointers_match_host_pointers(c1, method, tol):
+    _, xh, ih = gpu_solve(c1, O.PROB01, method, _eps(method))
+    _, xd, idd = gpu_solve(c1, O.PROB01, method, _eps(method), device=True)
+    assert np.array_equal(xh, xd) and ih["iters"] == idd["iters"]
+
+
+def test_host_loops_match_device_loops(c1, monkeypatch):
+    _, xa, ia = gpu_solve(c1, O.PROB01, "jacobi", 1e-12)
+    monkeypatch.setenv("REACH_HOST_LOOPS", "1")
+    for method, tol in METHODS:
+        cls_o, x_o = oracle_solution(c1)
+        cls, x, info = gpu_solve(c1, O.PROB01, method, _eps(method))
+        assert np.array_equal(cls, cls_o) and np.max(np.abs(x - x_o)) <= tol
+    _, xb, ib = gpu_solve(c1, O.PROB01, "jacobi", 1e-12)
+    assert np.array_equal(xa, xb) and ia["iters"] == ib["iters"]
+
+
+def test_warm_start_and_iteration_cap(c1):
+    cls_o, x_o = oracle_solution(c1)
+    torch = need_gpu()
+    with R.Solver(c1.n, c1.rowptr, c1.col, c1.val, c1.goal) as s:
+        x, info = s.solve("jacobi", eps=1e-12, max_iter=4, refine_k=2, check=False)
+        assert info["status"] == R.REACH_ENOTCONV and info["iters"] == 4
+        # resuming from the last iterate (the checkpoint) converges to the same answer
+        x2, info2 = s.solve("jacobi", eps=1e-13, x0=x)
+        assert np.max(np.abs(x2 - x_o)) <= TOL_FP64
+        # starting at the solution stops at the first check
+        x3, info3 = s.solve("jacobi", eps=1e-10, x0=x_o, refine_k=2)
+        assert info3["iters"] == 2 and np.max(np.abs(x3 - x_o)) <= 1e-10
+        x4, info4 = s.solve("bicgstab", eps=1e-12, max_iter=1, check=False)
+        assert info4["status"] in (R.REACH_ENOTCONV, R.REACH_OK)
+    del torch
+
+
+def test_jacobi_monotone_from_below(c1):
+    """Iterates from x = 0 never decrease and never pass x* (A >= 0, b >= 0)."""
+    cls_o, x_o = oracle_solution(c1)
+    prev = np.zeros(c1.n)
+    with R.Solver(c1.n, c1.rowptr, c1.col, c1.val, c1.goal) as s:
+        for it in (2, 4, 8, 16, 32):
+            x, _ = s.solve("jacobi", eps=1e-300, max_iter=it, refine_k=2, check=False)
+            assert np.all(x >= prev - 1e-15) and np.all(x <= x_o + 1e-12)
+            prev = x
+
+
+# ------------------------------------------------------------------ edge cases
+
+def _chain(rows, goal):
+    """Chain from a list of {col: prob} rows (input order kept)."""
+    rowptr = [0]
+    col, val = [], []
+    for r in rows:
+        for k, v in r:
+            col.append(k)
+            val.append(v)
+        rowptr.append(len(col))
+    return synth.Chain(n=len(rows), rowptr=np.array(rowptr, np.int64), col=np.array(col, np.int32),
+                       val=np.array(val, np.float64), goal=np.array(goal, np.uint8))
+
+
+@pytest.mark.parametrize("method", ["jacobi", "mixed", "bicgstab"])
+def test_single_state(method):
+    for goal, want in ((1, 1.0), (0, 0.0)):
+        c = _chain([[(0, 1.0)]], [goal])
+        cls, x, info = gpu_solve(c, O.PROB01, method, 1e-12)
+        assert x.tolist() == [want] and info["n_q"] == 0
+
+
+def test_empty_goal_set(c1):
+    c = synth.Chain(c1.n, c1.rowptr, c1.col, c1.val, np.zeros(c1.n, np.uint8))
+    cls, x, info = gpu_solve(c, O.PROB01, "bicgstab", 1e-12)
+    assert np.all(cls == 0) and np.all(x == 0.0)
+
+
+def test_all_goal_states(c1):
+    c = synth.Chain(c1.n, c1.rowptr, c1.col, c1.val, np.ones(c1.n, np.uint8))
+    cls, x, _ = gpu_solve(c, O.PROB0_ONLY, "jacobi", 1e-12)
+    assert np.all(cls == 1) and np.all(x == 1.0)
+
+
+def test_unsorted_duplicate_and_zero_entries():
+    # state 0: successors stored out of order, 2 split into two entries, an explicit zero to 1
+    c = _chain([[(3, 0.25), (2, 0.125), (1, 0.0), (0, 0.25), (2, 0.375)],
+                [(1, 1.0)], [(0, 0.4), (1, 0.6)], [(3, 1.0)]], [0, 0, 0, 1])
+    cls_o, x_o = oracle_solution(c)
+    for method, tol in METHODS:
+        cls, x, _ = gpu_solve(c, O.PROB01, method, 1e-14)
+        assert np.array_equal(cls, cls_o) and np.max(np.abs(x - x_o)) <= tol
+
+
+@pytest.mark.parametrize("bad", ["negative", "nan", "col", "rowsum", "rowptr"])
+def test_invalid_chains_are_rejected(bad):
+    need_gpu()
+    c = synth.worked_chain()
+    rowptr, col, val = c.rowptr.copy(), c.col.copy(), c.val.copy()
+    if bad == "negative":
+        val[0], val[1] = -0.5, 1.5
+    elif bad == "nan":
+        val[0] = np.nan
+    elif bad == "col":
+        col[0] = 4
+    elif bad == "rowsum":
+        val[0] = 0.6
+    elif bad == "rowptr":
+        rowptr[1], rowptr[2] = 3, 2
+    with pytest.raises(R.ReachError) as ei:
+        R.reach_create(c.n, rowptr, col, val, c.goal)
+    assert ei.value.status == R.REACH_EINVAL
+
+
+def test_solve_before_precompute_is_a_state_error():
+    need_gpu()
+    c = synth.worked_chain()
+    s = R.Solver(c.n, c.rowptr, c.col, c.val, c.goal, precompute=False)
+    with pytest.raises(R.ReachError) as ei:
+        s.solve()
+    assert ei.value.status == R.REACH_ESTATE
+    with pytest.raises(R.ReachError) as ei:
+        s.grad(0)
+    assert ei.value.status == R.REACH_ESTATE
+    s.close()
+
+
+def test_injected_allocation_failure(monkeypatch):
+    need_gpu()
+    monkeypatch.setenv("REACH_FAULT_ENOMEM", "1")
+    c = synth.worked_chain()
+    with pytest.raises(R.ReachError) as ei:
+        R.reach_create(c.n, c.rowptr, c.col, c.val, c.goal)
+    assert ei.value.status == R.REACH_ENOMEM
