@@ -306,6 +306,25 @@ def run_ours(args):
     return 0
 
 
+def run_profile(args):
+    """Small fixed run for ncu: the bench workload, one context, `--profile-iters`
+    iterations of one method (no stopping test can end it early)."""
+    import torch
+    import paper_1210_6412_gb300 as R
+    chain = make_chain()
+    dev = torch.device("cuda", 0)
+    d_in = [torch.from_numpy(a).to(dev) for a in (chain.rowptr, chain.col, chain.val, chain.goal)]
+    out = torch.empty(chain.n, dtype=torch.float64, device=dev)
+    with R.Solver(chain.n, *d_in, mode=R.REACH_PROB0_ONLY) as s:
+        del d_in                    # the context holds its own copy; keep the footprint small
+        torch.cuda.empty_cache()
+        _, info = s.solve(args.profile, eps=1e-300, max_iter=args.profile_iters, refine_k=K_REFINE,
+                          out=out, check=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "iters": info["iters"], "ms": info["ms_solve"]}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -313,7 +332,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["jacobi", "mixed", "bicgstab"], default=None,
+                    help="run a short fixed-length solve for ncu and exit")
+    ap.add_argument("--profile-iters", type=int, default=32)
     args = ap.parse_args()
+    if args.profile:
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

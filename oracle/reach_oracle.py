@@ -258,7 +258,14 @@ def bicgstab(m, b, eps, max_iter, x0=None):
         v = m @ p
         qv = float(q @ v)
         if qv == 0.0:
-            raise BreakdownError("q . v = 0")
+            if restarted:
+                raise BreakdownError("q . v = 0 after restart")
+            restarted = True
+            q, p, v = r.copy(), r.copy(), m @ r
+            y = float(q @ r)
+            qv = float(q @ v)
+            if qv == 0.0:
+                raise BreakdownError("q . v = 0")
         a = y / qv
         s = r - a * v
         s_norm = float(np.max(np.abs(s)))

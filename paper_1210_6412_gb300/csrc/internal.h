@@ -36,9 +36,11 @@ struct SolveState {
 
 // BiCGStab scalars (§3.2 names: y = rho, a = alpha, w = omega) in device memory.
 struct BiState {
-  double y, yprev, a, w, beta, qv, ts, tt, snorm, rnorm;
+  double y, yprev, a, w, beta, qv, ts, tt, snorm, rnorm, rr;
   int32_t s_done;       // max|s| < eps after the a-step: finish with x += a p
-  int32_t restarted;
+  int32_t restarted;    // a breakdown restart has happened (only one is allowed)
+  int32_t restart;      // next p-update restarts: q = r, p = r, v = 0
+  int32_t skip;         // rest of this iteration is skipped (breakdown at q.v)
 };
 
 struct BfsState {

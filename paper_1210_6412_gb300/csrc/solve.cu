@@ -368,6 +368,9 @@ __global__ void __launch_bounds__(NT) k_bi_init(int64_t nq, const int64_t* __res
     bi->beta = 0.0;
     bi->s_done = 0;
     bi->restarted = 0;
+    bi->restart = 0;
+    bi->skip = 0;
+    bi->rr = tot[0];
     bi->rnorm = tot[1];
     st->last = tot[1];
     if (tot[1] < st->eps) {
@@ -377,13 +380,39 @@ __global__ void __launch_bounds__(NT) k_bi_init(int64_t nq, const int64_t* __res
   }
 }
 
+// p = r + beta (p - w v).  After a breakdown the iteration restarts from the current
+// residual: q = r, p = r, v = 0 (y = r.r was set by the CTA that detected it).
 __global__ void k_bi_p(int64_t nq, const double* __restrict__ r, double* __restrict__ p,
-                       const double* __restrict__ v, const BiState* bi, const SolveState* st) {
+                       double* __restrict__ v, double* __restrict__ q, BiState* bi,
+                       const SolveState* st) {
   if (st->done) return;
   const double beta = bi->beta, w = bi->w;
+  const int rs = bi->restart;
+  if (blockIdx.x == 0 && threadIdx.x == 0) bi->skip = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = r[i] + beta * (p[i] - w * v[i]);
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = r[i];
+    if (rs) {
+      q[i] = ri;
+      p[i] = ri;
+      v[i] = 0.0;
+    } else {
+      p[i] = ri + beta * (p[i] - w * v[i]);
+    }
+  }
+}
+
+// A breakdown restarts once (q = r); a second one ends the solve with EBREAKDOWN.
+RDEV bool bi_restart_or_fail(BiState* bi, SolveState* st) {
+  if (bi->restarted) {
+    st->done = 1;
+    st->status = REACH_EBREAKDOWN;
+    return false;
+  }
+  bi->restarted = 1;
+  bi->restart = 1;
+  bi->y = bi->rr;
+  return true;
 }
 
 template <int G, bool V>
@@ -412,9 +441,9 @@ __global__ void __launch_bounds__(NT) k_bi_v(int64_t nq, const int64_t* __restri
   double tot[1];
   if (last_cta_reduce<1, 0>(acc, part, ticket, tot) && threadIdx.x == 0) {
     bi->qv = tot[0];
+    bi->restart = 0;
     if (tot[0] == 0.0 || !(fabs(tot[0]) <= DBL_MAX)) {
-      st->done = 1;
-      st->status = REACH_EBREAKDOWN;
+      if (bi_restart_or_fail(bi, st)) bi->skip = 1;
     } else {
       bi->a = bi->y / tot[0];
     }
@@ -431,7 +460,7 @@ __global__ void __launch_bounds__(NT) k_bi_t(int64_t nq, const int64_t* __restri
                                              double* __restrict__ s_out, double* __restrict__ t,
                                              double* part, unsigned* ticket, BiState* bi,
                                              SolveState* st) {
-  if (st->done) return;
+  if (st->done || bi->skip) return;
   const double a = bi->a;
   RowGroups rg = RowGroups::make<G>();
   double acc[3] = {0.0, 0.0, 0.0};
@@ -472,10 +501,10 @@ __global__ void __launch_bounds__(NT) k_bi_x(int64_t nq, double* __restrict__ x,
                                              const double* __restrict__ t, double* __restrict__ r,
                                              const double* __restrict__ q, double* part,
                                              unsigned* ticket, BiState* bi, SolveState* st) {
-  if (st->done) return;
+  if (st->done || bi->skip) return;
   const double a = bi->a, w = bi->w;
   const int s_done = bi->s_done;
-  double acc[2] = {0.0, 0.0};
+  double acc[3] = {0.0, 0.0, 0.0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (s_done) {
@@ -485,11 +514,12 @@ __global__ void __launch_bounds__(NT) k_bi_x(int64_t nq, double* __restrict__ x,
       const double ri = s[i] - w * t[i];
       r[i] = ri;
       acc[0] = fma(q[i], ri, acc[0]);
-      acc[1] = fmax(acc[1], nan_to_inf(fabs(ri)));
+      acc[1] = fma(ri, ri, acc[1]);
+      acc[2] = fmax(acc[2], nan_to_inf(fabs(ri)));
     }
   }
-  double tot[2];
-  if (last_cta_reduce<1, 1>(acc, part, ticket, tot) && threadIdx.x == 0) {
+  double tot[3];
+  if (last_cta_reduce<2, 1>(acc, part, ticket, tot) && threadIdx.x == 0) {
     st->iter += 1;
     if (s_done) {
       st->last = bi->snorm;
@@ -497,19 +527,19 @@ __global__ void __launch_bounds__(NT) k_bi_x(int64_t nq, double* __restrict__ x,
       st->status = REACH_OK;
       return;
     }
-    bi->rnorm = tot[1];
-    st->last = tot[1];
+    bi->rnorm = tot[2];
+    bi->rr = tot[1];
+    st->last = tot[2];
     bi->yprev = bi->y;
     bi->y = tot[0];
-    if (tot[1] < st->eps) {
+    if (tot[2] < st->eps) {
       st->done = 1;
       st->status = REACH_OK;
     } else if (st->iter >= st->max_iter) {
       st->done = 1;
       st->status = REACH_ENOTCONV;
-    } else if (bi->y == 0.0 || w == 0.0) {
-      st->done = 1;
-      st->status = REACH_EBREAKDOWN;
+    } else if (bi->y == 0.0 || w == 0.0 || !(fabs(bi->y) <= DBL_MAX)) {
+      bi_restart_or_fail(bi, st);
     } else {
       bi->beta = (bi->y / bi->yprev) * (a / w);
     }
@@ -717,7 +747,7 @@ cudaError_t solve_bicgstab(reach_ctx* c, const double* x0q) {
   const Lay L = layout(c, nq, c->m_q);
   LAY_DISPATCH(L, l_bi_init, c, s);
   cudaError_t e = run_loop(c, 2, shape_key(c, L, 1), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
-    k_bi_p<<<ew_grid(c, (const void*)k_bi_p, nq), NT, 0, cs>>>(nq, c->vr, c->vp, c->vv, c->bi, c->st);
+    k_bi_p<<<ew_grid(c, (const void*)k_bi_p, nq), NT, 0, cs>>>(nq, c->vr, c->vp, c->vv, c->vq, c->bi, c->st);
     LAY_DISPATCH(L, l_bi_v, c, cs);
     LAY_DISPATCH(L, l_bi_t, c, cs);
     k_bi_x<<<ew_grid(c, (const void*)k_bi_x, nq), NT, 0, cs>>>(nq, c->x, c->vp, c->vs, c->vt, c->vr, c->vq,

@@ -236,6 +236,18 @@ def test_bicgstab_finite_termination(N, p):
     np.testing.assert_allclose(x, want, atol=1e-9, rtol=0)
 
 
+def test_bicgstab_restart_after_breakdown():
+    """With the shadow vector q = b sparse, q . r can vanish exactly; one restart with
+    q = r recovers and the answer matches the direct solve."""
+    c = synth.table1_chain(92, 211)
+    cls = O.partition(*chain_arrays(c))
+    q, a, b = O.extract_system(c.n, c.rowptr, c.col, c.val, cls)
+    m = O.system_matrix(a)
+    x, it, res, ok = O.bicgstab(m, b, 1e-14, 500)
+    assert ok
+    np.testing.assert_allclose(x, O.dense_solve(m, b), atol=1e-12, rtol=0)
+
+
 def test_bicgstab_iteration_cap():
     c = synth.gamblers_ruin(200, 0.5)
     cls = O.partition(*chain_arrays(c))
