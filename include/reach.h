@@ -133,6 +133,36 @@ reach_status reach_param_grad_theta(int64_t n, int64_t m, const int64_t* rowptr,
                                     const int32_t* cls, const double* p, const double* g_p,
                                     int32_t n_classes, double* g_theta, void* stream);
 
+/* ---- Batched multi-RHS: K <= 8 goal sets over one chain ---------------------------
+ * Many independent chains are solved together by passing their block-diagonal union
+ * (state ids offset per chain).  Each goal set j has its own partition (§2.2) and
+ * system (§2.3); one pass over the matrix serves all K right-hand sides.
+ *
+ * goals: uint8[k * n], goal set j in goals[j*n .. j*n + n); nonzero marks GS_j.  P is
+ * validated as in reach_create.  The context copies every input. */
+reach_status reach_batch_create(reach_batch** out, int64_t n, int64_t m, const int64_t* rowptr,
+                                const int32_t* col, const double* val, int32_t k,
+                                const uint8_t* goals, int32_t flags, void* stream);
+
+/* S=0_j / S=1_j / S?_j for every goal set j (mode as in reach_precompute) by a
+ * bit-parallel backward fixed point over P (one bit per goal set), plus the
+ * off-diagonal part of P over all states as FP32 hi + lo pairs and d = 1 - P(s,s). */
+reach_status reach_batch_precompute(reach_batch* b, int32_t mode);
+
+/* Classes as uint8[k * n] (0 = S=0, 1 = S=1, 2 = S?), goal-set major. */
+reach_status reach_batch_get_classes(reach_batch* b, uint8_t* cls, int32_t flags);
+
+/* Jacobi on every right-hand side at once, as FP32 sweeps with an FP64 residual and
+ * correction every refine_k sweeps (even, in [2, 62]; 0 = 16):
+ * x_j[s] <- sum_{s' != s} P(s,s') x_j[s'] / (1 - P(s,s)) on S?_j, with x_j = 1 on
+ * S=1_j and 0 on S=0_j.  Stops when the largest FP64 Jacobi step over all S?_j is
+ * below eps.  x_out: float64[k * n], goal-set major.  Synchronises the stream. */
+reach_status reach_batch_solve(reach_batch* b, double eps, int64_t max_iter, int32_t refine_k,
+                               double* x_out, int32_t flags, reach_info* info);
+
+/* Release the batch.  NULL is a no-op. */
+void reach_batch_destroy(reach_batch* b);
+
 /* Last error message of ctx (NULL: of the calling thread's last context-free call). */
 const char* reach_last_error(const reach_ctx* ctx);
 

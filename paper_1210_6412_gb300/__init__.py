@@ -24,7 +24,8 @@ __all__ = [
     "REACH_PROB0_ONLY", "REACH_JACOBI_FP64", "REACH_JACOBI_MIXED", "REACH_BICGSTAB_FP64",
     "reach_create", "reach_precompute", "reach_get_classes", "reach_solve", "reach_grad",
     "reach_param_probs", "reach_param_grad_theta", "reach_last_error", "reach_destroy",
-    "reach_version", "Solver",
+    "reach_version", "Solver", "reach_batch_create", "reach_batch_precompute",
+    "reach_batch_get_classes", "reach_batch_solve", "reach_batch_destroy", "BatchSolver",
 ]
 
 REACH_OK, REACH_EINVAL, REACH_ENOMEM, REACH_ECUDA, REACH_ESTATE = 0, 1, 2, 3, 4
@@ -72,6 +73,11 @@ _SIGS = {
     "reach_last_error": (C.c_char_p, [_P]),
     "reach_destroy": (None, [_P]),
     "reach_version": (C.c_char_p, []),
+    "reach_batch_create": (_I32, [C.POINTER(_P), _I64, _I64, _P, _P, _P, _I32, _P, _I32, _P]),
+    "reach_batch_precompute": (_I32, [_P, _I32]),
+    "reach_batch_get_classes": (_I32, [_P, _P, _I32]),
+    "reach_batch_solve": (_I32, [_P, _D, _I64, _I32, _P, _I32, C.POINTER(ReachInfo)]),
+    "reach_batch_destroy": (None, [_P]),
 }
 
 
@@ -269,6 +275,89 @@ class Solver:
         if self.ctx:
             reach_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ batched multi-RHS
+
+def reach_batch_create(n, rowptr, col, val, goals, stream=None):
+    """Batch over one chain with goal sets goals[k, n] (k <= 8)."""
+    k = int(goals.shape[0]) if hasattr(goals, "shape") and len(goals.shape) == 2 else None
+    if k is None:
+        raise ValueError("goals must be a [k, n] array")
+    rowptr_p, f0, k0 = _arg(rowptr, np.int64, n + 1, "rowptr")
+    m = int(rowptr[-1])
+    col_p, f1, k1 = _arg(col, np.int32, m, "col")
+    val_p, f2, k2 = _arg(val, np.float64, m, "val")
+    goal_p, f3, k3 = _arg(goals, np.uint8, k * n, "goals")
+    if len({f0, f1, f2, f3}) != 1:
+        raise ValueError("all inputs must live in the same memory (host or device)")
+    if stream is None:
+        stream = _torch_stream()
+    b = _P()
+    st = lib().reach_batch_create(C.byref(b), int(n), m, rowptr_p, col_p, val_p, k, goal_p, f0, stream)
+    _check(st, None, "reach_batch_create")
+    return b
+
+
+def reach_batch_precompute(b, mode=REACH_PROB01):
+    _check(lib().reach_batch_precompute(b, int(mode)), None, "reach_batch_precompute")
+
+
+def reach_batch_get_classes(b, n, k, out=None):
+    if out is None:
+        out = np.empty((k, n), np.uint8)
+    p, f, keep = _arg(out, np.uint8, k * n, "cls")
+    _check(lib().reach_batch_get_classes(b, p, f), None, "reach_batch_get_classes")
+    return out
+
+
+def reach_batch_solve(b, n, k, eps=1e-8, max_iter=1_000_000, refine_k=0, out=None, check=True):
+    if out is None:
+        out = np.empty((k, n), np.float64)
+    p, f, keep = _arg(out, np.float64, k * n, "x_out")
+    info = ReachInfo()
+    st = lib().reach_batch_solve(b, float(eps), int(max_iter), int(refine_k), p, f, C.byref(info))
+    if check and st != REACH_OK:
+        raise ReachError(st, reach_last_error(None) or "reach_batch_solve")
+    return out, info.as_dict()
+
+
+def reach_batch_destroy(b):
+    if b:
+        lib().reach_batch_destroy(b)
+
+
+class BatchSolver:
+    """K goal sets over one chain: ``BatchSolver(n, rowptr, col, val, goals[k, n])``."""
+
+    def __init__(self, n, rowptr, col, val, goals, mode=REACH_PROB01, stream=None):
+        self.n = int(n)
+        self.k = int(goals.shape[0])
+        self.b = reach_batch_create(n, rowptr, col, val, goals, stream)
+        reach_batch_precompute(self.b, mode)
+
+    def classes(self, out=None):
+        return reach_batch_get_classes(self.b, self.n, self.k, out)
+
+    def solve(self, eps=1e-8, max_iter=1_000_000, refine_k=0, out=None, check=True):
+        return reach_batch_solve(self.b, self.n, self.k, eps, max_iter, refine_k, out, check)
+
+    def close(self):
+        if self.b:
+            reach_batch_destroy(self.b)
+            self.b = None
 
     def __enter__(self):
         return self

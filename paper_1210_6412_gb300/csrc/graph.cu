@@ -495,12 +495,27 @@ static cudaError_t dmalloc(T** p, int64_t count) {
 }
 
 cudaError_t classify_and_extract(reach_ctx* c, int mode) {
-  cudaStream_t s = c->stream;
   const int64_t n = c->n, words = (n + 31) >> 5;
   uint8_t* qflag = reinterpret_cast<uint8_t*>(c->queue);   // scratch: n bytes
-  int64_t* bsum = reinterpret_cast<int64_t*>(c->part);
-  k_classify<<<grid_for(c, (const void*)k_classify, 256, n), 256, 0, s>>>(
+  k_classify<<<grid_for(c, (const void*)k_classify, 256, n), 256, 0, c->stream>>>(
       n, mode, c->goal, c->vis, c->vis + words, c->cls, qflag);
+  return extract_rows(c);
+}
+
+// Every state kept as a row (batched solves: the classes differ per right-hand side,
+// so the off-diagonal part of P and d = 1 - P_ss are extracted for all states).
+cudaError_t extract_all_rows(reach_ctx* c) {
+  cudaMemsetAsync(c->cls, CLS_SQ, c->n, c->stream);
+  cudaMemsetAsync(c->queue, 1, c->n, c->stream);
+  return extract_rows(c);
+}
+
+// Scan of the S? flags (bytes in c->queue) into qidx, then A, d, b over those rows.
+cudaError_t extract_rows(reach_ctx* c) {
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n;
+  uint8_t* qflag = reinterpret_cast<uint8_t*>(c->queue);
+  int64_t* bsum = reinterpret_cast<int64_t*>(c->part);
   int64_t* nq_dev = reinterpret_cast<int64_t*>(c->st);     // scratch word
   exclusive_scan<uint8_t>(qflag, c->qidx, n, nq_dev, bsum, s);
   int64_t nq = 0;

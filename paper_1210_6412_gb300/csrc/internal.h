@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 
 #include "../../include/reach.h"
@@ -143,6 +144,8 @@ cudaError_t launch_validate(reach_ctx* c);
 cudaError_t build_reverse_pattern(reach_ctx* c);
 cudaError_t bfs_backward(reach_ctx* c, int source_kind, bool avoid_goal);
 cudaError_t classify_and_extract(reach_ctx* c, int mode);
+cudaError_t extract_rows(reach_ctx* c);
+cudaError_t extract_all_rows(reach_ctx* c);
 cudaError_t split_hilo(reach_ctx* c);
 cudaError_t build_transposed_system(reach_ctx* c);
 
@@ -154,6 +157,11 @@ cudaError_t residual_inf(reach_ctx* c, const double* xq, double* out_host);
 cudaError_t scatter_full(reach_ctx* c, const double* xq, double* full);
 cudaError_t gather_q(reach_ctx* c, const double* full, double* xq);
 cudaError_t grad_entries(reach_ctx* c, const double* yq, double* grad);
+// Runs body inside a cached conditional-while graph (or host loop) until SolveState::done.
+cudaError_t run_loop(reach_ctx* c, cudaGraphExec_t& exec, int64_t& exec_key, int64_t key,
+                     const std::function<void(cudaStream_t, cudaGraphConditionalHandle, int)>& body);
+void launch_check_mixed(cudaStream_t s, SolveState* st, int slot, int k);
+void launch_finalize_resid(cudaStream_t s, SolveState* st);
 
 // ---- shared host helpers (api.cu)
 int pick_group(int64_t rows, int64_t nnz);

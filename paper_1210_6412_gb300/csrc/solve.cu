@@ -634,8 +634,8 @@ static int ew_grid(reach_ctx* c, const void* k, int64_t n) { return grid_for(c, 
 // Runs `body` inside a conditional while node until SolveState::done (device
 // loops), or relaunches it from the host and polls `done` (host loops).  Graphs
 // are cached in slot `gs` under `key`; the stopping parameters live in SolveState.
-static cudaError_t run_loop(reach_ctx* c, int gs, int64_t key,
-                            const std::function<void(cudaStream_t, cudaGraphConditionalHandle, int)>& body) {
+cudaError_t run_loop(reach_ctx* c, cudaGraphExec_t& exec, int64_t& exec_key, int64_t key,
+                     const std::function<void(cudaStream_t, cudaGraphConditionalHandle, int)>& body) {
   cudaError_t e = cudaSuccess;
   if (!c->device_loops) {
     int32_t done = 0;
@@ -648,9 +648,9 @@ static cudaError_t run_loop(reach_ctx* c, int gs, int64_t key,
     }
     return cudaGetLastError();
   }
-  if (c->g_exec[gs] == nullptr || c->g_key[gs] != key) {
-    if (c->g_exec[gs]) cudaGraphExecDestroy(c->g_exec[gs]);
-    c->g_exec[gs] = nullptr;
+  if (exec == nullptr || exec_key != key) {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphConditionalHandle h;
     e = cudaGraphCreate(&graph, 0);
@@ -671,15 +671,15 @@ static cudaError_t run_loop(reach_ctx* c, int gs, int64_t key,
         e = cudaStreamEndCapture(c->cap, &bg);
       }
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->g_exec[gs], graph, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
-      c->g_exec[gs] = nullptr;
+      exec = nullptr;
       return e;
     }
-    c->g_key[gs] = key;
+    exec_key = key;
   }
-  return cudaGraphLaunch(c->g_exec[gs], c->stream);
+  return cudaGraphLaunch(exec, c->stream);
 }
 
 static int64_t shape_key(reach_ctx* c, const Lay& L, int k) {
@@ -697,7 +697,8 @@ cudaError_t solve_jacobi64(reach_ctx* c, const double* x0q, bool transposed) {
                      : Sys{nq, c->a_rowptr, c->a_col, c->a_val, c->b};
   const Lay L = layout(c, nq, c->m_q);
   const int k = c->tune.k;
-  cudaError_t e = run_loop(c, transposed ? 3 : 0, shape_key(c, L, k),
+  const int gs = transposed ? 3 : 0;
+  cudaError_t e = run_loop(c, c->g_exec[gs], c->g_key[gs], shape_key(c, L, k),
                            [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
                              for (int j = 0; j < k; ++j) {
                                const double* xi = (j & 1) ? xb : xa;
@@ -721,7 +722,7 @@ cudaError_t solve_mixed(reach_ctx* c, const double* x0q) {
   else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
   const Lay L = layout(c, nq, c->m_q);
   const int k = c->tune.k;
-  e = run_loop(c, 1, shape_key(c, L, k), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
+  e = run_loop(c, c->g_exec[1], c->g_key[1], shape_key(c, L, k), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
     LAY_DISPATCH(L, l_resid_hilo, c, 0, cs);
     k_check_mixed<<<1, 1, 0, cs>>>(c->st, 0, k);
     // k - 1 FP32 sweeps: dl[1] -> dl[0] -> dl[1] ... ; k even, so the last lands in dl[0]
@@ -746,7 +747,7 @@ cudaError_t solve_bicgstab(reach_ctx* c, const double* x0q) {
   else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
   const Lay L = layout(c, nq, c->m_q);
   LAY_DISPATCH(L, l_bi_init, c, s);
-  cudaError_t e = run_loop(c, 2, shape_key(c, L, 1), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
+  cudaError_t e = run_loop(c, c->g_exec[2], c->g_key[2], shape_key(c, L, 1), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
     k_bi_p<<<ew_grid(c, (const void*)k_bi_p, nq), NT, 0, cs>>>(nq, c->vr, c->vp, c->vv, c->vq, c->bi, c->st);
     LAY_DISPATCH(L, l_bi_v, c, cs);
     LAY_DISPATCH(L, l_bi_t, c, cs);
@@ -759,6 +760,12 @@ cudaError_t solve_bicgstab(reach_ctx* c, const double* x0q) {
   k_finalize_resid<<<1, 1, 0, s>>>(c->st);
   return cudaGetLastError();
 }
+
+void launch_check_mixed(cudaStream_t s, SolveState* st, int slot, int k) {
+  k_check_mixed<<<1, 1, 0, s>>>(st, slot, k);
+}
+
+void launch_finalize_resid(cudaStream_t s, SolveState* st) { k_finalize_resid<<<1, 1, 0, s>>>(st); }
 
 // ------------------------------------------------------------------ full-state vectors
 
