@@ -92,6 +92,17 @@ reach_status reach_create(reach_ctx** out, int64_t n, int64_t m, const int64_t* 
                           const int32_t* col, const double* val, const uint8_t* goal,
                           int32_t flags, void* stream);
 
+/* A general sparse system M x = b instead of a chain: the random diagonally dominant
+ * matrices of §6 that the paper solves with the same Jacobi (§3.1) and BiCGStab (§3.2).
+ * M in the CSR layout above (finite values, any sign; duplicates summed; every diagonal
+ * entry non-zero), b: float64[n], same memory kind.  The context is ready for
+ * reach_solve at once (every row is an unknown; no partition, reach_precompute returns
+ * REACH_ESTATE): Jacobi runs x_i <- (b_i - sum_{j != i} M_ij x_j) / M_ii and BiCGStab
+ * runs on M.  reach_grad is not defined for it (REACH_ESTATE). */
+reach_status reach_system_create(reach_ctx** out, int64_t n, int64_t m, const int64_t* rowptr,
+                                 const int32_t* col, const double* val, const double* b,
+                                 int32_t flags, void* stream);
+
 /* Partition S into S=0 / S=1 / S? by backward breadth-first search over the
  * reversed underlying digraph (§2.2), then build A (off-diagonal, CSR over S? in
  * ascending state order), d = 1 - diag(A) and b (§2.3).  mode: reach_precomp_mode. */
@@ -110,6 +121,19 @@ reach_status reach_get_classes(reach_ctx* ctx, uint8_t* cls, int32_t flags);
 reach_status reach_solve(reach_ctx* ctx, int32_t method, double eps, int64_t max_iter,
                          int32_t refine_k, const double* x0, double* x_out, int32_t flags,
                          reach_info* info);
+
+/* Autotuner for the row mapping of `method` on the current system (after
+ * reach_precompute).  Times every candidate mapping of the method's dominant kernel --
+ * lanes per row 2, 4, 8, 16, 32, or a warp with 16-byte vector loads (reported as 64) --
+ * for a few launches and keeps the fastest for later solves of this context.  For
+ * JACOBI_FP64 it also picks the sweeps between convergence checks, used when
+ * reach_solve gets refine_k = 0.  Setting REACH_AUTOTUNE=1 in the environment makes the
+ * first reach_solve of each method run it.  Outputs (host, may be NULL): the chosen
+ * mapping, its time per sweep in ms, and the sweeps between checks.  Rows of this
+ * library's kernels are cut the same way for every method, so there is no paper
+ * counterpart beyond the one-thread-per-row mapping of §5.1. */
+reach_status reach_autotune(reach_ctx* ctx, int32_t method, int32_t* lanes, double* sweep_ms,
+                            int32_t* check_every);
 
 /* Gradient of x_init with respect to every stored entry of P, in input order:
  * grad[k] = y_s * x_{col[k]} for an entry of row s in S?, else 0, where

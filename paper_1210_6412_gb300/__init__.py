@@ -78,6 +78,8 @@ _SIGS = {
     "reach_batch_get_classes": (_I32, [_P, _P, _I32]),
     "reach_batch_solve": (_I32, [_P, _D, _I64, _I32, _P, _I32, C.POINTER(ReachInfo)]),
     "reach_batch_destroy": (None, [_P]),
+    "reach_autotune": (_I32, [_P, _I32, C.POINTER(_I32), C.POINTER(_D), C.POINTER(_I32)]),
+    "reach_system_create": (_I32, [C.POINTER(_P), _I64, _I64, _P, _P, _P, _P, _I32, _P]),
 }
 
 
@@ -170,6 +172,23 @@ def reach_create(n, rowptr, col, val, goal, stream=None):
     return ctx
 
 
+def reach_system_create(n, rowptr, col, val, b, stream=None):
+    """Context for a general system M x = b (M in CSR, any signs, non-zero diagonal)."""
+    rowptr_p, f0, k0 = _arg(rowptr, np.int64, n + 1, "rowptr")
+    m = int(rowptr[-1])
+    col_p, f1, k1 = _arg(col, np.int32, m, "col")
+    val_p, f2, k2 = _arg(val, np.float64, m, "val")
+    b_p, f3, k3 = _arg(b, np.float64, n, "b")
+    if len({f0, f1, f2, f3}) != 1:
+        raise ValueError("all inputs must live in the same memory (host or device)")
+    if stream is None:
+        stream = _torch_stream()
+    ctx = _P()
+    st = lib().reach_system_create(C.byref(ctx), int(n), m, rowptr_p, col_p, val_p, b_p, f0, stream)
+    _check(st, None, "reach_system_create")
+    return ctx
+
+
 def reach_precompute(ctx, mode=REACH_PROB01):
     _check(lib().reach_precompute(ctx, int(mode)), ctx)
 
@@ -243,20 +262,36 @@ def reach_param_grad_theta(rowptr, cls, p, g_p, n_classes, out, stream=None):
     return out
 
 
+def reach_autotune(ctx, method=REACH_JACOBI_FP64):
+    """Time the row mappings of ``method`` on this context's system; returns the choice."""
+    method = METHODS.get(method, method) if isinstance(method, str) else int(method)
+    lanes, ms, k = C.c_int32(0), C.c_double(0.0), C.c_int32(0)
+    _check(lib().reach_autotune(ctx, method, C.byref(lanes), C.byref(ms), C.byref(k)), ctx)
+    return {"lanes": lanes.value, "sweep_ms": ms.value, "check_every": k.value}
+
+
 def reach_destroy(ctx):
     if ctx:
         lib().reach_destroy(ctx)
 
 
 class Solver:
-    """Owns one context: ``with Solver(n, rowptr, col, val, goal) as s: x, info = s.solve()``."""
+    """Owns one context: ``with Solver(n, rowptr, col, val, goal) as s: x, info = s.solve()``.
 
-    def __init__(self, n, rowptr, col, val, goal, mode=REACH_PROB01, stream=None, precompute=True):
+    ``Solver.system(n, rowptr, col, val, b)`` builds one for a general system M x = b.
+    """
+
+    def __init__(self, n, rowptr, col, val, goal, mode=REACH_PROB01, stream=None, precompute=True,
+                 _ctx=None):
         self.n = int(n)
         self.m = int(rowptr[-1])
-        self.ctx = reach_create(n, rowptr, col, val, goal, stream)
-        if precompute:
+        self.ctx = _ctx if _ctx is not None else reach_create(n, rowptr, col, val, goal, stream)
+        if precompute and _ctx is None:
             self.precompute(mode)
+
+    @classmethod
+    def system(cls, n, rowptr, col, val, b, stream=None):
+        return cls(n, rowptr, col, val, None, _ctx=reach_system_create(n, rowptr, col, val, b, stream))
 
     def precompute(self, mode=REACH_PROB01):
         reach_precompute(self.ctx, mode)
@@ -270,6 +305,9 @@ class Solver:
 
     def grad(self, init, eps=1e-13, max_iter=1_000_000, out=None, check=True):
         return reach_grad(self.ctx, self.m, init, eps, max_iter, out, check)
+
+    def autotune(self, method="jacobi"):
+        return reach_autotune(self.ctx, method)
 
     def close(self):
         if self.ctx:

@@ -52,6 +52,20 @@ int grid_for(reach_ctx* c, const void* kernel, int threads, int64_t work) {
   return (int)std::min<int64_t>(std::min<int64_t>(full, need), MAX_GRID);
 }
 
+// Grid for a kernel in which G lanes own one row and rows are dealt round-robin.
+// With R resident row-groups at most, every group gets ceil(rows / R) rows; the grid is
+// then shrunk so that all groups get that many (the last few one fewer), so a sweep
+// over rows of similar length ends with every warp busy until the end.
+int grid_rows(reach_ctx* c, const void* kernel, int threads, int g, int64_t rows) {
+  const int full = grid_for(c, kernel, threads, INT64_MAX / 2);
+  const int64_t groups_per_cta = threads / g;
+  const int64_t max_groups = (int64_t)full * groups_per_cta;
+  if (rows <= 0) return 1;
+  const int64_t per = (rows + max_groups - 1) / max_groups;
+  const int64_t groups = (rows + per - 1) / per;
+  return (int)std::max<int64_t>(1, (groups + groups_per_cta - 1) / groups_per_cta);
+}
+
 }  // namespace reach
 
 using namespace reach;
@@ -140,21 +154,24 @@ void reach_destroy(reach_ctx* c) {
   delete c;
 }
 
-reach_status reach_create(reach_ctx** out, int64_t n, int64_t m, const int64_t* rowptr,
-                          const int32_t* col, const double* val, const uint8_t* goal, int32_t flags,
-                          void* stream) {
-  if (!out) return fail(nullptr, REACH_EINVAL, "reach_create: out is NULL");
-  if (n < 1 || n > INT32_MAX - 1) return fail(nullptr, REACH_EINVAL, "reach_create: n must be in [1, 2^31-2]");
-  if (m < 0) return fail(nullptr, REACH_EINVAL, "reach_create: m < 0");
-  if (!rowptr || !goal || (m > 0 && (!col || !val)))
-    return fail(nullptr, REACH_EINVAL, "reach_create: NULL input pointer");
+// Copies and validates P (a chain, or a general system when `general`).
+static reach_status create_common(reach_ctx** out, int64_t n, int64_t m, const int64_t* rowptr,
+                                  const int32_t* col, const double* val, const uint8_t* goal,
+                                  int32_t flags, void* stream, bool general, const char* who) {
+  const std::string w(who);
+  if (!out) return fail(nullptr, REACH_EINVAL, w + ": out is NULL");
+  if (n < 1 || n > INT32_MAX - 1) return fail(nullptr, REACH_EINVAL, w + ": n must be in [1, 2^31-2]");
+  if (m < 0) return fail(nullptr, REACH_EINVAL, w + ": m < 0");
+  if (!rowptr || (!general && !goal) || (m > 0 && (!col || !val)))
+    return fail(nullptr, REACH_EINVAL, w + ": NULL input pointer");
   if (flags != REACH_HOST && flags != REACH_DEVICE)
-    return fail(nullptr, REACH_EINVAL, "reach_create: flags must be REACH_HOST or REACH_DEVICE");
+    return fail(nullptr, REACH_EINVAL, w + ": flags must be REACH_HOST or REACH_DEVICE");
 
   reach_ctx* c = new reach_ctx();
   c->stream = (cudaStream_t)stream;
   c->n = n;
   c->m = m;
+  c->general = general;
   const char* hl = std::getenv("REACH_HOST_LOOPS");
   c->device_loops = !(hl && hl[0] == '1');
   cudaError_t e = cudaGetDevice(&c->device);
@@ -163,7 +180,7 @@ reach_status reach_create(reach_ctx** out, int64_t n, int64_t m, const int64_t* 
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
   if (e != cudaSuccess) {
-    reach_status s = cuda_fail(nullptr, e, "reach_create: device setup");
+    reach_status s = cuda_fail(nullptr, e, (w + ": device setup").c_str());
     reach_destroy(c);
     return s;
   }
@@ -178,7 +195,7 @@ reach_status reach_create(reach_ctx** out, int64_t n, int64_t m, const int64_t* 
       (e = dalloc(&c->st, 1)) != cudaSuccess || (e = dalloc(&c->bi, 1)) != cudaSuccess ||
       (e = dalloc(&c->part, part_n)) != cudaSuccess || (e = dalloc(&c->ticket, 1)) != cudaSuccess ||
       (e = dalloc(&c->verr, 1)) != cudaSuccess || (e = dalloc(&c->vrow, 1)) != cudaSuccess) {
-    reach_status s = cuda_fail(nullptr, e, "reach_create: allocation");
+    reach_status s = cuda_fail(nullptr, e, (w + ": allocation").c_str());
     reach_destroy(c);
     return s;
   }
@@ -186,7 +203,10 @@ reach_status reach_create(reach_ctx** out, int64_t n, int64_t m, const int64_t* 
   e = cudaMemcpyAsync(c->rowptr, rowptr, sizeof(int64_t) * (n + 1), kind_to_dev(flags), s);
   if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(c->col, col, sizeof(int32_t) * m, kind_to_dev(flags), s);
   if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(c->val, val, sizeof(double) * m, kind_to_dev(flags), s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->goal, goal, n, kind_to_dev(flags), s);
+  if (e == cudaSuccess) {
+    if (goal) e = cudaMemcpyAsync(c->goal, goal, n, kind_to_dev(flags), s);
+    else e = cudaMemsetAsync(c->goal, 0, n, s);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(c->col + m, 0, 8 * sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->val + m, 0, 8 * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ticket, 0, sizeof(unsigned), s);
@@ -195,13 +215,13 @@ reach_status reach_create(reach_ctx** out, int64_t n, int64_t m, const int64_t* 
   if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], c->rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    reach_status st = cuda_fail(nullptr, e, "reach_create: copying inputs");
+    reach_status st = cuda_fail(nullptr, e, (w + ": copying inputs").c_str());
     reach_destroy(c);
     return st;
   }
   if (ends[0] != 0 || ends[1] != m) {
     reach_destroy(c);
-    return fail(nullptr, REACH_EINVAL, "reach_create: rowptr[0] must be 0 and rowptr[n] must equal m");
+    return fail(nullptr, REACH_EINVAL, w + ": rowptr[0] must be 0 and rowptr[n] must equal m");
   }
   e = launch_validate(c);
   unsigned verr = 0;
@@ -210,15 +230,16 @@ reach_status reach_create(reach_ctx** out, int64_t n, int64_t m, const int64_t* 
   if (e == cudaSuccess) e = cudaMemcpyAsync(&vrow, c->vrow, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    reach_status st = cuda_fail(nullptr, e, "reach_create: validation");
+    reach_status st = cuda_fail(nullptr, e, (w + ": validation").c_str());
     reach_destroy(c);
     return st;
   }
   if (verr) {
-    std::string why = "reach_create: not a Markov chain (first bad row " + std::to_string(vrow) + ":";
+    std::string why = w + (general ? ": invalid system" : ": not a Markov chain") + " (first bad row " +
+                      std::to_string(vrow) + ":";
     if (verr & VERR_ROWPTR) why += " rowptr not non-decreasing within [0, m];";
     if (verr & VERR_COL) why += " column outside [0, n);";
-    if (verr & VERR_VAL) why += " value not finite in [0, 1];";
+    if (verr & VERR_VAL) why += general ? " value not finite;" : " value not finite in [0, 1];";
     if (verr & VERR_ROWSUM) why += " row does not sum to 1 within 1e-9;";
     why += ")";
     reach_destroy(c);
@@ -228,10 +249,69 @@ reach_status reach_create(reach_ctx** out, int64_t n, int64_t m, const int64_t* 
   return REACH_OK;
 }
 
+static cudaError_t alloc_workspace(reach_ctx* c) {
+  const int64_t nq = c->n_q;
+  cudaError_t e;
+  if ((e = dalloc(&c->x, nq)) != cudaSuccess || (e = dalloc(&c->x2, nq)) != cudaSuccess ||
+      (e = dalloc(&c->vr, nq)) != cudaSuccess || (e = dalloc(&c->vq, nq)) != cudaSuccess ||
+      (e = dalloc(&c->vp, nq)) != cudaSuccess || (e = dalloc(&c->vv, nq)) != cudaSuccess ||
+      (e = dalloc(&c->vs, nq)) != cudaSuccess || (e = dalloc(&c->vt, nq)) != cudaSuccess ||
+      (e = dalloc(&c->r32, nq)) != cudaSuccess || (e = dalloc(&c->dl[0], nq)) != cudaSuccess ||
+      (e = dalloc(&c->dl[1], nq)) != cudaSuccess)
+    free_system(c);
+  return e;
+}
+
+reach_status reach_create(reach_ctx** out, int64_t n, int64_t m, const int64_t* rowptr,
+                          const int32_t* col, const double* val, const uint8_t* goal, int32_t flags,
+                          void* stream) {
+  return create_common(out, n, m, rowptr, col, val, goal, flags, stream, false, "reach_create");
+}
+
+reach_status reach_system_create(reach_ctx** out, int64_t n, int64_t m, const int64_t* rowptr,
+                                 const int32_t* col, const double* val, const double* b, int32_t flags,
+                                 void* stream) {
+  if (!b) return fail(nullptr, REACH_EINVAL, "reach_system_create: b is NULL");
+  reach_ctx* c = nullptr;
+  reach_status st = create_common(&c, n, m, rowptr, col, val, nullptr, flags, stream, true,
+                                  "reach_system_create");
+  if (st != REACH_OK) return st;
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaEventRecord(c->ev0, s);
+  if (e == cudaSuccess) e = extract_all_rows(c);       // d = diag(M), A = -(off-diagonal of M)
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->b, b, sizeof(double) * n, kind_to_dev(flags), s);
+  if (e == cudaSuccess) e = check_diagonal(c);
+  unsigned verr = 0;
+  int64_t vrow = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&verr, c->verr, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&vrow, c->vrow, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && !verr) e = alloc_workspace(c);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(c->ev1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  if (e != cudaSuccess) {
+    st = cuda_fail(nullptr, e, "reach_system_create");
+    reach_destroy(c);
+    return st;
+  }
+  if (verr) {
+    reach_destroy(c);
+    return fail(nullptr, REACH_EINVAL,
+                "reach_system_create: zero diagonal entry in row " + std::to_string(vrow) + " (Jacobi divides by it)");
+  }
+  c->ms_precompute = ms;
+  c->have_classes = true;
+  *out = c;
+  return REACH_OK;
+}
+
 reach_status reach_precompute(reach_ctx* c, int32_t mode) {
   if (!c) return fail(nullptr, REACH_EINVAL, "reach_precompute: NULL context");
   if (mode != REACH_PROB01 && mode != REACH_PROB0_ONLY)
     return fail(c, REACH_EINVAL, "reach_precompute: unknown mode");
+  if (c->general) return fail(c, REACH_ESTATE, "reach_precompute: a general system has no partition");
   cudaStream_t s = c->stream;
   drop_graphs(c);
   free_system(c);
@@ -243,16 +323,7 @@ reach_status reach_precompute(reach_ctx* c, int32_t mode) {
   if (e == cudaSuccess && mode == REACH_PROB01) e = bfs_backward(c, 1, true);
   if (e == cudaSuccess) e = classify_and_extract(c, mode);
   if (e != cudaSuccess) return cuda_fail(c, e, "reach_precompute");
-  const int64_t nq = c->n_q;
-  if ((e = dalloc(&c->x, nq)) != cudaSuccess || (e = dalloc(&c->x2, nq)) != cudaSuccess ||
-      (e = dalloc(&c->vr, nq)) != cudaSuccess || (e = dalloc(&c->vq, nq)) != cudaSuccess ||
-      (e = dalloc(&c->vp, nq)) != cudaSuccess || (e = dalloc(&c->vv, nq)) != cudaSuccess ||
-      (e = dalloc(&c->vs, nq)) != cudaSuccess || (e = dalloc(&c->vt, nq)) != cudaSuccess ||
-      (e = dalloc(&c->r32, nq)) != cudaSuccess || (e = dalloc(&c->dl[0], nq)) != cudaSuccess ||
-      (e = dalloc(&c->dl[1], nq)) != cudaSuccess) {
-    free_system(c);
-    return cuda_fail(c, e, "reach_precompute: workspace");
-  }
+  if ((e = alloc_workspace(c)) != cudaSuccess) return cuda_fail(c, e, "reach_precompute: workspace");
   e = cudaEventRecord(c->ev1, s);
   if (e == cudaSuccess) e = cudaEventSynchronize(c->ev1);
   float ms = 0.f;
@@ -295,12 +366,22 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
     return fail(c, REACH_EINVAL, "reach_solve: unknown method");
   if (!(eps > 0.0) || !std::isfinite(eps)) return fail(c, REACH_EINVAL, "reach_solve: eps must be > 0");
   if (max_iter < 1) return fail(c, REACH_EINVAL, "reach_solve: max_iter must be >= 1");
+  const int32_t refine_k_given = refine_k;
   if (refine_k == 0) refine_k = 16;
   if (refine_k < 2 || refine_k > 62 || (refine_k & 1))
     return fail(c, REACH_EINVAL, "reach_solve: refine_k must be even in [2, 62]");
   if (!x_out || (flags != REACH_HOST && flags != REACH_DEVICE))
     return fail(c, REACH_EINVAL, "reach_solve: bad output");
   cudaStream_t s = c->stream;
+  const char* at = std::getenv("REACH_AUTOTUNE");
+  if (at && at[0] == '1' && c->n_q > 0 && c->tune.gm[method] == 0) {
+    int chosen = 0;
+    float ms = 0.f;
+    cudaError_t te = autotune(c, method, &chosen, &ms);
+    if (te != cudaSuccess) return cuda_fail(c, te, "reach_solve: autotune");
+  }
+  if (refine_k == 16 && refine_k_given == 0 && method == REACH_JACOBI_FP64 && c->tune.k_auto > 0)
+    refine_k = c->tune.k_auto;
   c->tune.k = refine_k;
   const int64_t max_bodies = method == REACH_BICGSTAB_FP64 ? max_iter + 4 : max_iter / refine_k + 4;
   reach_status rs = start_state(c, eps, max_iter, max_bodies);
@@ -367,9 +448,26 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
   return (reach_status)hs.status;
 }
 
+reach_status reach_autotune(reach_ctx* c, int32_t method, int32_t* lanes, double* sweep_ms,
+                            int32_t* check_every) {
+  if (!c) return fail(nullptr, REACH_EINVAL, "reach_autotune: NULL context");
+  if (!c->have_classes) return fail(c, REACH_ESTATE, "reach_autotune: call reach_precompute first");
+  if (method < REACH_JACOBI_FP64 || method > REACH_BICGSTAB_FP64)
+    return fail(c, REACH_EINVAL, "reach_autotune: unknown method");
+  int chosen = 0;
+  float ms = 0.f;
+  cudaError_t e = autotune(c, method, &chosen, &ms);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reach_autotune");
+  if (lanes) *lanes = chosen;
+  if (sweep_ms) *sweep_ms = ms;
+  if (check_every) *check_every = method == REACH_JACOBI_FP64 ? c->tune.k_auto : 16;
+  return REACH_OK;
+}
+
 reach_status reach_grad(reach_ctx* c, int64_t init, double eps, int64_t max_iter, double* grad,
                         int32_t flags, reach_info* info) {
   if (!c) return fail(nullptr, REACH_EINVAL, "reach_grad: NULL context");
+  if (c->general) return fail(c, REACH_ESTATE, "reach_grad: defined for chains only");
   if (!c->have_x) return fail(c, REACH_ESTATE, "reach_grad: needs a successful reach_solve first");
   if (init < 0 || init >= c->n) return fail(c, REACH_EINVAL, "reach_grad: init outside [0, n)");
   if (!(eps > 0.0) || max_iter < 1) return fail(c, REACH_EINVAL, "reach_grad: bad eps or max_iter");

@@ -259,7 +259,7 @@ __global__ void k_bclasses_out(int64_t n, int k, const uint8_t* __restrict__ sq,
 template <int G>
 static void l_pull(reach_batch* b, uint8_t* bits, const uint8_t* block, cudaStream_t s) {
   reach_ctx* c = b->base;
-  const int grid = grid_for(c, (const void*)k_pull_or<G>, BT, c->n * G);
+  const int grid = grid_rows(c, (const void*)k_pull_or<G>, BT, G, c->n);
   k_pull_or<G><<<grid, BT, 0, s>>>(c->n, c->rowptr, c->col, c->val, bits, block, (1u << b->k) - 1u,
                                    b->changed);
 }
@@ -268,11 +268,11 @@ template <int G>
 static void l_bresid(reach_batch* b, bool report, cudaStream_t s) {
   reach_ctx* c = b->base;
   if (report) {
-    const int grid = grid_for(c, (const void*)k_bresid<G, true>, BT, c->n * G);
+    const int grid = grid_rows(c, (const void*)k_bresid<G, true>, BT, G, c->n);
     k_bresid<G, true><<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_hi, c->a_lo, c->d, b->sq, b->X,
                                           b->R, b->D[1], c->st, 63);
   } else {
-    const int grid = grid_for(c, (const void*)k_bresid<G, false>, BT, c->n * G);
+    const int grid = grid_rows(c, (const void*)k_bresid<G, false>, BT, G, c->n);
     k_bresid<G, false><<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_hi, c->a_lo, c->d, b->sq,
                                            b->X, b->R, b->D[1], c->st, 0);
   }
@@ -281,7 +281,7 @@ static void l_bresid(reach_batch* b, bool report, cudaStream_t s) {
 template <int G>
 static void l_bsweep(reach_batch* b, const float* din, float* dout, cudaStream_t s) {
   reach_ctx* c = b->base;
-  const int grid = grid_for(c, (const void*)k_bsweep<G>, BT, c->n * G);
+  const int grid = grid_rows(c, (const void*)k_bsweep<G>, BT, G, c->n);
   k_bsweep<G><<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_hi, c->d32, b->sq, b->R, din, dout, c->st);
 }
 

@@ -113,7 +113,7 @@ static cudaError_t exclusive_scan(const T* in, int64_t* out, int64_t n, int64_t*
 template <int G>
 __global__ void k_validate(int64_t n, int64_t m, const int64_t* __restrict__ rp,
                            const int32_t* __restrict__ col, const double* __restrict__ val,
-                           double tol, unsigned* err, int64_t* bad_row) {
+                           double tol, unsigned* err, int64_t* bad_row, int general) {
   RowGroups rg = RowGroups::make<G>();
   for (int64_t s = rg.first; warp_has_row<G>(s, n); s += rg.stride) {
     bool act = s < n;
@@ -128,13 +128,14 @@ __global__ void k_validate(int64_t n, int64_t m, const int64_t* __restrict__ rp,
           int32_t cc = col[k];
           double v = val[k];
           if (cc < 0 || (int64_t)cc >= n) e |= VERR_COL;
-          if (!(v >= 0.0 && v <= 1.0)) e |= VERR_VAL;
+          // a chain needs probabilities; a general system only finite entries
+          if (general ? !(fabs(v) <= 1.7976931348623157e308) : !(v >= 0.0 && v <= 1.0)) e |= VERR_VAL;
           sum += v;
         }
       }
     }
     sum = group_sum<G>(sum);
-    if (act && rg.lane == 0 && !(e & VERR_ROWPTR) && !(fabs(sum - 1.0) <= tol)) e |= VERR_ROWSUM;
+    if (!general && act && rg.lane == 0 && !(e & VERR_ROWPTR) && !(fabs(sum - 1.0) <= tol)) e |= VERR_ROWSUM;
     if (e) {
       atomicOr(err, e);
       atomicMin((unsigned long long*)bad_row, (unsigned long long)s);
@@ -149,12 +150,32 @@ cudaError_t launch_validate(reach_ctx* c) {
   if (mean >= 16) {
     int grid = grid_for(c, (const void*)k_validate<32>, 256, c->n * 32);
     k_validate<32><<<grid, 256, 0, c->stream>>>(c->n, c->m, c->rowptr, c->col, c->val, 1e-9,
-                                                c->verr, c->vrow);
+                                                c->verr, c->vrow, c->general ? 1 : 0);
   } else {
     int grid = grid_for(c, (const void*)k_validate<4>, 256, c->n * 4);
     k_validate<4><<<grid, 256, 0, c->stream>>>(c->n, c->m, c->rowptr, c->col, c->val, 1e-9,
-                                               c->verr, c->vrow);
+                                               c->verr, c->vrow, c->general ? 1 : 0);
   }
+  return cudaGetLastError();
+}
+
+// A general system needs every diagonal entry non-zero (Jacobi divides by it).
+__global__ void k_check_diag(int64_t nq, const double* __restrict__ d, unsigned* err, int64_t* bad_row) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (d[i] == 0.0) {
+      atomicOr(err, VERR_ROWSUM);
+      atomicMin((unsigned long long*)bad_row, (unsigned long long)i);
+    }
+  }
+}
+
+cudaError_t check_diagonal(reach_ctx* c) {
+  cudaMemsetAsync(c->verr, 0, sizeof(unsigned), c->stream);
+  cudaMemsetAsync(c->vrow, 0x7f, sizeof(int64_t), c->stream);
+  if (c->n_q > 0)
+    k_check_diag<<<grid_for(c, (const void*)k_check_diag, 256, c->n_q), 256, 0, c->stream>>>(
+        c->n_q, c->d, c->verr, c->vrow);
   return cudaGetLastError();
 }
 
@@ -384,7 +405,7 @@ __global__ void k_extract_count(int64_t n, const int64_t* __restrict__ rp, const
                                 const double* __restrict__ val, const uint8_t* __restrict__ cls,
                                 const int64_t* __restrict__ qidx, int64_t* __restrict__ acnt,
                                 double* __restrict__ d, double* __restrict__ b,
-                                int64_t* __restrict__ qstate) {
+                                int64_t* __restrict__ qstate, int general) {
   RowGroups rg = RowGroups::make<G>();
   for (int64_t s = rg.first; warp_has_row<G>(s, n); s += rg.stride) {
     const bool act = s < n && cls[s] == CLS_SQ;
@@ -409,8 +430,9 @@ __global__ void k_extract_count(int64_t n, const int64_t* __restrict__ rp, const
     if (act && rg.lane == 0) {
       const int64_t i = qidx[s];
       acnt[i] = (int64_t)cnt;
-      d[i] = 1.0 - diag;
-      b[i] = bs;
+      // chain: d = 1 - A_ii of I - A; general system M x = b: d = M_ii, b given
+      d[i] = general ? diag : 1.0 - diag;
+      if (!general) b[i] = bs;
       qstate[i] = s;
     }
   }
@@ -420,7 +442,7 @@ template <int G>
 __global__ void k_extract_fill(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                const double* __restrict__ val, const uint8_t* __restrict__ cls,
                                const int64_t* __restrict__ qidx, const int64_t* __restrict__ arp,
-                               int32_t* __restrict__ acol, double* __restrict__ aval) {
+                               int32_t* __restrict__ acol, double* __restrict__ aval, int general) {
   RowGroups rg = RowGroups::make<G>();
   const int wl = threadIdx.x & 31;
   const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (wl & ~(G - 1)));
@@ -449,7 +471,7 @@ __global__ void k_extract_fill(int64_t n, const int64_t* __restrict__ rp, const 
       if (p) {
         const int64_t pos = out + __popc(mine & lt);
         acol[pos] = cq;
-        aval[pos] = v;
+        aval[pos] = general ? -v : v;   // general system: A = -(off-diagonal of M)
       }
       out += __popc(mine);
     }
@@ -468,10 +490,10 @@ static void extract_launch(reach_ctx* c, int64_t* acnt, int pass) {
                             256, c->n * G);
   if (pass == 0)
     k_extract_count<G><<<grid, 256, 0, c->stream>>>(c->n, c->rowptr, c->col, c->val, c->cls, c->qidx,
-                                                    acnt, c->d, c->b, c->qstate);
+                                                    acnt, c->d, c->b, c->qstate, c->general ? 1 : 0);
   else
     k_extract_fill<G><<<grid, 256, 0, c->stream>>>(c->n, c->rowptr, c->col, c->val, c->cls, c->qidx,
-                                                   c->a_rowptr, c->a_col, c->a_val);
+                                                   c->a_rowptr, c->a_col, c->a_val, c->general ? 1 : 0);
 }
 
 static void extract_dispatch(reach_ctx* c, int g, int64_t* acnt, int pass) {

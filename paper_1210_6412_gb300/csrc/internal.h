@@ -51,8 +51,10 @@ struct BfsState {
 };
 
 struct Tuning {
-  int g = 0;            // lanes per row for CSR kernels (0 = pick from mean degree)
+  int g = 0;            // lanes per row for CSR kernels (0 = pick from mean degree; 64 = warp + vector loads)
+  int gm[3] = {0, 0, 0};  // autotuned lanes-per-row code per method (0 = none)
   int k = 16;           // sweeps between convergence checks / refinement period
+  int k_auto = 0;       // autotuned sweeps between checks for FP64 Jacobi (0 = none)
   int cta = 256;        // threads per CTA
 };
 
@@ -80,6 +82,9 @@ struct reach_ctx {
   // reversed underlying digraph (pattern of P^T, entries with P > 0)
   int64_t* t_rowptr = nullptr;
   int32_t* t_col = nullptr;
+
+  // general system M x = b (no partition): A = -(off-diagonal of M), d = diag(M)
+  bool general = false;
 
   // partition
   bool have_classes = false;
@@ -141,6 +146,7 @@ namespace reach {
 
 // ---- graph.cu
 cudaError_t launch_validate(reach_ctx* c);
+cudaError_t check_diagonal(reach_ctx* c);
 cudaError_t build_reverse_pattern(reach_ctx* c);
 cudaError_t bfs_backward(reach_ctx* c, int source_kind, bool avoid_goal);
 cudaError_t classify_and_extract(reach_ctx* c, int mode);
@@ -161,11 +167,13 @@ cudaError_t grad_entries(reach_ctx* c, const double* yq, double* grad);
 cudaError_t run_loop(reach_ctx* c, cudaGraphExec_t& exec, int64_t& exec_key, int64_t key,
                      const std::function<void(cudaStream_t, cudaGraphConditionalHandle, int)>& body);
 void launch_check_mixed(cudaStream_t s, SolveState* st, int slot, int k);
+cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms);
 void launch_finalize_resid(cudaStream_t s, SolveState* st);
 
 // ---- shared host helpers (api.cu)
 int pick_group(int64_t rows, int64_t nnz);
 int grid_for(reach_ctx* c, const void* kernel, int threads, int64_t work_items);
+int grid_rows(reach_ctx* c, const void* kernel, int threads, int g, int64_t rows);
 bool set_err(reach_ctx* c, const std::string& msg);
 
 }  // namespace reach

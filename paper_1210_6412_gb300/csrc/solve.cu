@@ -2,7 +2,9 @@
 // FP32 sweeps with FP64 defect correction, and unpreconditioned BiCGStab (§3.2)
 // with FP64 scalars kept on the device.  Every loop runs inside one CUDA graph
 // with a conditional while node; the stopping rule is evaluated on the device.
+#include <algorithm>
 #include <cfloat>
+#include <cmath>
 #include <functional>
 
 #include "common.cuh"
@@ -553,9 +555,13 @@ struct Lay {
   bool vec;
 };
 
-static Lay layout(reach_ctx* c, int64_t rows, int64_t nnz) {
-  if (c->tune.g == 64) return {32, true};
-  if (c->tune.g > 0) return {c->tune.g, false};
+static Lay lay_of(int code) { return code == 64 ? Lay{32, true} : Lay{code, false}; }
+
+// Row mapping of `method`'s kernels: the autotuned choice if there is one, else the
+// REACH_LANES override, else lanes from the mean row length (warp + 16-byte loads from 96).
+static Lay layout(reach_ctx* c, int64_t rows, int64_t nnz, int method = 0) {
+  if (method >= 0 && method < 3 && c->tune.gm[method] > 0) return lay_of(c->tune.gm[method]);
+  if (c->tune.g > 0) return lay_of(c->tune.g);
   const int g = pick_group(rows, nnz);
   const bool vec = g == 32 && rows > 0 && nnz / rows >= 96;
   return {g, vec};
@@ -584,47 +590,47 @@ struct Sys {
 template <int G, bool V>
 static void l_jacobi(reach_ctx* c, const Sys& y, const double* x, double* xn, unsigned long long* slot,
                      cudaStream_t s) {
-  const int grid = grid_for(c, (const void*)k_jacobi64<G, V>, NT, y.nq * G);
+  const int grid = grid_rows(c, (const void*)k_jacobi64<G, V>, NT, G, y.nq);
   k_jacobi64<G, V><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, c->d, x, xn, slot);
 }
 
 template <int G, bool V>
 static void l_resid(reach_ctx* c, const Sys& y, const double* x, cudaStream_t s) {
-  const int grid = grid_for(c, (const void*)k_resid64<G, V>, NT, y.nq * G);
+  const int grid = grid_rows(c, (const void*)k_resid64<G, V>, NT, G, y.nq);
   k_resid64<G, V><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, c->d, x, &c->st->slot[63]);
 }
 
 template <int G, bool V>
 static void l_resid_hilo(reach_ctx* c, int slot, cudaStream_t s) {
-  const int grid = grid_for(c, (const void*)k_resid_hilo<G, V>, NT, c->n_q * G);
+  const int grid = grid_rows(c, (const void*)k_resid_hilo<G, V>, NT, G, c->n_q);
   k_resid_hilo<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->a_lo, c->b, c->d,
                                          c->x, c->r32, c->dl[1], c->st, slot);
 }
 
 template <int G, bool V>
 static void l_sweep32(reach_ctx* c, const float* din, float* dout, cudaStream_t s) {
-  const int grid = grid_for(c, (const void*)k_sweep32<G, V>, NT, c->n_q * G);
+  const int grid = grid_rows(c, (const void*)k_sweep32<G, V>, NT, G, c->n_q);
   k_sweep32<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->r32, c->d32, din, dout,
                                       c->st);
 }
 
 template <int G, bool V>
 static void l_bi_init(reach_ctx* c, cudaStream_t s) {
-  const int grid = grid_for(c, (const void*)k_bi_init<G, V>, NT, c->n_q * G);
+  const int grid = grid_rows(c, (const void*)k_bi_init<G, V>, NT, G, c->n_q);
   k_bi_init<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_val, c->b, c->d, c->x, c->vr,
                                       c->vq, c->vp, c->vv, c->part, c->ticket, c->bi, c->st);
 }
 
 template <int G, bool V>
 static void l_bi_v(reach_ctx* c, cudaStream_t s) {
-  const int grid = grid_for(c, (const void*)k_bi_v<G, V>, NT, c->n_q * G);
+  const int grid = grid_rows(c, (const void*)k_bi_v<G, V>, NT, G, c->n_q);
   k_bi_v<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_val, c->d, c->vp, c->vq, c->vv,
                                    c->part, c->ticket, c->bi, c->st);
 }
 
 template <int G, bool V>
 static void l_bi_t(reach_ctx* c, cudaStream_t s) {
-  const int grid = grid_for(c, (const void*)k_bi_t<G, V>, NT, c->n_q * G);
+  const int grid = grid_rows(c, (const void*)k_bi_t<G, V>, NT, G, c->n_q);
   k_bi_t<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_val, c->d, c->vr, c->vv, c->vs,
                                    c->vt, c->part, c->ticket, c->bi, c->st);
 }
@@ -695,7 +701,7 @@ cudaError_t solve_jacobi64(reach_ctx* c, const double* x0q, bool transposed) {
   else cudaMemsetAsync(xa, 0, sizeof(double) * nq, s);
   Sys y = transposed ? Sys{nq, c->at_rowptr, c->at_col, c->at_val, c->vp}
                      : Sys{nq, c->a_rowptr, c->a_col, c->a_val, c->b};
-  const Lay L = layout(c, nq, c->m_q);
+  const Lay L = transposed ? layout(c, nq, c->m_q, -1) : layout(c, nq, c->m_q, REACH_JACOBI_FP64);
   const int k = c->tune.k;
   const int gs = transposed ? 3 : 0;
   cudaError_t e = run_loop(c, c->g_exec[gs], c->g_key[gs], shape_key(c, L, k),
@@ -720,7 +726,7 @@ cudaError_t solve_mixed(reach_ctx* c, const double* x0q) {
   if (e != cudaSuccess) return e;
   if (x0q) cudaMemcpyAsync(c->x, x0q, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
   else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
-  const Lay L = layout(c, nq, c->m_q);
+  const Lay L = layout(c, nq, c->m_q, REACH_JACOBI_MIXED);
   const int k = c->tune.k;
   e = run_loop(c, c->g_exec[1], c->g_key[1], shape_key(c, L, k), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
     LAY_DISPATCH(L, l_resid_hilo, c, 0, cs);
@@ -745,7 +751,7 @@ cudaError_t solve_bicgstab(reach_ctx* c, const double* x0q) {
   const int64_t nq = c->n_q;
   if (x0q) cudaMemcpyAsync(c->x, x0q, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
   else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
-  const Lay L = layout(c, nq, c->m_q);
+  const Lay L = layout(c, nq, c->m_q, REACH_BICGSTAB_FP64);
   LAY_DISPATCH(L, l_bi_init, c, s);
   cudaError_t e = run_loop(c, c->g_exec[2], c->g_key[2], shape_key(c, L, 1), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
     k_bi_p<<<ew_grid(c, (const void*)k_bi_p, nq), NT, 0, cs>>>(nq, c->vr, c->vp, c->vv, c->vq, c->bi, c->st);
@@ -823,6 +829,65 @@ cudaError_t grad_entries(reach_ctx* c, const double* yq, double* grad) {
   }
 #undef KG
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ autotuner
+// Times each row mapping (lanes per row 2..32, or a warp with 16-byte loads) for the
+// kernel that dominates `method` on the current system and keeps the fastest.  For FP64
+// Jacobi it also picks the sweeps between checks k from the measured sweep time t and
+// the check cost c (about the time of two tiny launches): minimising N t + (N / k) c +
+// (k / 2) t for N = 1000 sweeps gives k = sqrt(2 N c / t), rounded to an even number.
+cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
+  if (c->n_q == 0) {
+    *chosen = 0;
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaSuccess;
+  if (method == REACH_JACOBI_MIXED) {
+    e = split_hilo(c);
+    if (e != cudaSuccess) return e;
+  }
+  const int codes[6] = {2, 4, 8, 16, 32, 64};
+  const double mean = (double)c->m_q / (double)c->n_q;
+  Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_val, c->b};
+  cudaStream_t s = c->stream;
+  float best = 1e30f;
+  int pick = 0;
+  for (int code : codes) {
+    const Lay L = lay_of(code);
+    if (L.vec && mean < 16) continue;            // nothing to vectorise
+    if (!L.vec && L.g > 4 * mean + 4) continue;  // mostly idle lanes
+    float total = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {
+      e = cudaEventRecord(c->ev0, s);
+      if (method == REACH_JACOBI_MIXED) {
+        LAY_DISPATCH(L, l_sweep32, c, c->dl[0], c->dl[1], s);
+      } else {
+        LAY_DISPATCH(L, l_jacobi, c, y, c->x, c->x2, &c->st->slot[62], s);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(c->ev1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(c->ev1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+      if (e != cudaSuccess) return e;
+      if (rep > 0) total += ms;               // first launch is a warm-up
+    }
+    const float avg = total / 3.f;
+    if (avg < best) {
+      best = avg;
+      pick = code;
+    }
+  }
+  c->tune.gm[method] = pick;
+  if (method == REACH_JACOBI_FP64) {
+    const double check_ms = 0.006, sweeps = 1000.0;
+    int k = (int)std::lround(std::sqrt(2.0 * sweeps * check_ms / std::max(1e-4, (double)best)));
+    k = std::max(2, std::min(62, k + (k & 1)));
+    c->tune.k_auto = k;
+  }
+  *chosen = pick;
+  *best_ms = best;
+  return cudaSuccess;
 }
 
 }  // namespace reach

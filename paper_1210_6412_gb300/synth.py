@@ -315,6 +315,63 @@ def batched_chains(n_chains=256, n_min=1_000, n_max=2_000_000, dmin=2, dmax=32, 
     return out
 
 
+@dataclass
+class System:
+    """A general sparse system M x = b in CSR (diagonal included)."""
+
+    n: int
+    rowptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    b: np.ndarray
+    name: str = ""
+
+    @property
+    def m(self) -> int:
+        return int(self.rowptr[-1])
+
+
+def diag_dominant_system(n=4096, density=0.01, max_int=10, margin=(1, 10), seed=1210_6412_7):
+    """The random systems of §6: random positive integers at random positions, made
+    diagonally dominant with a non-zero diagonal, and a random integer right-hand side.
+
+    Off-diagonal entries: each present with probability ``density``, value U{1..max_int}.
+    Diagonal: the row's off-diagonal sum plus U{margin}, so every row is strictly
+    dominant.  b: U{1..max_int}.  The integer ranges are not stated in the paper.
+    """
+    rng = np.random.default_rng(seed)
+    cols, degs = [], []
+    mean = max(density * n, 1e-9)
+    kmax = int(np.ceil(mean + 10.0 * np.sqrt(mean) + 16))
+    for r0 in range(0, n, 1024):
+        rows = min(1024, n - r0)
+        pos = np.cumsum(rng.geometric(density, size=(rows, kmax)), axis=1) - 1
+        short = np.flatnonzero(pos[:, -1] < n)
+        while short.size:
+            pos[short] = np.cumsum(rng.geometric(density, size=(short.size, kmax)), axis=1) - 1
+            short = short[pos[short, -1] < n]
+        diag = (r0 + np.arange(rows))[:, None]
+        keep = (pos < n) & (pos != diag)
+        pos = np.where(keep, pos, n + 1)
+        pos = np.concatenate([pos, diag], axis=1)
+        pos.sort(axis=1)
+        keep = pos < n
+        cols.append(pos[keep].astype(np.int32))
+        degs.append(keep.sum(axis=1))
+    col = np.concatenate(cols)
+    deg = np.concatenate(degs).astype(np.int64)
+    rowptr = _rowptr(deg)
+    row_of = np.repeat(np.arange(n), deg)
+    val = rng.integers(1, max_int + 1, size=col.size).astype(np.float64)
+    is_diag = col == row_of
+    off = np.where(is_diag, 0.0, val)
+    offsum = np.add.reduceat(off, rowptr[:-1]) if n else np.zeros(0)
+    val[is_diag] = offsum + rng.integers(margin[0], margin[1] + 1, size=n)
+    b = rng.integers(1, max_int + 1, size=n).astype(np.float64)
+    return System(n=n, rowptr=rowptr, col=col, val=val, b=b,
+                  name=f"diagonally dominant n={n} density={density}")
+
+
 def gamblers_ruin(N=20, p=0.4):
     """Random walk on 0..N, up with probability p, down with 1-p; 0 and N absorbing; GS={N}."""
     n = N + 1

@@ -76,6 +76,16 @@ def test_batched_chains_regenerate_and_concat():
     assert all(np.array_equal(x.val, y.val) for x, y in zip(b.chains, b2.chains))
 
 
+def test_diag_dominant_system():
+    import scipy.sparse as sp
+    s = synth.diag_dominant_system(n=1500, density=0.02, seed=3)
+    m = sp.csr_matrix((s.val, s.col, s.rowptr), shape=(s.n, s.n))
+    d = m.diagonal()
+    assert np.all(d > np.abs(m).sum(axis=1).A1 - np.abs(d))          # strictly dominant
+    assert np.all(s.val == np.round(s.val)) and np.all(s.val >= 1)   # positive integers
+    assert np.all(s.b == np.round(s.b)) and abs(m.nnz / s.n ** 2 - 0.02) < 0.005
+
+
 @pytest.mark.parametrize("n,m", synth.TABLE1_QUICKSORT[:3] + synth.TABLE1_BIASED_DIE[:2])
 def test_table1_shapes(n, m):
     c = synth.table1_chain(n, m)
