@@ -56,8 +56,10 @@ int grid_for(reach_ctx* c, const void* kernel, int threads, int64_t work) {
 // With R resident row-groups at most, every group gets ceil(rows / R) rows; the grid is
 // then shrunk so that all groups get that many (the last few one fewer), so a sweep
 // over rows of similar length ends with every warp busy until the end.
-int grid_rows(reach_ctx* c, const void* kernel, int threads, int g, int64_t rows) {
+int grid_rows(reach_ctx* c, const void* kernel, int threads, int g, int64_t rows, bool dynamic) {
   const int full = grid_for(c, kernel, threads, INT64_MAX / 2);
+  // dynamic rows: every resident CTA, capped at one warp per row
+  if (dynamic) return (int)std::max<int64_t>(1, std::min<int64_t>(full, (rows + threads / 32 - 1) / (threads / 32)));
   const int64_t groups_per_cta = threads / g;
   const int64_t max_groups = (int64_t)full * groups_per_cta;
   if (rows <= 0) return 1;
@@ -105,11 +107,11 @@ void dfree(T*& p) {
 }
 
 void free_system(reach_ctx* c) {
-  dfree(c->a_rowptr); dfree(c->a_col); dfree(c->a_val); dfree(c->a_hi); dfree(c->a_lo);
+  dfree(c->a_rowptr); dfree(c->a_col); dfree(c->a_val); dfree(c->a_hi); dfree(c->a_lo); dfree(c->a_col16);
   dfree(c->d); dfree(c->b); dfree(c->d32); dfree(c->qstate);
   dfree(c->at_rowptr); dfree(c->at_col); dfree(c->at_val);
   dfree(c->x); dfree(c->x2); dfree(c->vr); dfree(c->vq); dfree(c->vp); dfree(c->vv);
-  dfree(c->vs); dfree(c->vt); dfree(c->r32); dfree(c->dl[0]); dfree(c->dl[1]);
+  dfree(c->vs); dfree(c->vt); dfree(c->r32); dfree(c->xf); dfree(c->dl[0]); dfree(c->dl[1]);
 }
 
 void drop_graphs(reach_ctx* c) {
@@ -256,7 +258,8 @@ static cudaError_t alloc_workspace(reach_ctx* c) {
       (e = dalloc(&c->vr, nq)) != cudaSuccess || (e = dalloc(&c->vq, nq)) != cudaSuccess ||
       (e = dalloc(&c->vp, nq)) != cudaSuccess || (e = dalloc(&c->vv, nq)) != cudaSuccess ||
       (e = dalloc(&c->vs, nq)) != cudaSuccess || (e = dalloc(&c->vt, nq)) != cudaSuccess ||
-      (e = dalloc(&c->r32, nq)) != cudaSuccess || (e = dalloc(&c->dl[0], nq)) != cudaSuccess ||
+      (e = dalloc(&c->r32, nq)) != cudaSuccess || (e = dalloc(&c->xf, nq)) != cudaSuccess ||
+      (e = dalloc(&c->dl[0], nq)) != cudaSuccess ||
       (e = dalloc(&c->dl[1], nq)) != cudaSuccess)
     free_system(c);
   return e;

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(BT) k_bresid(int64_t n, const int64_t* __restr
     for (int j = 0; j < 8; ++j) acc[j] = 0.0;
     if (s < n) {
       for (int64_t k = rp[s] + rg.lane; k < rp[s + 1]; k += G) {
-        const double v = (double)__ldcs(ah + k) + (double)__ldcs(al + k);
+        const double v = widen(__ldcs(ah + k)) + widen(__ldcs(al + k));
         const double2* xr = reinterpret_cast<const double2*>(X + (int64_t)__ldcs(ci + k) * 8);
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(BT) k_bresid(int64_t n, const int64_t* __restr
         if (REPORT) {
           mx = fmax(mx, fabs(r));
         } else {
-          const double qd = r / ds;
+          // absorbing states have d_s = 0 but are never in S?: divide on S? only
+          const double qd = q ? r / ds : 0.0;
           R[s * 8 + j] = __double2float_rn(r);
           D1[s * 8 + j] = __double2float_rn(qd);
           mx = fmax(mx, fabs(qd));

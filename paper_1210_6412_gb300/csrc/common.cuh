@@ -50,6 +50,20 @@ RDEV void block_reduce(double (&v)[NV], double* sh) {
   __syncthreads();
 }
 
+// FP32 -> FP64 widening with integer operations.  On GB300 the conversion
+// instruction shares the (narrow) FP64 pipe, while the bit rearrangement below runs
+// on the integer units; both are exact.  Zero, subnormal, infinite and NaN inputs
+// (never produced by the hi/lo split of a probability except zero padding) take the
+// hardware conversion.
+RDEV double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const uint64_t d = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
+                     ((uint64_t)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
 // Max of non-negative doubles through the integer order of their bit patterns.
 RDEV void atomic_max_nonneg(unsigned long long* slot, double v) {
   if (v > 0.0) atomicMax(slot, (unsigned long long)__double_as_longlong(v));
@@ -109,6 +123,30 @@ template <int G>
 RDEV bool warp_has_row(int64_t row, int64_t nrows) {
   const int64_t warp_first = row - ((threadIdx.x & 31) / G);
   return warp_first < nrows;
+}
+
+// Row order of a kernel.  Static: groups take rows first, first + stride, ...
+// Dynamic (warp per row, ctr != nullptr): each warp takes the next row from a
+// counter in device memory, so warps that drew short rows take more of them and all
+// SMs stay busy until the last rows (the counter must be 0 at launch).
+RDEV int64_t warp_fetch_row(unsigned* ctr) {
+  unsigned r = 0;
+  if ((threadIdx.x & 31) == 0) r = atomicAdd(ctr, 1u);
+  return (int64_t)__shfl_sync(FULL, r, 0);
+}
+template <int G>
+RDEV int64_t row_begin(const RowGroups& rg, unsigned* ctr) {
+  if constexpr (G == 32) {
+    if (ctr) return warp_fetch_row(ctr);
+  }
+  return rg.first;
+}
+template <int G>
+RDEV int64_t row_next(const RowGroups& rg, unsigned* ctr, int64_t i) {
+  if constexpr (G == 32) {
+    if (ctr) return warp_fetch_row(ctr);
+  }
+  return i + rg.stride;
 }
 
 }  // namespace reach

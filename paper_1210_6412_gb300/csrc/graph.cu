@@ -573,6 +573,7 @@ cudaError_t extract_rows(reach_ctx* c) {
   // the hi/lo split and the transposed system are rebuilt on demand
   if (c->a_hi) { cudaFree(c->a_hi); c->a_hi = nullptr; }
   if (c->a_lo) { cudaFree(c->a_lo); c->a_lo = nullptr; }
+  if (c->a_col16) { cudaFree(c->a_col16); c->a_col16 = nullptr; }
   if (c->at_rowptr) { cudaFree(c->at_rowptr); c->at_rowptr = nullptr; }
   if (c->at_col) { cudaFree(c->at_col); c->at_col = nullptr; }
   if (c->at_val) { cudaFree(c->at_val); c->at_val = nullptr; }
@@ -592,6 +593,12 @@ __global__ void k_split(int64_t m, const double* __restrict__ v, float* __restri
   }
 }
 
+__global__ void k_narrow(int64_t m, const int32_t* __restrict__ col, uint16_t* __restrict__ col16) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+       k += (int64_t)gridDim.x * blockDim.x)
+    col16[k] = (uint16_t)col[k];
+}
+
 cudaError_t split_hilo(reach_ctx* c) {
   if (c->a_hi && c->a_lo) return cudaSuccess;
   cudaError_t e;
@@ -599,6 +606,11 @@ cudaError_t split_hilo(reach_ctx* c) {
   if ((e = dmalloc(&c->a_lo, c->m_q + 8)) != cudaSuccess) return e;
   const int64_t mm = c->m_q + 8;   // slack entries are zeros of a_val
   k_split<<<grid_for(c, (const void*)k_split, 256, mm), 256, 0, c->stream>>>(mm, c->a_val, c->a_hi, c->a_lo);
+  // 16-bit column indices when every S? index fits: 2 bytes less per entry in the sweeps
+  if (c->n_q <= 65536 && !c->a_col16) {
+    if ((e = dmalloc(&c->a_col16, c->m_q + 8)) != cudaSuccess) return e;
+    k_narrow<<<grid_for(c, (const void*)k_narrow, 256, mm), 256, 0, c->stream>>>(mm, c->a_col, c->a_col16);
+  }
   return cudaGetLastError();
 }
 

@@ -33,6 +33,7 @@ struct SolveState {
   int64_t bodies;       // loop bodies run (hard stop at max_bodies)
   int64_t max_bodies;
   unsigned long long slot[64];  // per-sweep max|dx| bit patterns (non-negative doubles)
+  unsigned rowctr[64];          // per-launch row counters of warp-per-row kernels (dynamic rows)
 };
 
 // BiCGStab scalars (§3.2 names: y = rho, a = alpha, w = omega) in device memory.
@@ -103,6 +104,7 @@ struct reach_ctx {
   double* a_val = nullptr;
   float* a_hi = nullptr;
   float* a_lo = nullptr;
+  uint16_t* a_col16 = nullptr;  // a_col narrowed to 16 bits when n? <= 65536 (mixed sweeps)
   double* d = nullptr;
   double* b = nullptr;
   float* d32 = nullptr;
@@ -122,6 +124,7 @@ struct reach_ctx {
   double* vs = nullptr;     // BiCGStab s
   double* vt = nullptr;     // BiCGStab t
   float* r32 = nullptr;     // mixed: residual
+  float* xf = nullptr;      // mixed: FP32 copy of x (lo-part products of the residual)
   float* dl[2] = {nullptr, nullptr};  // mixed: correction ping-pong
   double* xfull = nullptr;  // full-state x of the last successful solve
   bool have_x = false;
@@ -173,7 +176,7 @@ void launch_finalize_resid(cudaStream_t s, SolveState* st);
 // ---- shared host helpers (api.cu)
 int pick_group(int64_t rows, int64_t nnz);
 int grid_for(reach_ctx* c, const void* kernel, int threads, int64_t work_items);
-int grid_rows(reach_ctx* c, const void* kernel, int threads, int g, int64_t rows);
+int grid_rows(reach_ctx* c, const void* kernel, int threads, int g, int64_t rows, bool dynamic = false);
 bool set_err(reach_ctx* c, const std::string& msg);
 
 }  // namespace reach

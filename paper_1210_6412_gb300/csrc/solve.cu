@@ -20,6 +20,15 @@ constexpr int NT = 256;
 // start to four entries; the tail is scalar again.  Matrix data is streamed with
 // evict-first loads; the gathered vector goes through the read-only cache.
 
+// Column-index loads: int32, or uint16 when every column of the system fits (n? <= 65536).
+RDEV int ld_idx(const int32_t* p) { return __ldcs(p); }
+RDEV int ld_idx(const uint16_t* p) { return (int)__ldcs(reinterpret_cast<const unsigned short*>(p)); }
+RDEV int4 ld_idx4(const int32_t* p) { return __ldcs(reinterpret_cast<const int4*>(p)); }
+RDEV int4 ld_idx4(const uint16_t* p) {
+  const ushort4 u = __ldcs(reinterpret_cast<const ushort4*>(p));
+  return make_int4(u.x, u.y, u.z, u.w);
+}
+
 template <int G, bool V, typename XF>
 RDEV double dot64(int64_t lo, int64_t hi, int lane, const int32_t* __restrict__ ci,
                   const double* __restrict__ av, XF xf) {
@@ -46,35 +55,51 @@ RDEV double dot64(int64_t lo, int64_t hi, int lane, const int32_t* __restrict__ 
 }
 
 // FP32 values, FP32 accumulation (inner sweeps of the mixed method).
-template <int G, bool V>
-RDEV float dot32(int64_t lo, int64_t hi, int lane, const int32_t* __restrict__ ci,
+template <int G, bool V, typename IT = int32_t>
+RDEV float dot32(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
                  const float* __restrict__ av, const float* __restrict__ x) {
   float s = 0.0f;
   if constexpr (V) {
     int64_t a = (lo + 3) & ~int64_t(3);
     if (a > hi) a = hi;
     const int64_t e = a + ((hi - a) & ~int64_t(3));
-    if (lo + lane < a) s = fmaf(__ldcs(av + lo + lane), __ldg(x + __ldcs(ci + lo + lane)), s);
-    for (int64_t k = a + 4 * lane; k < e; k += 128) {
-      const int4 c4 = __ldcs(reinterpret_cast<const int4*>(ci + k));
+    if (lo + lane < a) s = fmaf(__ldcs(av + lo + lane), __ldg(x + ld_idx(ci + lo + lane)), s);
+    // two quads per lane per trip: both loads are in flight before either is used
+    float s2 = 0.0f;
+    for (int64_t k = a + 4 * lane; k < e; k += 256) {
+      const bool two = k + 128 < e;
+      const int4 c4 = ld_idx4(ci + k);
       const float4 v = __ldcs(reinterpret_cast<const float4*>(av + k));
+      int4 c4b = make_int4(0, 0, 0, 0);
+      float4 vb = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (two) {
+        c4b = ld_idx4(ci + k + 128);
+        vb = __ldcs(reinterpret_cast<const float4*>(av + k + 128));
+      }
       s = fmaf(v.x, __ldg(x + c4.x), s);
       s = fmaf(v.y, __ldg(x + c4.y), s);
       s = fmaf(v.z, __ldg(x + c4.z), s);
       s = fmaf(v.w, __ldg(x + c4.w), s);
+      s2 = fmaf(vb.x, __ldg(x + c4b.x), s2);
+      s2 = fmaf(vb.y, __ldg(x + c4b.y), s2);
+      s2 = fmaf(vb.z, __ldg(x + c4b.z), s2);
+      s2 = fmaf(vb.w, __ldg(x + c4b.w), s2);
     }
-    if (e + lane < hi) s = fmaf(__ldcs(av + e + lane), __ldg(x + __ldcs(ci + e + lane)), s);
+    s += s2;
+    if (e + lane < hi) s = fmaf(__ldcs(av + e + lane), __ldg(x + ld_idx(ci + e + lane)), s);
   } else {
-    for (int64_t k = lo + lane; k < hi; k += G) s = fmaf(__ldcs(av + k), __ldg(x + __ldcs(ci + k)), s);
+    for (int64_t k = lo + lane; k < hi; k += G) s = fmaf(__ldcs(av + k), __ldg(x + ld_idx(ci + k)), s);
   }
   return s;
 }
 
-// Values as FP32 hi + lo pairs widened to FP64, FP64 accumulation (residual step).
-template <int G, bool V>
-RDEV double dot_hilo(int64_t lo, int64_t hi, int lane, const int32_t* __restrict__ ci,
+// Residual step with values v = hi + lo (FP32 pair, v to about 2^-48 relative):
+// sum hi * x in FP64 (one FP64 FMA per entry) and sum lo * x in FP32 against an FP32
+// copy of x (lo is 2^-24 of hi, so FP32 keeps that term to about 2^-48 of the total).
+template <int G, bool V, typename IT = int32_t>
+RDEV double dot_hilo(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
                      const float* __restrict__ ah, const float* __restrict__ al,
-                     const double* __restrict__ x) {
+                     const double* __restrict__ x, const float* __restrict__ xf, float& sl) {
   double s = 0.0;
   if constexpr (V) {
     int64_t a = (lo + 3) & ~int64_t(3);
@@ -82,24 +107,35 @@ RDEV double dot_hilo(int64_t lo, int64_t hi, int lane, const int32_t* __restrict
     const int64_t e = a + ((hi - a) & ~int64_t(3));
     if (lo + lane < a) {
       const int64_t k = lo + lane;
-      s = fma((double)__ldcs(ah + k) + (double)__ldcs(al + k), __ldg(x + __ldcs(ci + k)), s);
+      const int c = ld_idx(ci + k);
+      s = fma(widen(__ldcs(ah + k)), __ldg(x + c), s);
+      sl = fmaf(__ldcs(al + k), __ldg(xf + c), sl);
     }
     for (int64_t k = a + 4 * lane; k < e; k += 128) {
-      const int4 c4 = __ldcs(reinterpret_cast<const int4*>(ci + k));
+      const int4 c4 = ld_idx4(ci + k);
       const float4 h = __ldcs(reinterpret_cast<const float4*>(ah + k));
       const float4 l = __ldcs(reinterpret_cast<const float4*>(al + k));
-      s = fma((double)h.x + (double)l.x, __ldg(x + c4.x), s);
-      s = fma((double)h.y + (double)l.y, __ldg(x + c4.y), s);
-      s = fma((double)h.z + (double)l.z, __ldg(x + c4.z), s);
-      s = fma((double)h.w + (double)l.w, __ldg(x + c4.w), s);
+      s = fma(widen(h.x), __ldg(x + c4.x), s);
+      s = fma(widen(h.y), __ldg(x + c4.y), s);
+      s = fma(widen(h.z), __ldg(x + c4.z), s);
+      s = fma(widen(h.w), __ldg(x + c4.w), s);
+      sl = fmaf(l.x, __ldg(xf + c4.x), sl);
+      sl = fmaf(l.y, __ldg(xf + c4.y), sl);
+      sl = fmaf(l.z, __ldg(xf + c4.z), sl);
+      sl = fmaf(l.w, __ldg(xf + c4.w), sl);
     }
     if (e + lane < hi) {
       const int64_t k = e + lane;
-      s = fma((double)__ldcs(ah + k) + (double)__ldcs(al + k), __ldg(x + __ldcs(ci + k)), s);
+      const int c = ld_idx(ci + k);
+      s = fma(widen(__ldcs(ah + k)), __ldg(x + c), s);
+      sl = fmaf(__ldcs(al + k), __ldg(xf + c), sl);
     }
   } else {
-    for (int64_t k = lo + lane; k < hi; k += G)
-      s = fma((double)__ldcs(ah + k) + (double)__ldcs(al + k), __ldg(x + __ldcs(ci + k)), s);
+    for (int64_t k = lo + lane; k < hi; k += G) {
+      const int c = ld_idx(ci + k);
+      s = fma(widen(__ldcs(ah + k)), __ldg(x + c), s);
+      sl = fmaf(__ldcs(al + k), __ldg(xf + c), sl);
+    }
   }
   return s;
 }
@@ -181,11 +217,11 @@ __global__ void __launch_bounds__(NT) k_jacobi64(int64_t nq, const int64_t* __re
                                                  const double* __restrict__ b,
                                                  const double* __restrict__ d,
                                                  const double* __restrict__ x,
-                                                 double* __restrict__ xn, unsigned long long* slot) {
+                                                 double* __restrict__ xn, unsigned long long* slot, unsigned* ctr) {
   RowGroups rg = RowGroups::make<G>();
   double mx = 0.0;
   auto xf = [x](int32_t j) { return __ldg(x + j); };
-  for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
+  for (int64_t i = row_begin<G>(rg, ctr); warp_has_row<G>(i, nq); i = row_next<G>(rg, ctr, i)) {
     double s = 0.0;
     if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, av, xf);
     s = group_sum<G>(s);
@@ -231,7 +267,10 @@ __global__ void k_check(SolveState* st, int slot_idx, int sweeps, int reset_n) {
     st->done = 1;
     st->status = REACH_ENOTCONV;
   }
-  for (int j = 0; j < reset_n; ++j) st->slot[j] = 0ull;
+  for (int j = 0; j < reset_n; ++j) {
+    st->slot[j] = 0ull;
+    st->rowctr[j] = 0u;
+  }
 }
 
 __global__ void k_loop_ctl(SolveState* st, cudaGraphConditionalHandle h, int use_cond) {
@@ -254,26 +293,29 @@ __global__ void k_finalize_resid(SolveState* st) {
 // (I - A) delta = r; then x += delta in FP64.  max|r_i / d_i| is exactly the
 // max|x' - x| of an FP64 Jacobi sweep from x, so the stopping rule matches.
 
-template <int G, bool V>
+template <int G, bool V, typename IT>
 __global__ void __launch_bounds__(NT) k_resid_hilo(int64_t nq, const int64_t* __restrict__ rp,
-                                                   const int32_t* __restrict__ ci,
+                                                   const IT* __restrict__ ci,
                                                    const float* __restrict__ ah,
                                                    const float* __restrict__ al,
                                                    const double* __restrict__ b,
                                                    const double* __restrict__ d,
                                                    const double* __restrict__ x,
+                                                   const float* __restrict__ xf,
                                                    float* __restrict__ r32, float* __restrict__ dl0,
-                                                   SolveState* st, int slot_idx) {
+                                                   SolveState* st, int slot_idx, unsigned* ctr) {
   if (st->done) return;
   RowGroups rg = RowGroups::make<G>();
   double mx = 0.0;
-  for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
+  for (int64_t i = row_begin<G>(rg, ctr); warp_has_row<G>(i, nq); i = row_next<G>(rg, ctr, i)) {
     double s = 0.0;
-    if (i < nq) s = dot_hilo<G, V>(rp[i], rp[i + 1], rg.lane, ci, ah, al, x);
+    float sl = 0.0f;
+    if (i < nq) s = dot_hilo<G, V, IT>(rp[i], rp[i + 1], rg.lane, ci, ah, al, x, xf, sl);
     s = group_sum<G>(s);
+    sl = group_sum<G>(sl);
     if (i < nq && rg.lane == 0) {
       const double di = d[i];
-      const double r = b[i] + s - di * x[i];
+      const double r = b[i] + (s + (double)sl) - di * x[i];
       const double q = r / di;
       r32[i] = __double2float_rn(r);
       dl0[i] = __double2float_rn(q);
@@ -301,30 +343,36 @@ __global__ void k_check_mixed(SolveState* st, int slot_idx, int k) {
   }
 }
 
-template <int G, bool V>
+template <int G, bool V, typename IT>
 __global__ void __launch_bounds__(NT) k_sweep32(int64_t nq, const int64_t* __restrict__ rp,
-                                                const int32_t* __restrict__ ci,
+                                                const IT* __restrict__ ci,
                                                 const float* __restrict__ ah,
                                                 const float* __restrict__ r32,
                                                 const float* __restrict__ d32,
                                                 const float* __restrict__ din,
-                                                float* __restrict__ dout, const SolveState* st) {
+                                                float* __restrict__ dout, const SolveState* st, unsigned* ctr) {
   if (st->done) return;
   RowGroups rg = RowGroups::make<G>();
-  for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
+  for (int64_t i = row_begin<G>(rg, ctr); warp_has_row<G>(i, nq); i = row_next<G>(rg, ctr, i)) {
     float s = 0.0f;
-    if (i < nq) s = dot32<G, V>(rp[i], rp[i + 1], rg.lane, ci, ah, din);
+    if (i < nq) s = dot32<G, V, IT>(rp[i], rp[i + 1], rg.lane, ci, ah, din);
     s = group_sum<G>(s);
     if (i < nq && rg.lane == 0) dout[i] = (r32[i] + s) / d32[i];
   }
 }
 
-__global__ void k_apply(int64_t nq, double* __restrict__ x, const float* __restrict__ dl,
-                        const SolveState* st) {
+// x += delta in FP64, and the FP32 copy of x used by the next residual step.
+// With dl == nullptr only the copy is refreshed (start of a solve).
+__global__ void k_apply(int64_t nq, double* __restrict__ x, float* __restrict__ xf,
+                        const float* __restrict__ dl, SolveState* st, int reset_n) {
   if (st->done) return;
+  if (blockIdx.x == 0 && threadIdx.x < reset_n) st->rowctr[threadIdx.x] = 0u;  // counters of this body
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
-       i += (int64_t)gridDim.x * blockDim.x)
-    x[i] += (double)dl[i];
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = dl ? x[i] + (double)dl[i] : x[i];
+    x[i] = v;
+    xf[i] = __double2float_rn(v);
+  }
 }
 
 // ------------------------------------------------------------------ BiCGStab (§3.2)
@@ -386,11 +434,15 @@ __global__ void __launch_bounds__(NT) k_bi_init(int64_t nq, const int64_t* __res
 // residual: q = r, p = r, v = 0 (y = r.r was set by the CTA that detected it).
 __global__ void k_bi_p(int64_t nq, const double* __restrict__ r, double* __restrict__ p,
                        double* __restrict__ v, double* __restrict__ q, BiState* bi,
-                       const SolveState* st) {
+                       SolveState* st) {
   if (st->done) return;
   const double beta = bi->beta, w = bi->w;
   const int rs = bi->restart;
-  if (blockIdx.x == 0 && threadIdx.x == 0) bi->skip = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    bi->skip = 0;
+    st->rowctr[0] = 0u;   // row counters of k_bi_v and k_bi_t
+    st->rowctr[1] = 0u;
+  }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double ri = r[i];
@@ -425,12 +477,12 @@ __global__ void __launch_bounds__(NT) k_bi_v(int64_t nq, const int64_t* __restri
                                              const double* __restrict__ p,
                                              const double* __restrict__ q, double* __restrict__ v,
                                              double* part, unsigned* ticket, BiState* bi,
-                                             SolveState* st) {
+                                             SolveState* st, unsigned* ctr) {
   if (st->done) return;
   RowGroups rg = RowGroups::make<G>();
   double acc[1] = {0.0};
   auto pf = [p](int32_t j) { return __ldg(p + j); };
-  for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
+  for (int64_t i = row_begin<G>(rg, ctr); warp_has_row<G>(i, nq); i = row_next<G>(rg, ctr, i)) {
     double s = 0.0;
     if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, av, pf);
     s = group_sum<G>(s);
@@ -461,13 +513,13 @@ __global__ void __launch_bounds__(NT) k_bi_t(int64_t nq, const int64_t* __restri
                                              const double* __restrict__ v,
                                              double* __restrict__ s_out, double* __restrict__ t,
                                              double* part, unsigned* ticket, BiState* bi,
-                                             SolveState* st) {
+                                             SolveState* st, unsigned* ctr) {
   if (st->done || bi->skip) return;
   const double a = bi->a;
   RowGroups rg = RowGroups::make<G>();
   double acc[3] = {0.0, 0.0, 0.0};
   auto sf = [r, v, a](int32_t j) { return __ldg(r + j) - a * __ldg(v + j); };
-  for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
+  for (int64_t i = row_begin<G>(rg, ctr); warp_has_row<G>(i, nq); i = row_next<G>(rg, ctr, i)) {
     double s = 0.0;
     if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, av, sf);
     s = group_sum<G>(s);
@@ -589,9 +641,9 @@ struct Sys {
 
 template <int G, bool V>
 static void l_jacobi(reach_ctx* c, const Sys& y, const double* x, double* xn, unsigned long long* slot,
-                     cudaStream_t s) {
-  const int grid = grid_rows(c, (const void*)k_jacobi64<G, V>, NT, G, y.nq);
-  k_jacobi64<G, V><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, c->d, x, xn, slot);
+                     cudaStream_t s, unsigned* ctr = nullptr) {
+  const int grid = grid_rows(c, (const void*)k_jacobi64<G, V>, NT, G, y.nq, G == 32 && ctr);
+  k_jacobi64<G, V><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, c->d, x, xn, slot, G == 32 ? ctr : nullptr);
 }
 
 template <int G, bool V>
@@ -601,17 +653,31 @@ static void l_resid(reach_ctx* c, const Sys& y, const double* x, cudaStream_t s)
 }
 
 template <int G, bool V>
-static void l_resid_hilo(reach_ctx* c, int slot, cudaStream_t s) {
-  const int grid = grid_rows(c, (const void*)k_resid_hilo<G, V>, NT, G, c->n_q);
-  k_resid_hilo<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->a_lo, c->b, c->d,
-                                         c->x, c->r32, c->dl[1], c->st, slot);
+static void l_resid_hilo(reach_ctx* c, int slot, cudaStream_t s, unsigned* ctr = nullptr) {
+  unsigned* cr = G == 32 ? ctr : nullptr;
+  if (V && c->a_col16) {
+    const int grid = grid_rows(c, (const void*)k_resid_hilo<G, V, uint16_t>, NT, G, c->n_q, cr != nullptr);
+    k_resid_hilo<G, V, uint16_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col16, c->a_hi, c->a_lo, c->b,
+                                                     c->d, c->x, c->xf, c->r32, c->dl[1], c->st, slot, cr);
+  } else {
+    const int grid = grid_rows(c, (const void*)k_resid_hilo<G, V, int32_t>, NT, G, c->n_q, cr != nullptr);
+    k_resid_hilo<G, V, int32_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->a_lo, c->b,
+                                                    c->d, c->x, c->xf, c->r32, c->dl[1], c->st, slot, cr);
+  }
 }
 
 template <int G, bool V>
-static void l_sweep32(reach_ctx* c, const float* din, float* dout, cudaStream_t s) {
-  const int grid = grid_rows(c, (const void*)k_sweep32<G, V>, NT, G, c->n_q);
-  k_sweep32<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->r32, c->d32, din, dout,
-                                      c->st);
+static void l_sweep32(reach_ctx* c, const float* din, float* dout, cudaStream_t s, unsigned* ctr = nullptr) {
+  unsigned* cr = G == 32 ? ctr : nullptr;
+  if (V && c->a_col16) {
+    const int grid = grid_rows(c, (const void*)k_sweep32<G, V, uint16_t>, NT, G, c->n_q, cr != nullptr);
+    k_sweep32<G, V, uint16_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col16, c->a_hi, c->r32, c->d32,
+                                                  din, dout, c->st, cr);
+  } else {
+    const int grid = grid_rows(c, (const void*)k_sweep32<G, V, int32_t>, NT, G, c->n_q, cr != nullptr);
+    k_sweep32<G, V, int32_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->r32, c->d32,
+                                                 din, dout, c->st, cr);
+  }
 }
 
 template <int G, bool V>
@@ -623,16 +689,18 @@ static void l_bi_init(reach_ctx* c, cudaStream_t s) {
 
 template <int G, bool V>
 static void l_bi_v(reach_ctx* c, cudaStream_t s) {
-  const int grid = grid_rows(c, (const void*)k_bi_v<G, V>, NT, G, c->n_q);
+  unsigned* cr = G == 32 ? &c->st->rowctr[0] : nullptr;
+  const int grid = grid_rows(c, (const void*)k_bi_v<G, V>, NT, G, c->n_q, cr != nullptr);
   k_bi_v<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_val, c->d, c->vp, c->vq, c->vv,
-                                   c->part, c->ticket, c->bi, c->st);
+                                   c->part, c->ticket, c->bi, c->st, cr);
 }
 
 template <int G, bool V>
 static void l_bi_t(reach_ctx* c, cudaStream_t s) {
-  const int grid = grid_rows(c, (const void*)k_bi_t<G, V>, NT, G, c->n_q);
+  unsigned* cr = G == 32 ? &c->st->rowctr[1] : nullptr;
+  const int grid = grid_rows(c, (const void*)k_bi_t<G, V>, NT, G, c->n_q, cr != nullptr);
   k_bi_t<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_val, c->d, c->vr, c->vv, c->vs,
-                                   c->vt, c->part, c->ticket, c->bi, c->st);
+                                   c->vt, c->part, c->ticket, c->bi, c->st, cr);
 }
 
 static int ew_grid(reach_ctx* c, const void* k, int64_t n) { return grid_for(c, k, NT, n); }
@@ -709,7 +777,7 @@ cudaError_t solve_jacobi64(reach_ctx* c, const double* x0q, bool transposed) {
                              for (int j = 0; j < k; ++j) {
                                const double* xi = (j & 1) ? xb : xa;
                                double* xo = (j & 1) ? xa : xb;
-                               LAY_DISPATCH(L, l_jacobi, c, y, xi, xo, &c->st->slot[j], cs);
+                               LAY_DISPATCH(L, l_jacobi, c, y, xi, xo, &c->st->slot[j], cs, &c->st->rowctr[j]);
                              }
                              k_check<<<1, 1, 0, cs>>>(c->st, k - 1, k, k);
                            });
@@ -726,18 +794,19 @@ cudaError_t solve_mixed(reach_ctx* c, const double* x0q) {
   if (e != cudaSuccess) return e;
   if (x0q) cudaMemcpyAsync(c->x, x0q, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
   else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
+  k_apply<<<ew_grid(c, (const void*)k_apply, nq), NT, 0, s>>>(nq, c->x, c->xf, nullptr, c->st, 0);
   const Lay L = layout(c, nq, c->m_q, REACH_JACOBI_MIXED);
   const int k = c->tune.k;
   e = run_loop(c, c->g_exec[1], c->g_key[1], shape_key(c, L, k), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
-    LAY_DISPATCH(L, l_resid_hilo, c, 0, cs);
+    LAY_DISPATCH(L, l_resid_hilo, c, 0, cs, &c->st->rowctr[0]);
     k_check_mixed<<<1, 1, 0, cs>>>(c->st, 0, k);
     // k - 1 FP32 sweeps: dl[1] -> dl[0] -> dl[1] ... ; k even, so the last lands in dl[0]
     for (int j = 1; j < k; ++j) {
       const float* din = (j & 1) ? c->dl[1] : c->dl[0];
       float* dout = (j & 1) ? c->dl[0] : c->dl[1];
-      LAY_DISPATCH(L, l_sweep32, c, din, dout, cs);
+      LAY_DISPATCH(L, l_sweep32, c, din, dout, cs, &c->st->rowctr[j]);
     }
-    k_apply<<<ew_grid(c, (const void*)k_apply, nq), NT, 0, cs>>>(nq, c->x, c->dl[0], c->st);
+    k_apply<<<ew_grid(c, (const void*)k_apply, nq), NT, 0, cs>>>(nq, c->x, c->xf, c->dl[0], c->st, k);
   });
   if (e != cudaSuccess) return e;
   Sys y{nq, c->a_rowptr, c->a_col, c->a_val, c->b};
