@@ -187,6 +187,30 @@ reach_status reach_batch_solve(reach_batch* b, double eps, int64_t max_iter, int
 /* Release the batch.  NULL is a no-op. */
 void reach_batch_destroy(reach_batch* b);
 
+/* ---- Allocation-free Jacobi solve ----------------------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code inside a host application that owns all device memory through its
+ * own pool, code on a path where cudaMalloc/cudaFree would stall the device, or code
+ * that must not hit out-of-memory once running.  It allocates nothing.  The caller
+ * passes an already extracted system over S? in device memory (A off-diagonal CSR with
+ * rowptr int64[n_q+1] and col int32 in [0, n_q), val float64; b and d = 1 - A_ii as
+ * float64[n_q]) and x float64[n_q] (start vector in, solution out).  It runs Jacobi
+ * sweeps x <- (b + A x) / d and checks max|x' - x| < eps every check_every (even, >= 2)
+ * sweeps, at most max_iter sweeps; *iters_out and *delta_out (host, may be NULL)
+ * receive the sweep count and the last max|x' - x|.
+ * Scratch (the second Jacobi vector) lives in a fixed device array inside the library,
+ * sized for n_q <= 524288 (4 MiB + 4 KiB, held on every device that loads the library
+ * until the process exits); larger n_q returns REACH_EINVAL.  The first call on a
+ * device looks up that array's device address; make that first call before any stream
+ * capture.  Every call on a device shares the array, so calls that overlap on the GPU
+ * (other streams or threads) race: serialise them.  Returns REACH_ENOTCONV when
+ * max_iter runs out.  Synchronises `stream` after every check. */
+reach_status reach_jacobi_solve_noalloc(int64_t n_q, const int64_t* rowptr, const int32_t* col,
+                                        const double* val, const double* b, const double* d,
+                                        double eps, int64_t max_iter, int32_t check_every,
+                                        double* x, int64_t* iters_out, double* delta_out,
+                                        void* stream);
+
 /* Last error message of ctx (NULL: of the calling thread's last context-free call). */
 const char* reach_last_error(const reach_ctx* ctx);
 

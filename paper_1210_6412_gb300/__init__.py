@@ -80,6 +80,8 @@ _SIGS = {
     "reach_batch_destroy": (None, [_P]),
     "reach_autotune": (_I32, [_P, _I32, C.POINTER(_I32), C.POINTER(_D), C.POINTER(_I32)]),
     "reach_system_create": (_I32, [C.POINTER(_P), _I64, _I64, _P, _P, _P, _P, _I32, _P]),
+    "reach_jacobi_solve_noalloc": (_I32, [_I64, _P, _P, _P, _P, _P, _D, _I64, _I32, _P,
+                                          C.POINTER(_I64), C.POINTER(_D), _P]),
 }
 
 
