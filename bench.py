@@ -44,6 +44,11 @@ K_REFINE = 16
 # DRAM traffic per FP64 Jacobi sweep from an ncu capture of the same kernel
 # (profiles/jacobi64_dense32768.md); None until captured for the current kernel.
 NCU_TRAFFIC_BYTES = None
+NCU_TRAFFIC_SWEEP32_BYTES = None
+# FP64 peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA per clock (ncu's
+# roofline reports 4 FP64 flop/clk/SM) x 2 flop x 2.07 GHz; matches the 1.25 TFLOP/s nominal.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_PEAK_KIND = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"
 
 
 def peaks():
@@ -187,6 +192,21 @@ def run_reference(args):
     return 0
 
 
+def kernel_times(R, n, d_in, stream, launches=20):
+    """Per-launch device time of the four solver kernels on the bench system."""
+    out = {}
+    ctx = R.reach_create(n, *d_in, stream=stream.cuda_stream)
+    try:
+        R.reach_precompute(ctx, R.REACH_PROB0_ONLY)
+        for meth in ("jacobi", "mixed", "bicgstab"):
+            R.reach_autotune(ctx, meth)        # the mappings the timed solves used
+        for k in ("jacobi64", "sweep32", "resid_hilo", "bicgstab_spmv"):
+            out[k] = R.reach_time_kernel(ctx, k, launches)
+    finally:
+        R.reach_destroy(ctx)
+    return out
+
+
 def launches_per_step(infos, k):
     """Kernels of this library launched in one step (counted from the loop structure)."""
     j, mx, b = infos["jacobi"], infos["mixed"], infos["bicgstab"]
@@ -201,6 +221,7 @@ def launches_per_step(infos, k):
 def run_ours(args):
     import torch
     import paper_1210_6412_gb300 as R
+    from paper_1210_6412_gb300 import replicas
 
     ws, rank, local = dist_init()
     dev = torch.device("cuda", local)
@@ -219,6 +240,8 @@ def run_ours(args):
         try:
             R.reach_precompute(ctx, R.REACH_PROB0_ONLY)
             for meth in ("jacobi", "mixed", "bicgstab"):
+                # row mapping from the autotuner (measured once per system shape, then cached)
+                R.reach_autotune(ctx, meth)
                 _, infos[meth] = R.reach_solve(ctx, n, meth, eps=EPS[meth], max_iter=200_000,
                                                refine_k=K_REFINE, out=outputs[meth])
         finally:
@@ -228,11 +251,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         infos = step(d_in, outs)
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
+    barrier = replicas.barrier
     barrier()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -246,11 +265,7 @@ def run_ours(args):
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
     clocks = clk.summary()
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(ms, dev)
     infos = all_infos[-1]
     errs = {k: float(torch.max(torch.abs(outs[k] - 1.0)).item()) for k in outs}
 
@@ -265,30 +280,51 @@ def run_ours(args):
     d2h = 3 * n * 8
 
     jac = infos["jacobi"]
+    nq, mq = jac["n_q"], jac["m_q"]
     sweep_ms = jac["ms_solve"] / max(jac["iters"], 1)
-    alg_bytes = jac["m_q"] * 12 + jac["n_q"] * 40
-    achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
-    peak, peak_kind = peaks()
+    alg_bytes = mq * 12 + nq * 40
+    peak_hbm, peak_kind = peaks()
+    # per-kernel device times, measured live on the context stream with CUDA events
+    kern = kernel_times(R, n, d_in, stream)
+    kbytes = {"jacobi64": mq * 12 + nq * 40, "sweep32": mq * (6 if nq <= 65536 else 8) + nq * 24,
+              "resid_hilo": mq * (10 if nq <= 65536 else 12) + nq * 40, "bicgstab_spmv": mq * 12 + nq * 40}
+    kernels = {}
+    for k, t in kern.items():
+        gbs = kbytes[k] / (t * 1e-3) / 1e9
+        kernels[k] = {"ms": t, "alg_bytes": kbytes[k], "alg_GBps": gbs, "hbm_frac": gbs / peak_hbm}
+        if k != "sweep32":
+            tf = 2.0 * mq / (t * 1e-3) / 1e12
+            kernels[k].update({"fp64_TFLOPs": tf, "fp64_frac": tf / FP64_PEAK_TFLOPS})
     methods = {}
     for k, inf in infos.items():
         methods[k] = {"ms": inf["ms_solve"], "iters": inf["iters"], "max_err": errs[k],
                       "resid_inf": inf["resid_inf"], "alg_GBps": inf["bytes_moved"] / (inf["ms_solve"] * 1e6),
                       "refinements": inf["refinements"]}
+    fp64_tf = 2.0 * mq / (sweep_ms * 1e-3) / 1e12
+    hbm_gbs = alg_bytes / (sweep_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "nnz": m, "n_q": jac["n_q"], "nnz_q": jac["m_q"],
+        "config": {"workload": WORKLOAD, "n": n, "nnz": m, "n_q": nq, "nnz_q": mq,
                    "refine_k": K_REFINE, "l2": "inputs (1.3 GB) larger than L2; no flush",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "methods": methods,
         "precompute_ms": jac["ms_precompute"],
         "max_err_all": max(errs.values()),
-        "roofline": {"bound": "hbm", "kernel": "k_jacobi64 (FP64 Jacobi sweep)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": f"{peak_kind} copy bandwidth",
-                     "traffic": NCU_TRAFFIC_BYTES, "alg_bytes_per_launch": alg_bytes,
-                     "avg_launch_ms": sweep_ms},
+        # the dominant kernel (FP64 Jacobi sweep) is bound by the FP64 pipe, not HBM
+        "roofline": {"bound": "alu", "kernel": "k_jacobi64 (FP64 Jacobi sweep)",
+                     "achieved": fp64_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": fp64_tf / FP64_PEAK_TFLOPS, "peak_kind": FP64_PEAK_KIND,
+                     "traffic": NCU_TRAFFIC_BYTES, "alg_flops_per_launch": 2 * mq,
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sweep_ms,
+                     "hbm_GBps": hbm_gbs, "hbm_frac": hbm_gbs / peak_hbm,
+                     "hbm_peak": peak_hbm, "hbm_peak_kind": f"{peak_kind} copy bandwidth"},
+        "spmv_hbm": {"kernel": "k_sweep32 (FP32 sweep of the mixed method)",
+                     "achieved": kernels.get("sweep32", {}).get("alg_GBps"), "peak": peak_hbm,
+                     "unit": "GB/s", "frac": kernels.get("sweep32", {}).get("hbm_frac"),
+                     "traffic": NCU_TRAFFIC_SWEEP32_BYTES},
+        "kernels": kernels,
         "e2e": {"value": statistics.median(e_ms), "unit": "ms", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step(infos, K_REFINE) * args.steps,

@@ -135,6 +135,14 @@ reach_status reach_solve(reach_ctx* ctx, int32_t method, double eps, int64_t max
 reach_status reach_autotune(reach_ctx* ctx, int32_t method, int32_t* lanes, double* sweep_ms,
                             int32_t* check_every);
 
+/* Average device time, in ms, of `launches` (1..1000) back-to-back launches of one
+ * solver kernel on the context stream, in the layout the solves use, measured with
+ * CUDA events on that stream after one warm-up launch: kernel 0 = FP64 Jacobi sweep
+ * (§3.1), 1 = FP32 sweep of the mixed method, 2 = its FP64 residual step, 3 = the
+ * BiCGStab product v = (I - A) p (§3.2).  For roofline figures (bytes or flops of one
+ * launch over this time).  Overwrites solve workspace: solve again before reach_grad. */
+reach_status reach_time_kernel(reach_ctx* ctx, int32_t kernel, int32_t launches, double* avg_ms);
+
 /* Gradient of x_init with respect to every stored entry of P, in input order:
  * grad[k] = y_s * x_{col[k]} for an entry of row s in S?, else 0, where
  * (I - A)^T y = e_init is solved by Jacobi on the transposed system (FP64, stop at

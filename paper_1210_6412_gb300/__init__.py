@@ -80,6 +80,7 @@ _SIGS = {
     "reach_batch_destroy": (None, [_P]),
     "reach_autotune": (_I32, [_P, _I32, C.POINTER(_I32), C.POINTER(_D), C.POINTER(_I32)]),
     "reach_system_create": (_I32, [C.POINTER(_P), _I64, _I64, _P, _P, _P, _P, _I32, _P]),
+    "reach_time_kernel": (_I32, [_P, _I32, _I32, C.POINTER(_D)]),
     "reach_jacobi_solve_noalloc": (_I32, [_I64, _P, _P, _P, _P, _P, _D, _I64, _I32, _P,
                                           C.POINTER(_I64), C.POINTER(_D), _P]),
 }
@@ -270,6 +271,17 @@ def reach_autotune(ctx, method=REACH_JACOBI_FP64):
     lanes, ms, k = C.c_int32(0), C.c_double(0.0), C.c_int32(0)
     _check(lib().reach_autotune(ctx, method, C.byref(lanes), C.byref(ms), C.byref(k)), ctx)
     return {"lanes": lanes.value, "sweep_ms": ms.value, "check_every": k.value}
+
+
+KERNELS = {"jacobi64": 0, "sweep32": 1, "resid_hilo": 2, "bicgstab_spmv": 3}
+
+
+def reach_time_kernel(ctx, kernel, launches=20):
+    """Average ms per launch of one solver kernel (CUDA events on the context stream)."""
+    k = KERNELS.get(kernel, kernel) if isinstance(kernel, str) else int(kernel)
+    ms = C.c_double(0.0)
+    _check(lib().reach_time_kernel(ctx, k, int(launches), C.byref(ms)), ctx)
+    return ms.value
 
 
 def reach_destroy(ctx):

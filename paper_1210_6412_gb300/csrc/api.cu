@@ -467,6 +467,19 @@ reach_status reach_autotune(reach_ctx* c, int32_t method, int32_t* lanes, double
   return REACH_OK;
 }
 
+reach_status reach_time_kernel(reach_ctx* c, int32_t kernel, int32_t launches, double* avg_ms) {
+  if (!c) return fail(nullptr, REACH_EINVAL, "reach_time_kernel: NULL context");
+  if (!c->have_classes) return fail(c, REACH_ESTATE, "reach_time_kernel: call reach_precompute first");
+  if (kernel < 0 || kernel > 3 || launches < 1 || launches > 1000 || !avg_ms)
+    return fail(c, REACH_EINVAL, "reach_time_kernel: kernel in [0, 3], launches in [1, 1000]");
+  float ms = 0.f;
+  cudaError_t e = time_kernel(c, kernel, launches, &ms);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reach_time_kernel");
+  *avg_ms = ms;
+  c->have_x = false;   // the launches overwrote solve workspace
+  return REACH_OK;
+}
+
 reach_status reach_grad(reach_ctx* c, int64_t init, double eps, int64_t max_iter, double* grad,
                         int32_t flags, reach_info* info) {
   if (!c) return fail(nullptr, REACH_EINVAL, "reach_grad: NULL context");

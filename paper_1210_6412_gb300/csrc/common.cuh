@@ -50,18 +50,18 @@ RDEV void block_reduce(double (&v)[NV], double* sh) {
   __syncthreads();
 }
 
-// FP32 -> FP64 widening with integer operations.  On GB300 the conversion
-// instruction shares the (narrow) FP64 pipe, while the bit rearrangement below runs
-// on the integer units; both are exact.  Zero, subnormal, infinite and NaN inputs
-// (never produced by the hi/lo split of a probability except zero padding) take the
-// hardware conversion.
+// FP32 -> FP64 widening with integer operations only.  On GB300 the conversion
+// instruction shares the (narrow) FP64 pipe, while this bit rearrangement runs on the
+// integer units.  Exact for normal numbers, zero, infinities and NaN; FP32 subnormals
+// (below 1.2e-38) become signed zero.  No branch: a branch to the hardware conversion
+// would be if-converted and executed for every element.
 RDEV double widen(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const uint64_t d = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
-                     ((uint64_t)(u & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)d);
+  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  const uint64_t ex = e == 0u ? 0ull : (e == 0xffu ? 0x7ffull : (uint64_t)(e + 896u));
+  const uint64_t mant = e == 0u ? 0ull : (uint64_t)(u & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(sign | (ex << 52) | mant));
 }
 
 // Max of non-negative doubles through the integer order of their bit patterns.

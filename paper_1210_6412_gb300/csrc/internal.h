@@ -56,6 +56,7 @@ struct Tuning {
   int gm[3] = {0, 0, 0};  // autotuned lanes-per-row code per method (0 = none)
   int k = 16;           // sweeps between convergence checks / refinement period
   int k_auto = 0;       // autotuned sweeps between checks for FP64 Jacobi (0 = none)
+  int sweep_u = 2;      // quads per lane per trip of the vector FP32 sweep (2, or 4 for layout code 66)
   int cta = 256;        // threads per CTA
 };
 
@@ -171,6 +172,7 @@ cudaError_t run_loop(reach_ctx* c, cudaGraphExec_t& exec, int64_t& exec_key, int
                      const std::function<void(cudaStream_t, cudaGraphConditionalHandle, int)>& body);
 void launch_check_mixed(cudaStream_t s, SolveState* st, int slot, int k);
 cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms);
+cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms);
 void launch_finalize_resid(cudaStream_t s, SolveState* st);
 
 // ---- shared host helpers (api.cu)

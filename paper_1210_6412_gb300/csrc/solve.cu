@@ -5,7 +5,11 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstring>
 #include <functional>
+#include <mutex>
+#include <string>
+#include <unordered_map>
 
 #include "common.cuh"
 #include "internal.h"
@@ -38,15 +42,19 @@ RDEV double dot64(int64_t lo, int64_t hi, int lane, const int32_t* __restrict__ 
     if (a > hi) a = hi;
     const int64_t e = a + ((hi - a) & ~int64_t(3));
     if (lo + lane < a) s = fma(__ldcs(av + lo + lane), xf(__ldcs(ci + lo + lane)), s);
+    // four independent FP64 accumulators: the narrow FP64 pipe of GB300 has a long
+    // latency, and one dependent chain per lane would leave it waiting
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
     for (int64_t k = a + 4 * lane; k < e; k += 128) {
       const int4 c4 = __ldcs(reinterpret_cast<const int4*>(ci + k));
       const double2 v0 = __ldcs(reinterpret_cast<const double2*>(av + k));
       const double2 v1 = __ldcs(reinterpret_cast<const double2*>(av + k + 2));
       s = fma(v0.x, xf(c4.x), s);
-      s = fma(v0.y, xf(c4.y), s);
-      s = fma(v1.x, xf(c4.z), s);
-      s = fma(v1.y, xf(c4.w), s);
+      s1 = fma(v0.y, xf(c4.y), s1);
+      s2 = fma(v1.x, xf(c4.z), s2);
+      s3 = fma(v1.y, xf(c4.w), s3);
     }
+    s = (s + s1) + (s2 + s3);
     if (e + lane < hi) s = fma(__ldcs(av + e + lane), xf(__ldcs(ci + e + lane)), s);
   } else {
     for (int64_t k = lo + lane; k < hi; k += G) s = fma(__ldcs(av + k), xf(__ldcs(ci + k)), s);
@@ -55,7 +63,7 @@ RDEV double dot64(int64_t lo, int64_t hi, int lane, const int32_t* __restrict__ 
 }
 
 // FP32 values, FP32 accumulation (inner sweeps of the mixed method).
-template <int G, bool V, typename IT = int32_t>
+template <int G, bool V, typename IT = int32_t, int U = 2>
 RDEV float dot32(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
                  const float* __restrict__ av, const float* __restrict__ x) {
   float s = 0.0f;
@@ -64,28 +72,34 @@ RDEV float dot32(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
     if (a > hi) a = hi;
     const int64_t e = a + ((hi - a) & ~int64_t(3));
     if (lo + lane < a) s = fmaf(__ldcs(av + lo + lane), __ldg(x + ld_idx(ci + lo + lane)), s);
-    // two quads per lane per trip: both loads are in flight before either is used
-    float s2 = 0.0f;
-    for (int64_t k = a + 4 * lane; k < e; k += 256) {
-      const bool two = k + 128 < e;
-      const int4 c4 = ld_idx4(ci + k);
-      const float4 v = __ldcs(reinterpret_cast<const float4*>(av + k));
-      int4 c4b = make_int4(0, 0, 0, 0);
-      float4 vb = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (two) {
-        c4b = ld_idx4(ci + k + 128);
-        vb = __ldcs(reinterpret_cast<const float4*>(av + k + 128));
+    // U quads per lane per trip: all U loads are in flight before any is used
+    float acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = 0.0f;
+    for (int64_t k = a + 4 * lane; k < e; k += 128 * U) {
+      int4 c4[U];
+      float4 v4[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t kk = k + 128 * u;
+        if (u == 0 || kk < e) {
+          c4[u] = ld_idx4(ci + kk);
+          v4[u] = __ldcs(reinterpret_cast<const float4*>(av + kk));
+        } else {
+          c4[u] = make_int4(0, 0, 0, 0);
+          v4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
-      s = fmaf(v.x, __ldg(x + c4.x), s);
-      s = fmaf(v.y, __ldg(x + c4.y), s);
-      s = fmaf(v.z, __ldg(x + c4.z), s);
-      s = fmaf(v.w, __ldg(x + c4.w), s);
-      s2 = fmaf(vb.x, __ldg(x + c4b.x), s2);
-      s2 = fmaf(vb.y, __ldg(x + c4b.y), s2);
-      s2 = fmaf(vb.z, __ldg(x + c4b.z), s2);
-      s2 = fmaf(vb.w, __ldg(x + c4b.w), s2);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        acc[u] = fmaf(v4[u].x, __ldg(x + c4[u].x), acc[u]);
+        acc[u] = fmaf(v4[u].y, __ldg(x + c4[u].y), acc[u]);
+        acc[u] = fmaf(v4[u].z, __ldg(x + c4[u].z), acc[u]);
+        acc[u] = fmaf(v4[u].w, __ldg(x + c4[u].w), acc[u]);
+      }
     }
-    s += s2;
+#pragma unroll
+    for (int u = 0; u < U; ++u) s += acc[u];
     if (e + lane < hi) s = fmaf(__ldcs(av + e + lane), __ldg(x + ld_idx(ci + e + lane)), s);
   } else {
     for (int64_t k = lo + lane; k < hi; k += G) s = fmaf(__ldcs(av + k), __ldg(x + ld_idx(ci + k)), s);
@@ -111,19 +125,21 @@ RDEV double dot_hilo(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci
       s = fma(widen(__ldcs(ah + k)), __ldg(x + c), s);
       sl = fmaf(__ldcs(al + k), __ldg(xf + c), sl);
     }
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0;   // independent FP64 chains (see dot64)
     for (int64_t k = a + 4 * lane; k < e; k += 128) {
       const int4 c4 = ld_idx4(ci + k);
       const float4 h = __ldcs(reinterpret_cast<const float4*>(ah + k));
       const float4 l = __ldcs(reinterpret_cast<const float4*>(al + k));
       s = fma(widen(h.x), __ldg(x + c4.x), s);
-      s = fma(widen(h.y), __ldg(x + c4.y), s);
-      s = fma(widen(h.z), __ldg(x + c4.z), s);
-      s = fma(widen(h.w), __ldg(x + c4.w), s);
+      s1 = fma(widen(h.y), __ldg(x + c4.y), s1);
+      s2 = fma(widen(h.z), __ldg(x + c4.z), s2);
+      s3 = fma(widen(h.w), __ldg(x + c4.w), s3);
       sl = fmaf(l.x, __ldg(xf + c4.x), sl);
       sl = fmaf(l.y, __ldg(xf + c4.y), sl);
       sl = fmaf(l.z, __ldg(xf + c4.z), sl);
       sl = fmaf(l.w, __ldg(xf + c4.w), sl);
     }
+    s = (s + s1) + (s2 + s3);
     if (e + lane < hi) {
       const int64_t k = e + lane;
       const int c = ld_idx(ci + k);
@@ -343,7 +359,7 @@ __global__ void k_check_mixed(SolveState* st, int slot_idx, int k) {
   }
 }
 
-template <int G, bool V, typename IT>
+template <int G, bool V, typename IT, int U>
 __global__ void __launch_bounds__(NT) k_sweep32(int64_t nq, const int64_t* __restrict__ rp,
                                                 const IT* __restrict__ ci,
                                                 const float* __restrict__ ah,
@@ -355,7 +371,7 @@ __global__ void __launch_bounds__(NT) k_sweep32(int64_t nq, const int64_t* __res
   RowGroups rg = RowGroups::make<G>();
   for (int64_t i = row_begin<G>(rg, ctr); warp_has_row<G>(i, nq); i = row_next<G>(rg, ctr, i)) {
     float s = 0.0f;
-    if (i < nq) s = dot32<G, V, IT>(rp[i], rp[i + 1], rg.lane, ci, ah, din);
+    if (i < nq) s = dot32<G, V, IT, U>(rp[i], rp[i + 1], rg.lane, ci, ah, din);
     s = group_sum<G>(s);
     if (i < nq && rg.lane == 0) dout[i] = (r32[i] + s) / d32[i];
   }
@@ -607,7 +623,7 @@ struct Lay {
   bool vec;
 };
 
-static Lay lay_of(int code) { return code == 64 ? Lay{32, true} : Lay{code, false}; }
+static Lay lay_of(int code) { return code >= 64 ? Lay{32, true} : Lay{code, false}; }
 
 // Row mapping of `method`'s kernels: the autotuned choice if there is one, else the
 // REACH_LANES override, else lanes from the mean row length (warp + 16-byte loads from 96).
@@ -666,18 +682,31 @@ static void l_resid_hilo(reach_ctx* c, int slot, cudaStream_t s, unsigned* ctr =
   }
 }
 
+template <int G, bool V, int U>
+static void l_sweep32_u(reach_ctx* c, const float* din, float* dout, cudaStream_t s, unsigned* cr) {
+  if (V && c->a_col16) {
+    const int grid = grid_rows(c, (const void*)k_sweep32<G, V, uint16_t, U>, NT, G, c->n_q, cr != nullptr);
+    k_sweep32<G, V, uint16_t, U><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col16, c->a_hi, c->r32, c->d32,
+                                                     din, dout, c->st, cr);
+  } else {
+    const int grid = grid_rows(c, (const void*)k_sweep32<G, V, int32_t, U>, NT, G, c->n_q, cr != nullptr);
+    k_sweep32<G, V, int32_t, U><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->r32, c->d32,
+                                                    din, dout, c->st, cr);
+  }
+}
+
+// FP32 sweep; with warp-per-row vector loads the quads per trip (2 or 4) come from the
+// layout code (64 or 66).
 template <int G, bool V>
 static void l_sweep32(reach_ctx* c, const float* din, float* dout, cudaStream_t s, unsigned* ctr = nullptr) {
   unsigned* cr = G == 32 ? ctr : nullptr;
-  if (V && c->a_col16) {
-    const int grid = grid_rows(c, (const void*)k_sweep32<G, V, uint16_t>, NT, G, c->n_q, cr != nullptr);
-    k_sweep32<G, V, uint16_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col16, c->a_hi, c->r32, c->d32,
-                                                  din, dout, c->st, cr);
-  } else {
-    const int grid = grid_rows(c, (const void*)k_sweep32<G, V, int32_t>, NT, G, c->n_q, cr != nullptr);
-    k_sweep32<G, V, int32_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->r32, c->d32,
-                                                 din, dout, c->st, cr);
+  if constexpr (V) {
+    if (c->tune.sweep_u == 4) {
+      l_sweep32_u<G, V, 4>(c, din, dout, s, cr);
+      return;
+    }
   }
+  l_sweep32_u<G, V, 2>(c, din, dout, s, cr);
 }
 
 template <int G, bool V>
@@ -916,7 +945,30 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
     e = split_hilo(c);
     if (e != cudaSuccess) return e;
   }
-  const int codes[6] = {2, 4, 8, 16, 32, 64};
+  // process-wide cache: contexts over the same system shape reuse the measurement
+  static std::mutex cache_mu;
+  static std::unordered_map<std::string, std::pair<int, float>> cache;
+  const std::string key = std::to_string(c->n_q) + "/" + std::to_string(c->m_q) + "/" + std::to_string(method);
+  {
+    std::lock_guard<std::mutex> lk(cache_mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      const int pick = it->second.first;
+      const float best = it->second.second;
+      c->tune.gm[method] = pick;
+      if (method == REACH_JACOBI_MIXED) c->tune.sweep_u = pick == 66 ? 4 : 2;
+      if (method == REACH_JACOBI_FP64) {
+        const double check_ms = 0.006, sweeps = 1000.0;
+        int k = (int)std::lround(std::sqrt(2.0 * sweeps * check_ms / std::max(1e-4, (double)best)));
+        c->tune.k_auto = std::max(2, std::min(62, k + (k & 1)));
+      }
+      *chosen = pick;
+      *best_ms = best;
+      return cudaSuccess;
+    }
+  }
+  // 66: warp + vector loads with four quads per trip (FP32 sweep only)
+  const int codes[7] = {2, 4, 8, 16, 32, 64, 66};
   const double mean = (double)c->m_q / (double)c->n_q;
   Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_val, c->b};
   cudaStream_t s = c->stream;
@@ -924,15 +976,19 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
   int pick = 0;
   for (int code : codes) {
     const Lay L = lay_of(code);
+    if (code == 66 && method != REACH_JACOBI_MIXED) continue;
     if (L.vec && mean < 16) continue;            // nothing to vectorise
     if (!L.vec && L.g > 4 * mean + 4) continue;  // mostly idle lanes
+    if (method == REACH_JACOBI_MIXED) c->tune.sweep_u = code == 66 ? 4 : 2;
+    unsigned* ctr = &c->st->rowctr[0];
     float total = 0.f;
     for (int rep = 0; rep < 4; ++rep) {
+      cudaMemsetAsync(ctr, 0, sizeof(unsigned), s);
       e = cudaEventRecord(c->ev0, s);
       if (method == REACH_JACOBI_MIXED) {
-        LAY_DISPATCH(L, l_sweep32, c, c->dl[0], c->dl[1], s);
+        LAY_DISPATCH(L, l_sweep32, c, c->dl[0], c->dl[1], s, ctr);
       } else {
-        LAY_DISPATCH(L, l_jacobi, c, y, c->x, c->x2, &c->st->slot[62], s);
+        LAY_DISPATCH(L, l_jacobi, c, y, c->x, c->x2, &c->st->slot[62], s, ctr);
       }
       if (e == cudaSuccess) e = cudaEventRecord(c->ev1, s);
       if (e == cudaSuccess) e = cudaEventSynchronize(c->ev1);
@@ -947,6 +1003,11 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
       pick = code;
     }
   }
+  if (method == REACH_JACOBI_MIXED) c->tune.sweep_u = pick == 66 ? 4 : 2;
+  {
+    std::lock_guard<std::mutex> lk(cache_mu);
+    cache[key] = {pick, best};
+  }
   c->tune.gm[method] = pick;
   if (method == REACH_JACOBI_FP64) {
     const double check_ms = 0.006, sweeps = 1000.0;
@@ -957,6 +1018,51 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
   *chosen = pick;
   *best_ms = best;
   return cudaSuccess;
+}
+
+// Average device time of `launches` back-to-back launches of one solver kernel on the
+// context stream, in the layout and row order the solves use (CUDA events on that
+// stream).  kernel: 0 FP64 Jacobi sweep, 1 FP32 sweep, 2 FP64 hi+lo residual,
+// 3 BiCGStab product v = M p.  The kernels only touch solve workspace.
+cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
+  *avg_ms = 0.f;
+  if (c->n_q == 0 || launches < 1) return cudaSuccess;
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaSuccess;
+  if (kernel == 1 || kernel == 2) {
+    e = split_hilo(c);
+    if (e != cudaSuccess) return e;
+    k_apply<<<ew_grid(c, (const void*)k_apply, c->n_q), NT, 0, s>>>(c->n_q, c->x, c->xf, nullptr, c->st, 0);
+  }
+  const int method = kernel == 0 ? REACH_JACOBI_FP64 : kernel == 3 ? REACH_BICGSTAB_FP64 : REACH_JACOBI_MIXED;
+  const Lay L = layout(c, c->n_q, c->m_q, method);
+  Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_val, c->b};
+  SolveState hs;
+  std::memset(&hs, 0, sizeof(hs));
+  hs.eps = 1e-300;
+  hs.max_iter = 1;
+  hs.max_bodies = 1;
+  e = cudaMemcpyAsync(c->st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  auto one = [&](int) {
+    unsigned* ctr = &c->st->rowctr[0];
+    cudaMemsetAsync(ctr, 0, sizeof(unsigned), s);   // fresh row counter for every launch
+    if (kernel == 0) LAY_DISPATCH(L, l_jacobi, c, y, c->x, c->x2, &c->st->slot[0], s, ctr);
+    else if (kernel == 1) LAY_DISPATCH(L, l_sweep32, c, c->dl[0], c->dl[1], s, ctr);
+    else if (kernel == 2) LAY_DISPATCH(L, l_resid_hilo, c, 0, s, ctr);
+    else LAY_DISPATCH(L, l_bi_v, c, s);
+  };
+  one(0);  // warm-up
+  e = cudaEventRecord(c->ev0, s);
+  for (int j = 1; j <= launches && e == cudaSuccess; ++j) one(j);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(c->ev1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  *avg_ms = ms / (float)launches;
+  return e;
 }
 
 }  // namespace reach
