@@ -212,6 +212,8 @@ static reach_status create_common(reach_ctx** out, int64_t n, int64_t m, const i
   if (e == cudaSuccess) e = cudaMemsetAsync(c->col + m, 0, 8 * sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->val + m, 0, 8 * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ticket, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->st, 0, sizeof(SolveState), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->bi, 0, sizeof(BiState), s);
   int64_t ends[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[0], c->rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], c->rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);

@@ -967,6 +967,18 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
       return cudaSuccess;
     }
   }
+  // a fresh solve state: a finished solve leaves `done` set, and the solve kernels
+  // return at once when it is
+  {
+    SolveState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.eps = 1e-300;
+    hs.max_iter = 1;
+    hs.max_bodies = 1;
+    e = cudaMemcpyAsync(c->st, &hs, sizeof(hs), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return e;
+  }
   // 66: warp + vector loads with four quads per trip (FP32 sweep only)
   const int codes[7] = {2, 4, 8, 16, 32, 64, 66};
   const double mean = (double)c->m_q / (double)c->n_q;
@@ -1045,9 +1057,14 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
   e = cudaMemcpyAsync(c->st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
+  if (kernel == 3) {   // a non-zero shadow vector, so q.v never reads as a breakdown
+    e = cudaMemcpyAsync(c->vq, c->b, sizeof(double) * c->n_q, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
   auto one = [&](int) {
     unsigned* ctr = &c->st->rowctr[0];
     cudaMemsetAsync(ctr, 0, sizeof(unsigned), s);   // fresh row counter for every launch
+    cudaMemsetAsync(&c->st->done, 0, sizeof(int32_t), s);
     if (kernel == 0) LAY_DISPATCH(L, l_jacobi, c, y, c->x, c->x2, &c->st->slot[0], s, ctr);
     else if (kernel == 1) LAY_DISPATCH(L, l_sweep32, c, c->dl[0], c->dl[1], s, ctr);
     else if (kernel == 2) LAY_DISPATCH(L, l_resid_hilo, c, 0, s, ctr);

@@ -146,6 +146,22 @@ def test_warm_start_and_iteration_cap(c1):
     del torch
 
 
+@pytest.mark.parametrize("method,tol", METHODS)
+def test_autotune_then_solve(c1, method, tol):
+    """The autotuner's pick (timed on a fresh solve state, even after a finished solve)
+    is a valid mapping, and solves with it still match the oracle."""
+    cls_o, x_o = oracle_solution(c1)
+    need_gpu()
+    with R.Solver(c1.n, c1.rowptr, c1.col, c1.val, c1.goal) as s:
+        s.solve("jacobi", eps=1e-12)                 # leaves the device state 'done'
+        t = s.autotune(method)
+        assert t["lanes"] in (2, 4, 8, 16, 32, 64, 66) and t["sweep_ms"] > 0
+        x, info = s.solve(method, eps=_eps(method))
+        assert np.max(np.abs(x - x_o)) <= tol
+        for k in ("jacobi64", "sweep32", "resid_hilo", "bicgstab_spmv"):
+            assert R.reach_time_kernel(s.ctx, k, 3) > 0.0
+
+
 def test_jacobi_monotone_from_below(c1):
     """Iterates from x = 0 never decrease and never pass x* (A >= 0, b >= 0)."""
     cls_o, x_o = oracle_solution(c1)
