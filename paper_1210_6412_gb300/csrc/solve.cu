@@ -72,31 +72,44 @@ RDEV float dot32(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
     if (a > hi) a = hi;
     const int64_t e = a + ((hi - a) & ~int64_t(3));
     if (lo + lane < a) s = fmaf(__ldcs(av + lo + lane), __ldg(x + ld_idx(ci + lo + lane)), s);
-    // U quads per lane per trip: all U loads are in flight before any is used
+    // U quads per lane per trip, software-pipelined: the next trip's index and value
+    // loads are issued before this trip's gathers, so HBM loads stay in flight while
+    // the gathers of x (L1 / L2) complete.  Quads past the row end load as zeros.
     float acc[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) acc[u] = 0.0f;
-    for (int64_t k = a + 4 * lane; k < e; k += 128 * U) {
-      int4 c4[U];
-      float4 v4[U];
+    int4 c4[U];
+    float4 v4[U];
+    auto load_trip = [&](int64_t k, int4 (&ci4)[U], float4 (&vv4)[U]) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int64_t kk = k + 128 * u;
-        if (u == 0 || kk < e) {
-          c4[u] = ld_idx4(ci + kk);
-          v4[u] = __ldcs(reinterpret_cast<const float4*>(av + kk));
+        if (kk < e) {
+          ci4[u] = ld_idx4(ci + kk);
+          vv4[u] = __ldcs(reinterpret_cast<const float4*>(av + kk));
         } else {
-          c4[u] = make_int4(0, 0, 0, 0);
-          v4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          ci4[u] = make_int4(0, 0, 0, 0);
+          vv4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
+    };
+    int64_t k = a + 4 * lane;
+    load_trip(k, c4, v4);
+    while (k < e) {
+      const int64_t kn = k + 128 * U;
+      int4 n4[U];
+      float4 w4[U];
+      load_trip(kn, n4, w4);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         acc[u] = fmaf(v4[u].x, __ldg(x + c4[u].x), acc[u]);
         acc[u] = fmaf(v4[u].y, __ldg(x + c4[u].y), acc[u]);
         acc[u] = fmaf(v4[u].z, __ldg(x + c4[u].z), acc[u]);
         acc[u] = fmaf(v4[u].w, __ldg(x + c4[u].w), acc[u]);
+        c4[u] = n4[u];
+        v4[u] = w4[u];
       }
+      k = kn;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) s += acc[u];
