@@ -41,10 +41,11 @@ TARGET_ERR = 1e-9
 # stopping thresholds that give max error <= 1e-9 on this system (contraction ~0.99)
 EPS = {"jacobi": 5e-12, "mixed": 5e-12, "bicgstab": 5e-12}
 K_REFINE = 16
-# DRAM traffic per FP64 Jacobi sweep from an ncu capture of the same kernel
-# (profiles/jacobi64_dense32768.md); None until captured for the current kernel.
-NCU_TRAFFIC_BYTES = None
-NCU_TRAFFIC_SWEEP32_BYTES = None
+# DRAM bytes (read + write) per launch from ncu captures of the current kernels on this
+# workload: profiles/jacobi64_dense32768.md and profiles/mixed_dense32768.md.  Set back
+# to None whenever the kernel changes, until it is captured again.
+NCU_TRAFFIC_BYTES = 1.271852e9 + 3.255296e6
+NCU_TRAFFIC_SWEEP32_BYTES = 0.633176e9 + 3.001344e6
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA per clock (ncu's
 # roofline reports 4 FP64 flop/clk/SM) x 2 flop x 2.07 GHz; matches the 1.25 TFLOP/s nominal.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
