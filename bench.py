@@ -343,6 +343,93 @@ def run_ours(args):
     return 0
 
 
+def _timed_solves(R, torch, n, d_in, mode, eps, methods, stream):
+    """One context: create + precompute + each method; device times from the library."""
+    out = {}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    ctx = R.reach_create(n, *d_in, stream=stream.cuda_stream)
+    try:
+        R.reach_precompute(ctx, mode)
+        xo = torch.empty(n, dtype=torch.float64, device="cuda")
+        for meth in methods:
+            R.reach_autotune(ctx, meth)
+            _, info = R.reach_solve(ctx, n, meth, eps=eps[meth], max_iter=2_000_000, refine_k=K_REFINE,
+                                    out=xo)
+            out[meth] = {"ms": info["ms_solve"], "iters": info["iters"], "resid_inf": info["resid_inf"],
+                         "alg_GBps": info["bytes_moved"] / max(info["ms_solve"], 1e-9) / 1e6,
+                         "n_q": info["n_q"], "m_q": info["m_q"], "precompute_ms": info["ms_precompute"]}
+    finally:
+        R.reach_destroy(ctx)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return out, ev0.elapsed_time(ev1)
+
+
+def run_workload(args):
+    """The other workloads of the method, one JSON line each (not the headline metric).
+
+    random4096: 4096 states, 16 successors, 2% goals, 2% sinks, solved to max|dx| < 1e-10.
+    layered: 2000 x 4000 layered model-checker-like chain (8M states).
+    batched: independent chains with 8 goal sets each (`--chains`, default 64; 256 is the
+             full batch), 2% sinks, FP32 + FP64 refinement to 1e-6.
+    parametric: 4M-state softmax chain, forward solve plus the adjoint gradient in theta.
+    """
+    import torch
+    import paper_1210_6412_gb300 as R
+    from paper_1210_6412_gb300 import synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    dev = lambda *a: [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in a]
+    line = {"workload": args.workload, "unit": "ms"}
+    if args.workload in ("random4096", "layered"):
+        c = synth.random_chain() if args.workload == "random4096" else synth.layered_chain()
+        eps = ({"jacobi": 1e-10, "mixed": 1e-10, "bicgstab": 1e-10} if args.workload == "random4096"
+               else {"jacobi": 1e-12, "mixed": 1e-10, "bicgstab": 1e-12})
+        d_in = dev(c.rowptr, c.col, c.val, c.goal)
+        for _ in range(max(1, args.warmup)):
+            _timed_solves(R, torch, c.n, d_in, R.REACH_PROB01, eps, list(eps), stream)
+        res, total = _timed_solves(R, torch, c.n, d_in, R.REACH_PROB01, eps, list(eps), stream)
+        line.update({"n": c.n, "nnz": c.m, "eps": eps, "methods": res, "step_ms": total})
+    elif args.workload == "batched":
+        bt = synth.batched_chains(n_chains=args.chains, sink_frac=0.02)
+        n, rowptr, col, val, goals, offs = bt.concat()
+        d_in = dev(rowptr, col, val, goals)
+        for rep in range(max(1, args.warmup) + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with R.BatchSolver(n, *d_in) as bs:
+                x, info = bs.solve(eps=1e-8, out=torch.empty((goals.shape[0], n), dtype=torch.float64,
+                                                              device="cuda"))
+            torch.cuda.synchronize()
+            wall = (time.perf_counter() - t0) * 1e3
+        line.update({"chains": args.chains, "n": n, "nnz": int(rowptr[-1]), "k": int(goals.shape[0]),
+                     "precompute_ms": info["ms_precompute"], "solve_ms": info["ms_solve"],
+                     "iters": info["iters"], "refinements": info["refinements"],
+                     "resid_inf": info["resid_inf"],
+                     "alg_GBps": info["bytes_moved"] / info["ms_solve"] / 1e6, "wall_ms": wall})
+    elif args.workload == "parametric":
+        from paper_1210_6412_gb300.autograd import reach_prob
+        pc = synth.parametric_chain()
+        args_d = dev(pc.rowptr, pc.col, pc.cls, pc.offset, pc.goal)
+        for rep in range(max(1, args.warmup) + 1):
+            theta = torch.from_numpy(pc.theta).cuda().requires_grad_(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            y = reach_prob(theta, *args_d, pc.init, eps=1e-13)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            y.backward()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+        line.update({"n": pc.n, "nnz": pc.m, "classes": int(pc.theta.size), "x_init": float(y),
+                     "forward_ms": (t1 - t0) * 1e3, "backward_ms": (t2 - t1) * 1e3,
+                     "grad_norm": float(theta.grad.norm())})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_profile(args):
     """Small fixed run for ncu: the bench workload, one context, `--profile-iters`
     iterations of one method (no stopping test can end it early)."""
@@ -372,9 +459,14 @@ def main():
     ap.add_argument("--profile", choices=["jacobi", "mixed", "bicgstab"], default=None,
                     help="run a short fixed-length solve for ncu and exit")
     ap.add_argument("--profile-iters", type=int, default=32)
+    ap.add_argument("--workload", choices=["dense", "random4096", "layered", "batched", "parametric"],
+                    default="dense", help="dense = the benchmark; the others print their own line")
+    ap.add_argument("--chains", type=int, default=64, help="--workload batched: number of chains")
     args = ap.parse_args()
     if args.profile:
         return run_profile(args)
+    if args.workload != "dense":
+        return run_workload(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

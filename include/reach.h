@@ -68,7 +68,12 @@ typedef enum { REACH_PROB01 = 0, REACH_PROB0_ONLY = 1 } reach_precomp_mode;
 typedef enum {
   REACH_JACOBI_FP64 = 0,
   REACH_JACOBI_MIXED = 1,
-  REACH_BICGSTAB_FP64 = 2
+  REACH_BICGSTAB_FP64 = 2,
+  /* The FP64 Jacobi iteration and stopping rule of JACOBI_FP64 with a different sweep:
+   * work is split over stored entries instead of rows, by a segmented reduction over
+   * the flat entry array (the related work of §8 runs Jacobi on a segmented scan), so
+   * very long rows do not serialise on one warp.  Only the summation order differs. */
+  REACH_JACOBI_SEG = 3
 } reach_method;
 
 typedef struct {

@@ -22,6 +22,7 @@ __all__ = [
     "REACH_OK", "REACH_EINVAL", "REACH_ENOMEM", "REACH_ECUDA", "REACH_ESTATE", "REACH_ENOTCONV",
     "REACH_EBREAKDOWN", "REACH_ETIMEOUT", "REACH_HOST", "REACH_DEVICE", "REACH_PROB01",
     "REACH_PROB0_ONLY", "REACH_JACOBI_FP64", "REACH_JACOBI_MIXED", "REACH_BICGSTAB_FP64",
+    "REACH_JACOBI_SEG",
     "reach_create", "reach_precompute", "reach_get_classes", "reach_solve", "reach_grad",
     "reach_param_probs", "reach_param_grad_theta", "reach_last_error", "reach_destroy",
     "reach_version", "Solver", "reach_batch_create", "reach_batch_precompute",
@@ -32,13 +33,14 @@ REACH_OK, REACH_EINVAL, REACH_ENOMEM, REACH_ECUDA, REACH_ESTATE = 0, 1, 2, 3, 4
 REACH_ENOTCONV, REACH_EBREAKDOWN, REACH_ETIMEOUT = 5, 6, 7
 REACH_HOST, REACH_DEVICE = 0, 1
 REACH_PROB01, REACH_PROB0_ONLY = 0, 1
-REACH_JACOBI_FP64, REACH_JACOBI_MIXED, REACH_BICGSTAB_FP64 = 0, 1, 2
+REACH_JACOBI_FP64, REACH_JACOBI_MIXED, REACH_BICGSTAB_FP64, REACH_JACOBI_SEG = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENOTCONV",
                 6: "EBREAKDOWN", 7: "ETIMEOUT"}
 METHODS = {"jacobi": REACH_JACOBI_FP64, "jacobi_fp64": REACH_JACOBI_FP64,
            "mixed": REACH_JACOBI_MIXED, "jacobi_mixed": REACH_JACOBI_MIXED,
-           "bicgstab": REACH_BICGSTAB_FP64, "bicgstab_fp64": REACH_BICGSTAB_FP64}
+           "bicgstab": REACH_BICGSTAB_FP64, "bicgstab_fp64": REACH_BICGSTAB_FP64,
+           "jacobi_seg": REACH_JACOBI_SEG}
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "reach.h")
 
 

@@ -112,10 +112,11 @@ void free_system(reach_ctx* c) {
   dfree(c->at_rowptr); dfree(c->at_col); dfree(c->at_val);
   dfree(c->x); dfree(c->x2); dfree(c->vr); dfree(c->vq); dfree(c->vp); dfree(c->vv);
   dfree(c->vs); dfree(c->vt); dfree(c->r32); dfree(c->xf); dfree(c->dl[0]); dfree(c->dl[1]);
+  seg_free(c);
 }
 
 void drop_graphs(reach_ctx* c) {
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 5; ++i) {
     if (c->g_exec[i]) cudaGraphExecDestroy(c->g_exec[i]);
     c->g_exec[i] = nullptr;
     c->g_key[i] = -1;
@@ -367,7 +368,7 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
                          const double* x0, double* x_out, int32_t flags, reach_info* info) {
   if (!c) return fail(nullptr, REACH_EINVAL, "reach_solve: NULL context");
   if (!c->have_classes) return fail(c, REACH_ESTATE, "reach_solve: call reach_precompute first");
-  if (method < REACH_JACOBI_FP64 || method > REACH_BICGSTAB_FP64)
+  if (method < REACH_JACOBI_FP64 || method > REACH_JACOBI_SEG)
     return fail(c, REACH_EINVAL, "reach_solve: unknown method");
   if (!(eps > 0.0) || !std::isfinite(eps)) return fail(c, REACH_EINVAL, "reach_solve: eps must be > 0");
   if (max_iter < 1) return fail(c, REACH_EINVAL, "reach_solve: max_iter must be >= 1");
@@ -407,6 +408,7 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
   if (e == cudaSuccess && c->n_q > 0) {
     if (method == REACH_JACOBI_FP64) e = solve_jacobi64(c, x0q, false);
     else if (method == REACH_JACOBI_MIXED) e = solve_mixed(c, x0q);
+    else if (method == REACH_JACOBI_SEG) e = solve_jacobi_seg(c, x0q);
     else e = solve_bicgstab(c, x0q);
   }
   if (e == cudaSuccess) e = scatter_full(c, c->x, c->xfull);
@@ -425,7 +427,7 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
   }
   const double mq = (double)c->m_q, nq = (double)c->n_q;
   double bytes = 0.0;
-  if (method == REACH_JACOBI_FP64) bytes = (double)hs.iter * (mq * 12.0 + nq * 40.0);
+  if (method == REACH_JACOBI_FP64 || method == REACH_JACOBI_SEG) bytes = (double)hs.iter * (mq * 12.0 + nq * 40.0);
   else if (method == REACH_JACOBI_MIXED)
     bytes = (double)hs.refinements * (mq * 12.0 + nq * 40.0) +
             (double)(hs.iter - hs.refinements) * (mq * 8.0 + nq * 24.0);

@@ -516,6 +516,10 @@ static cudaError_t dmalloc(T** p, int64_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (size_t)count);
 }
 
+cudaError_t exclusive_scan_u8(reach_ctx* c, const uint8_t* in, int64_t* out, int64_t n, int64_t* total_dev) {
+  return exclusive_scan<uint8_t>(in, out, n, total_dev, reinterpret_cast<int64_t*>(c->part), c->stream);
+}
+
 cudaError_t classify_and_extract(reach_ctx* c, int mode) {
   const int64_t n = c->n, words = (n + 31) >> 5;
   uint8_t* qflag = reinterpret_cast<uint8_t*>(c->queue);   // scratch: n bytes

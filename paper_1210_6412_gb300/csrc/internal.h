@@ -142,8 +142,10 @@ struct reach_ctx {
   double ms_precompute = 0.0;
 
   // cached solve graphs, keyed by method and shape
-  cudaGraphExec_t g_exec[4] = {nullptr, nullptr, nullptr, nullptr};
-  int64_t g_key[4] = {-1, -1, -1, -1};
+  cudaGraphExec_t g_exec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t g_key[5] = {-1, -1, -1, -1, -1};
+
+  void* seg = nullptr;      // tile plan of the entry-balanced Jacobi sweep (segscan.cu)
 };
 
 namespace reach {
@@ -174,6 +176,13 @@ void launch_check_mixed(cudaStream_t s, SolveState* st, int slot, int k);
 cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms);
 cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms);
 void launch_finalize_resid(cudaStream_t s, SolveState* st);
+
+// ---- segscan.cu
+cudaError_t solve_jacobi_seg(reach_ctx* c, const double* x0q);
+void seg_free(reach_ctx* c);
+// ---- more of graph.cu / solve.cu used by segscan.cu
+cudaError_t exclusive_scan_u8(reach_ctx* c, const uint8_t* in, int64_t* out, int64_t n, int64_t* total_dev);
+cudaError_t residual_report(reach_ctx* c, const double* xq);
 
 // ---- shared host helpers (api.cu)
 int pick_group(int64_t rows, int64_t nnz);

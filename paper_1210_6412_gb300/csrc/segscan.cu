@@ -1,0 +1,383 @@
+// FP64 Jacobi sweep balanced over stored entries instead of rows: a segmented
+// reduction over the flat entry array of A (the related work the paper cites runs the
+// Jacobi iteration on a backward segmented scan; the forward segmented reduction used
+// here yields the same row sums).  Every CTA processes one tile of SEG_T consecutive
+// entries whatever the row lengths, so a matrix with a few very long rows keeps every
+// SM busy, where a row-per-warp mapping would leave one warp with a whole long row.
+//
+// Per sweep: k_seg_sweep reads each entry once, finishes every row whose entries lie in
+// one tile, and leaves for each tile the sum before its first row end (head) and after
+// its last row end (tail); k_seg_fix completes the rows that span tiles by adding those
+// partial sums in tile order and also handles rows without entries.  All sums are in a
+// fixed order, so the sweep is deterministic.
+#include <algorithm>
+#include <cstdint>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace reach {
+
+constexpr int SEG_NT = 256;
+constexpr int SEG_ITEMS = 8;
+constexpr int64_t SEG_T = SEG_NT * SEG_ITEMS;   // entries per tile
+
+struct SegPlan {
+  int64_t ntiles = 0;
+  int64_t n_span = 0;      // rows whose entries span more than one tile
+  int64_t n_empty = 0;     // rows without entries
+  uint32_t* endbits = nullptr;    // bit k: entry k is the last of its row
+  int64_t* tile_row0 = nullptr;   // nonempty-row index of the row holding the tile's first entry
+  int64_t* nonempty = nullptr;    // nonempty-row index -> row
+  int64_t* span = nullptr;        // rows spanning tiles
+  int64_t* empty = nullptr;       // rows without entries
+  double* head = nullptr;         // per tile
+  double* tail = nullptr;         // per tile
+};
+
+// ---- plan construction (once per system)
+
+__global__ void k_seg_marks(int64_t nq, const int64_t* __restrict__ rp, uint32_t* endbits,
+                            uint8_t* nonempty_flag, uint8_t* span_flag, uint8_t* empty_flag) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nq;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lo = rp[r], hi = rp[r + 1];
+    const bool ne = hi > lo;
+    nonempty_flag[r] = ne;
+    empty_flag[r] = !ne;
+    span_flag[r] = ne && (lo / SEG_T) != ((hi - 1) / SEG_T);
+    if (ne) atomicOr(endbits + ((hi - 1) >> 5), 1u << ((hi - 1) & 31));
+  }
+}
+
+__global__ void k_seg_compact(int64_t nq, const uint8_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                              int64_t* __restrict__ out) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nq;
+       r += (int64_t)gridDim.x * blockDim.x)
+    if (flag[r]) out[pos[r]] = r;
+}
+
+// Row holding entry t*SEG_T (binary search in rp), as a nonempty-row index.
+__global__ void k_seg_tile_rows(int64_t nq, int64_t ntiles, const int64_t* __restrict__ rp,
+                                const int64_t* __restrict__ ne_pos, int64_t* __restrict__ tile_row0) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = t * SEG_T;
+    int64_t lo = 0, hi = nq;                 // last r with rp[r] <= k
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (rp[mid] <= k) lo = mid;
+      else hi = mid;
+    }
+    while (lo < nq && rp[lo + 1] <= k) ++lo;  // skip empty rows sitting at k
+    tile_row0[t] = ne_pos[lo];
+  }
+}
+
+// ---- the sweep
+
+// Inclusive segmented sum across the CTA: (v, f) then (w, g) -> (g ? w : v + w, f | g).
+RDEV void seg_scan_cta(double& v, int& f, double* shv, int* shf) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double pv = __shfl_up_sync(FULL, v, o);
+    const int pf = __shfl_up_sync(FULL, f, o);
+    if (lane >= o && !f) v += pv;
+    if (lane >= o) f |= pf;
+  }
+  if (lane == 31) {
+    shv[w] = v;
+    shf[w] = f;
+  }
+  __syncthreads();
+  if (w == 0) {
+    double a = lane < (SEG_NT / 32) ? shv[lane] : 0.0;
+    int af = lane < (SEG_NT / 32) ? shf[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double pv = __shfl_up_sync(FULL, a, o);
+      const int pf = __shfl_up_sync(FULL, af, o);
+      if (lane >= o && !af) a += pv;
+      if (lane >= o) af |= pf;
+    }
+    if (lane < SEG_NT / 32) {
+      shv[lane] = a;
+      shf[lane] = af;
+    }
+  }
+  __syncthreads();
+  if (w > 0 && !f) v += shv[w - 1];
+  if (w > 0) f |= shf[w - 1];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(SEG_NT) k_seg_sweep(int64_t mq, int64_t ntiles, const int64_t* __restrict__ rp,
+                                                      const int32_t* __restrict__ ci, const double* __restrict__ av,
+                                                      const double* __restrict__ b, const double* __restrict__ d,
+                                                      const double* __restrict__ x, double* __restrict__ xn,
+                                                      const uint32_t* __restrict__ endbits,
+                                                      const int64_t* __restrict__ tile_row0,
+                                                      const int64_t* __restrict__ nonempty,
+                                                      double* __restrict__ head, double* __restrict__ tail,
+                                                      unsigned long long* slot) {
+  __shared__ double shv[SEG_NT / 32];
+  __shared__ int shf[SEG_NT / 32];
+  __shared__ int shc[SEG_NT / 32];
+  double mx = 0.0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t base = t * SEG_T + (int64_t)threadIdx.x * SEG_ITEMS;
+    // products of this thread's entries and their row-end flags
+    double p[SEG_ITEMS];
+    unsigned flags = 0;
+    if (base + SEG_ITEMS <= mq) {
+      const int4 c0 = __ldcs(reinterpret_cast<const int4*>(ci + base));
+      const int4 c1 = __ldcs(reinterpret_cast<const int4*>(ci + base + 4));
+      const int cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const double2 v = __ldcs(reinterpret_cast<const double2*>(av + base + 2 * h));
+        p[2 * h] = v.x * __ldg(x + cc[2 * h]);
+        p[2 * h + 1] = v.y * __ldg(x + cc[2 * h + 1]);
+      }
+      flags = (__ldg(endbits + (base >> 5)) >> (base & 31)) & 0xffu;
+    } else {
+#pragma unroll
+      for (int j = 0; j < SEG_ITEMS; ++j) {
+        const int64_t k = base + j;
+        p[j] = k < mq ? __ldcs(av + k) * __ldg(x + __ldcs(ci + k)) : 0.0;
+        if (k < mq && ((__ldg(endbits + (k >> 5)) >> (k & 31)) & 1u)) flags |= 1u << j;
+      }
+    }
+    const int cnt = __popc(flags);
+    // row index (among non-empty rows) of this thread's first entry: tile start + row ends before it
+    int excl = cnt;
+    {
+      const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int pv = __shfl_up_sync(FULL, excl, o);
+        if (lane >= o) excl += pv;
+      }
+      if (lane == 31) shc[w] = excl;
+      __syncthreads();
+      int off = 0;
+      for (int j = 0; j < w; ++j) off += shc[j];
+      excl += off - cnt;
+      __syncthreads();
+    }
+    // thread-local pieces: head (up to the first row end), whole rows inside, tail
+    double head_v = 0.0, run = 0.0, tail_v = 0.0;
+    int seen = 0;
+    const int64_t row0 = tile_row0[t] + excl;    // nonempty index of this thread's first row
+#pragma unroll
+    for (int j = 0; j < SEG_ITEMS; ++j) {
+      run += p[j];
+      if ((flags >> j) & 1u) {
+        if (seen == 0) {
+          head_v = run;                          // completed below, after the carry-in
+        } else {
+          const int64_t r = nonempty[row0 + seen];   // row entirely inside this thread
+          const double xv = (b[r] + run) / d[r];
+          mx = fmax(mx, fabs(xv - x[r]));
+          xn[r] = xv;
+        }
+        ++seen;
+        run = 0.0;
+      }
+    }
+    tail_v = run;   // entries after the last row end (all of them when cnt == 0)
+    // Segmented scan over threads: value = this thread's tail, a segment starts at every
+    // thread with a row end.  The exclusive result is the part of this thread's first row
+    // that lies in earlier threads of the tile.
+    int f = cnt ? 1 : 0;
+    double incl = tail_v;
+    seg_scan_cta(incl, f, shv, shf);
+    double carry = __shfl_up_sync(FULL, incl, 1);
+    {
+      const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+      __shared__ double lastv[SEG_NT / 32];
+      if (lane == 31) lastv[w] = incl;
+      __syncthreads();
+      if (lane == 0) carry = w > 0 ? lastv[w - 1] : 0.0;
+      __syncthreads();
+    }
+    if (cnt) {
+      const double first_total = carry + head_v;
+      const int64_t r = nonempty[row0];
+      if (rp[r] >= t * SEG_T) {                  // the row starts inside this tile: complete
+        const double xv = (b[r] + first_total) / d[r];
+        mx = fmax(mx, fabs(xv - x[r]));
+        xn[r] = xv;
+      } else {                                   // started in an earlier tile: finished by k_seg_fix
+        head[t] = first_total;
+      }
+    }
+    // the tile's last thread publishes what follows the tile's last row end
+    if (threadIdx.x == SEG_NT - 1) tail[t] = incl;
+    __syncthreads();
+  }
+  __shared__ double sh[32];
+  double a[1] = {mx != mx ? __longlong_as_double(0x7ff0000000000000LL) : mx};
+  block_reduce<1, true>(a, sh);
+  if (threadIdx.x == 0) atomic_max_nonneg(slot, a[0]);
+}
+
+// Rows spanning tiles: tail of the first tile + whole middle tiles + head of the last
+// tile, in tile order.  Threads past the spanning rows handle rows without entries.
+__global__ void k_seg_fix(int64_t n_span, int64_t n_empty, const int64_t* __restrict__ span,
+                          const int64_t* __restrict__ empty, const int64_t* __restrict__ rp,
+                          const double* __restrict__ head, const double* __restrict__ tail,
+                          const double* __restrict__ b, const double* __restrict__ d,
+                          const double* __restrict__ x, double* __restrict__ xn, unsigned long long* slot) {
+  double mx = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_span + n_empty;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r;
+    double s = 0.0;
+    if (i < n_span) {
+      r = span[i];
+      const int64_t t0 = rp[r] / SEG_T, t1 = (rp[r + 1] - 1) / SEG_T;
+      s = tail[t0];
+      for (int64_t t = t0 + 1; t < t1; ++t) s += tail[t];
+      s += head[t1];
+    } else {
+      r = empty[i - n_span];
+    }
+    const double xv = (b[r] + s) / d[r];
+    mx = fmax(mx, fabs(xv - x[r]));
+    xn[r] = xv;
+  }
+  __shared__ double sh[32];
+  double a[1] = {mx != mx ? __longlong_as_double(0x7ff0000000000000LL) : mx};
+  block_reduce<1, true>(a, sh);
+  if (threadIdx.x == 0) atomic_max_nonneg(slot, a[0]);
+}
+
+__global__ void k_seg_check(SolveState* st, int slot_idx, int sweeps, int reset_n) {
+  if (st->done) return;
+  const double dl = slot_value(&st->slot[slot_idx]);
+  st->iter += sweeps;
+  st->last = dl;
+  if (dl < st->eps) {
+    st->done = 1;
+    st->status = REACH_OK;
+  } else if (st->iter >= st->max_iter) {
+    st->done = 1;
+    st->status = REACH_ENOTCONV;
+  }
+  for (int j = 0; j < reset_n; ++j) st->slot[j] = 0ull;
+}
+
+// ---- host side
+
+template <typename T>
+static cudaError_t salloc(T** p, int64_t n) {
+  return cudaMalloc((void**)p, sizeof(T) * (size_t)(n > 0 ? n : 1));
+}
+
+void seg_free(reach_ctx* c) {
+  SegPlan* sp = static_cast<SegPlan*>(c->seg);
+  if (!sp) return;
+  cudaFree(sp->endbits);
+  cudaFree(sp->tile_row0);
+  cudaFree(sp->nonempty);
+  cudaFree(sp->span);
+  cudaFree(sp->empty);
+  cudaFree(sp->head);
+  cudaFree(sp->tail);
+  delete sp;
+  c->seg = nullptr;
+}
+
+// Tile plan of the current system: row-end bits, the row of each tile's first entry,
+// the rows spanning tiles and the rows without entries.
+static cudaError_t seg_plan(reach_ctx* c) {
+  if (c->seg) return cudaSuccess;
+  cudaStream_t s = c->stream;
+  const int64_t nq = c->n_q, mq = c->m_q;
+  SegPlan* sp = new SegPlan();
+  c->seg = sp;
+  sp->ntiles = (mq + SEG_T - 1) / SEG_T;
+  const int64_t words = (mq + 31) / 32 + 1;
+  uint8_t *fne = nullptr, *fspan = nullptr, *fempty = nullptr;
+  int64_t *pne = nullptr, *pspan = nullptr, *pempty = nullptr;
+  cudaError_t e;
+  if ((e = salloc(&sp->endbits, words)) != cudaSuccess || (e = salloc(&sp->tile_row0, sp->ntiles)) != cudaSuccess ||
+      (e = salloc(&sp->head, sp->ntiles)) != cudaSuccess || (e = salloc(&sp->tail, sp->ntiles)) != cudaSuccess ||
+      (e = salloc(&fne, nq)) != cudaSuccess || (e = salloc(&fspan, nq)) != cudaSuccess ||
+      (e = salloc(&fempty, nq)) != cudaSuccess || (e = salloc(&pne, nq + 1)) != cudaSuccess ||
+      (e = salloc(&pspan, nq + 1)) != cudaSuccess || (e = salloc(&pempty, nq + 1)) != cudaSuccess) {
+    cudaFree(fne); cudaFree(fspan); cudaFree(fempty); cudaFree(pne); cudaFree(pspan); cudaFree(pempty);
+    seg_free(c);
+    return e;
+  }
+  cudaMemsetAsync(sp->endbits, 0, sizeof(uint32_t) * words, s);
+  const int g = grid_for(c, (const void*)k_seg_marks, 256, nq);
+  k_seg_marks<<<g, 256, 0, s>>>(nq, c->a_rowptr, sp->endbits, fne, fspan, fempty);
+  int64_t counts[3] = {0, 0, 0};
+  int64_t* tot = reinterpret_cast<int64_t*>(c->st) + 2;     // scratch words
+  e = exclusive_scan_u8(c, fne, pne, nq, tot);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&counts[0], tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = exclusive_scan_u8(c, fspan, pspan, nq, tot);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&counts[1], tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = exclusive_scan_u8(c, fempty, pempty, nq, tot);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&counts[2], tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) {
+    sp->n_span = counts[1];
+    sp->n_empty = counts[2];
+    if ((e = salloc(&sp->nonempty, counts[0])) == cudaSuccess && (e = salloc(&sp->span, counts[1])) == cudaSuccess &&
+        (e = salloc(&sp->empty, counts[2])) == cudaSuccess) {
+      k_seg_compact<<<g, 256, 0, s>>>(nq, fne, pne, sp->nonempty);
+      k_seg_compact<<<g, 256, 0, s>>>(nq, fspan, pspan, sp->span);
+      k_seg_compact<<<g, 256, 0, s>>>(nq, fempty, pempty, sp->empty);
+      if (sp->ntiles > 0)
+        k_seg_tile_rows<<<grid_for(c, (const void*)k_seg_tile_rows, 256, sp->ntiles), 256, 0, s>>>(
+            nq, sp->ntiles, c->a_rowptr, pne, sp->tile_row0);
+      e = cudaStreamSynchronize(s);
+    }
+  }
+  cudaFree(fne); cudaFree(fspan); cudaFree(fempty); cudaFree(pne); cudaFree(pspan); cudaFree(pempty);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) seg_free(c);
+  return e;
+}
+
+static void seg_sweep(reach_ctx* c, const double* x, double* xn, unsigned long long* slot, cudaStream_t s) {
+  SegPlan* sp = static_cast<SegPlan*>(c->seg);
+  if (sp->ntiles > 0) {
+    const int grid = (int)std::min<int64_t>(sp->ntiles, grid_for(c, (const void*)k_seg_sweep, SEG_NT, INT64_MAX / 2));
+    k_seg_sweep<<<grid, SEG_NT, 0, s>>>(c->m_q, sp->ntiles, c->a_rowptr, c->a_col, c->a_val, c->b, c->d, x, xn,
+                                         sp->endbits, sp->tile_row0, sp->nonempty, sp->head, sp->tail, slot);
+  }
+  const int64_t rest = sp->n_span + sp->n_empty;
+  if (rest > 0)
+    k_seg_fix<<<grid_for(c, (const void*)k_seg_fix, 256, rest), 256, 0, s>>>(
+        sp->n_span, sp->n_empty, sp->span, sp->empty, c->a_rowptr, sp->head, sp->tail, c->b, c->d, x, xn, slot);
+}
+
+// FP64 Jacobi (§3.1) with the entry-balanced sweep: same iteration and stopping rule as
+// REACH_JACOBI_FP64, different work distribution (and summation order).
+cudaError_t solve_jacobi_seg(reach_ctx* c, const double* x0q) {
+  cudaStream_t s = c->stream;
+  const int64_t nq = c->n_q;
+  cudaError_t e = seg_plan(c);
+  if (e != cudaSuccess) return e;
+  if (x0q) cudaMemcpyAsync(c->x, x0q, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
+  else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
+  const int k = c->tune.k;
+  const int64_t key = (nq * 1000003LL + c->m_q) * 131 + 1000LL * k + 77;
+  e = run_loop(c, c->g_exec[4], c->g_key[4], key, [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
+    for (int j = 0; j < k; ++j) {
+      const double* xi = (j & 1) ? c->x2 : c->x;
+      double* xo = (j & 1) ? c->x : c->x2;
+      seg_sweep(c, xi, xo, &c->st->slot[j], cs);
+    }
+    k_seg_check<<<1, 1, 0, cs>>>(c->st, k - 1, k, k);
+  });
+  if (e != cudaSuccess) return e;
+  return residual_report(c, c->x);
+}
+
+}  // namespace reach

@@ -533,29 +533,36 @@ __global__ void __launch_bounds__(NT) k_bi_v(int64_t nq, const int64_t* __restri
   }
 }
 
+// s = r - a v (elementwise; formed once here instead of at every gather of the next
+// product, which doubled that product's FP64 work).
+__global__ void k_bi_s(int64_t nq, const double* __restrict__ r, const double* __restrict__ v,
+                       double* __restrict__ s, const BiState* bi, const SolveState* st) {
+  if (st->done || bi->skip) return;
+  const double a = bi->a;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s[i] = r[i] - a * v[i];
+}
+
 template <int G, bool V>
 __global__ void __launch_bounds__(NT) k_bi_t(int64_t nq, const int64_t* __restrict__ rp,
                                              const int32_t* __restrict__ ci,
                                              const double* __restrict__ av,
                                              const double* __restrict__ d,
-                                             const double* __restrict__ r,
-                                             const double* __restrict__ v,
-                                             double* __restrict__ s_out, double* __restrict__ t,
+                                             const double* __restrict__ sv, double* __restrict__ t,
                                              double* part, unsigned* ticket, BiState* bi,
                                              SolveState* st, unsigned* ctr) {
   if (st->done || bi->skip) return;
-  const double a = bi->a;
   RowGroups rg = RowGroups::make<G>();
   double acc[3] = {0.0, 0.0, 0.0};
-  auto sf = [r, v, a](int32_t j) { return __ldg(r + j) - a * __ldg(v + j); };
+  auto sf = [sv](int32_t j) { return __ldg(sv + j); };
   for (int64_t i = row_begin<G>(rg, ctr); warp_has_row<G>(i, nq); i = row_next<G>(rg, ctr, i)) {
     double s = 0.0;
     if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, av, sf);
     s = group_sum<G>(s);
     if (i < nq && rg.lane == 0) {
-      const double si = r[i] - a * v[i];
+      const double si = sv[i];
       const double ti = d[i] * si - s;
-      s_out[i] = si;
       t[i] = ti;
       acc[0] = fma(ti, si, acc[0]);
       acc[1] = fma(ti, ti, acc[1]);
@@ -741,7 +748,7 @@ template <int G, bool V>
 static void l_bi_t(reach_ctx* c, cudaStream_t s) {
   unsigned* cr = G == 32 ? &c->st->rowctr[1] : nullptr;
   const int grid = grid_rows(c, (const void*)k_bi_t<G, V>, NT, G, c->n_q, cr != nullptr);
-  k_bi_t<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_val, c->d, c->vr, c->vv, c->vs,
+  k_bi_t<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_val, c->d, c->vs,
                                    c->vt, c->part, c->ticket, c->bi, c->st, cr);
 }
 
@@ -857,6 +864,15 @@ cudaError_t solve_mixed(reach_ctx* c, const double* x0q) {
   return cudaGetLastError();
 }
 
+// FP64 max|b - (I - A) x| of the final iterate into SolveState::resid.
+cudaError_t residual_report(reach_ctx* c, const double* xq) {
+  const Lay L = layout(c, c->n_q, c->m_q, REACH_JACOBI_FP64);
+  Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_val, c->b};
+  LAY_DISPATCH(L, l_resid, c, y, xq, c->stream);
+  k_finalize_resid<<<1, 1, 0, c->stream>>>(c->st);
+  return cudaGetLastError();
+}
+
 cudaError_t solve_bicgstab(reach_ctx* c, const double* x0q) {
   cudaStream_t s = c->stream;
   const int64_t nq = c->n_q;
@@ -867,6 +883,7 @@ cudaError_t solve_bicgstab(reach_ctx* c, const double* x0q) {
   cudaError_t e = run_loop(c, c->g_exec[2], c->g_key[2], shape_key(c, L, 1), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
     k_bi_p<<<ew_grid(c, (const void*)k_bi_p, nq), NT, 0, cs>>>(nq, c->vr, c->vp, c->vv, c->vq, c->bi, c->st);
     LAY_DISPATCH(L, l_bi_v, c, cs);
+    k_bi_s<<<ew_grid(c, (const void*)k_bi_s, nq), NT, 0, cs>>>(nq, c->vr, c->vv, c->vs, c->bi, c->st);
     LAY_DISPATCH(L, l_bi_t, c, cs);
     k_bi_x<<<ew_grid(c, (const void*)k_bi_x, nq), NT, 0, cs>>>(nq, c->x, c->vp, c->vs, c->vt, c->vr, c->vq,
                                                                c->part, c->ticket, c->bi, c->st);

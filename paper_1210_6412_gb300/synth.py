@@ -372,6 +372,32 @@ def diag_dominant_system(n=4096, density=0.01, max_int=10, margin=(1, 10), seed=
                   name=f"diagonally dominant n={n} density={density}")
 
 
+def skewed_chain(n=20000, zipf_a=1.6, max_deg=64, hubs=8, hub_deg=6000, goal_frac=0.02,
+                 sink_frac=0.02, seed=1210_6412_8):
+    """Chain with skewed out-degrees: Zipf(zipf_a) degrees capped at max_deg, plus `hubs`
+    states with `hub_deg` distinct successors (the load-balancing case of row-wise
+    kernels).  Successors uniform and distinct, weights U(0,1] normalised."""
+    rng = np.random.default_rng(seed)
+    d = np.minimum(rng.zipf(zipf_a, size=n), max_deg).astype(np.int64)
+    hub_idx = np.sort(rng.choice(np.arange(1, n), size=min(hubs, n - 1), replace=False))
+    d[hub_idx] = 1                      # placeholder row, replaced below
+    col = _distinct_columns(rng, d, lambda r, s: rng.integers(0, n, size=np.shape(r), dtype=np.int64))
+    # hub rows: hub_deg distinct successors each, drawn without replacement
+    rowptr = _rowptr(d)
+    pieces, start = [], 0
+    for h in hub_idx:
+        pieces.append(col[start:rowptr[h]])
+        pieces.append(np.sort(rng.choice(n, size=min(hub_deg, n), replace=False)).astype(np.int32))
+        start = rowptr[h + 1]
+    pieces.append(col[start:])
+    col = np.concatenate(pieces)
+    d[hub_idx] = min(hub_deg, n)
+    w = 1.0 - rng.random(col.size)
+    cand = np.setdiff1d(np.arange(1, n), hub_idx)
+    g, s = _goals_and_sinks(rng, n, max(1, int(round(goal_frac * n))), int(round(sink_frac * n)), cand)
+    return _finish(n, _rowptr(d), col, w, rng, g, s, f"skewed n={n} zipf={zipf_a} hubs={hubs}x{hub_deg}")
+
+
 def gamblers_ruin(N=20, p=0.4):
     """Random walk on 0..N, up with probability p, down with 1-p; 0 and N absorbing; GS={N}."""
     n = N + 1

@@ -146,6 +146,24 @@ def test_warm_start_and_iteration_cap(c1):
     del torch
 
 
+@pytest.mark.parametrize("name", ["random", "skewed", "dense", "gambler", "table1", "layered"])
+def test_segmented_jacobi_matches_oracle(c1, name):
+    """The entry-balanced sweep (segmented reduction) gives the FP64 Jacobi answer:
+    long rows spanning many tiles, rows without off-diagonal entries, a ragged last tile."""
+    c = {"random": lambda: c1,
+         "skewed": lambda: synth.skewed_chain(n=20000, hub_deg=9000),
+         "dense": lambda: synth.dense_random_chain(n=2000, density=0.1, sink_frac=0.02, seed=5),
+         "gambler": lambda: synth.gamblers_ruin(40, 0.45),
+         "table1": lambda: synth.table1_chain(1333, 2665),
+         "layered": lambda: synth.layered_chain(layers=60, width=300, seed=11)}[name]()
+    cls_o, x_o = oracle_solution(c)
+    cls, x, info = gpu_solve(c, O.PROB01, "jacobi_seg", 1e-13)
+    _, xj, ij = gpu_solve(c, O.PROB01, "jacobi", 1e-13)
+    assert np.array_equal(cls, cls_o)
+    assert np.max(np.abs(x - x_o)) <= TOL_FP64
+    assert abs(info["iters"] - ij["iters"]) <= 16 and info["resid_inf"] < 1e-11
+
+
 @pytest.mark.parametrize("method,tol", METHODS)
 def test_autotune_then_solve(c1, method, tol):
     """The autotuner's pick (timed on a fresh solve state, even after a finished solve)
