@@ -354,7 +354,8 @@ def _timed_solves(R, torch, n, d_in, mode, eps, methods, stream):
         R.reach_precompute(ctx, mode)
         xo = torch.empty(n, dtype=torch.float64, device="cuda")
         for meth in methods:
-            R.reach_autotune(ctx, meth)
+            if meth != "jacobi_seg":
+                R.reach_autotune(ctx, meth)
             _, info = R.reach_solve(ctx, n, meth, eps=eps[meth], max_iter=2_000_000, refine_k=K_REFINE,
                                     out=xo)
             out[meth] = {"ms": info["ms_solve"], "iters": info["iters"], "resid_inf": info["resid_inf"],
@@ -383,10 +384,16 @@ def run_workload(args):
     stream = torch.cuda.current_stream()
     dev = lambda *a: [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in a]
     line = {"workload": args.workload, "unit": "ms"}
-    if args.workload in ("random4096", "layered"):
-        c = synth.random_chain() if args.workload == "random4096" else synth.layered_chain()
-        eps = ({"jacobi": 1e-10, "mixed": 1e-10, "bicgstab": 1e-10} if args.workload == "random4096"
-               else {"jacobi": 1e-12, "mixed": 1e-10, "bicgstab": 1e-12})
+    if args.workload in ("random4096", "layered", "skewed"):
+        if args.workload == "random4096":
+            c = synth.random_chain()
+            eps = {"jacobi": 1e-10, "mixed": 1e-10, "bicgstab": 1e-10}
+        elif args.workload == "layered":
+            c = synth.layered_chain()
+            eps = {"jacobi": 1e-12, "mixed": 1e-10, "bicgstab": 1e-12}
+        else:   # row-wise vs entry-balanced sweeps on a few very long rows
+            c = synth.skewed_chain(n=1_000_000, hubs=16, hub_deg=200_000)
+            eps = {"jacobi": 1e-12, "jacobi_seg": 1e-12, "mixed": 1e-10, "bicgstab": 1e-12}
         d_in = dev(c.rowptr, c.col, c.val, c.goal)
         for _ in range(max(1, args.warmup)):
             _timed_solves(R, torch, c.n, d_in, R.REACH_PROB01, eps, list(eps), stream)
@@ -459,7 +466,7 @@ def main():
     ap.add_argument("--profile", choices=["jacobi", "mixed", "bicgstab"], default=None,
                     help="run a short fixed-length solve for ncu and exit")
     ap.add_argument("--profile-iters", type=int, default=32)
-    ap.add_argument("--workload", choices=["dense", "random4096", "layered", "batched", "parametric"],
+    ap.add_argument("--workload", choices=["dense", "random4096", "layered", "skewed", "batched", "parametric"],
                     default="dense", help="dense = the benchmark; the others print their own line")
     ap.add_argument("--chains", type=int, default=64, help="--workload batched: number of chains")
     args = ap.parse_args()
