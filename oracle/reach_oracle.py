@@ -18,6 +18,9 @@ paper's order and notation:
   (none)     adjoint solve and parameter gradients                -> adjoint, grad_p,
                                                                      softmax_probs, grad_theta
   (none)     a-posteriori error bound                             -> error_bound
+  §6         strongly connected components of the digraph of A, solved in reverse
+             topological order (the future-work idea of §6)      -> scc_labels, scc_levels,
+                                                                     block_jacobi
 
 Where the paper is silent or ambiguous the oracle takes these readings:
   * initial vector x = 0 for both methods (the listings draw it at random);
@@ -339,6 +342,111 @@ def error_bound(m, b, x):
     tau = dense_solve(m, np.ones(m.shape[0]))
     r = b - m @ x
     return float(np.max(tau) * np.max(np.abs(r))) if r.size else 0.0
+
+
+# ---------------------------------------------------------------- §6: SCCs in reverse topological order
+
+def scc_labels(a):
+    """Strongly connected component of every row of the digraph of A (§6).
+
+    The digraph has an edge i -> j for every off-diagonal A_ij != 0 (the diagonal sits
+    in d and links a state only to itself).  Rows i and j share a component exactly when
+    each reaches the other.  The components come from scipy's strong-connectivity
+    routine (a library step); each is labelled by its largest row index, a name that
+    does not depend on how the components were found.
+    """
+    import scipy.sparse.csgraph as csg
+    a = sp.csr_matrix(a)
+    nq = a.shape[0]
+    if nq == 0:
+        return np.zeros(0, np.int64)
+    pat = sp.csr_matrix((np.ones(a.nnz), a.indices, a.indptr), shape=a.shape)
+    pat.setdiag(0)
+    pat.eliminate_zeros()
+    _, comp = csg.connected_components(pat, directed=True, connection="strong")
+    top = np.full(comp.max() + 1, -1, np.int64)
+    np.maximum.at(top, comp, np.arange(nq))
+    return top[comp]
+
+
+def scc_levels(a, labels):
+    """Level of every row: its component's height in the condensation DAG (§6).
+
+    A component without edges to other components has level 0; any other component
+    sits one above the highest component it has an edge to.  Components of one level
+    never link to each other, and every edge leaves a level for a lower one, so solving
+    level 0, 1, 2, ... in turn is the reverse topological order of §6.  Computed by
+    peeling the condensation from its sinks, one level per pass.
+    """
+    a = sp.csr_matrix(a)
+    nq = a.shape[0]
+    labels = np.asarray(labels, np.int64)
+    row = np.repeat(np.arange(nq), np.diff(a.indptr))
+    src, dst = labels[row], labels[a.indices]
+    keep = src != dst
+    pairs = np.unique(np.stack([src[keep], dst[keep]], 1), axis=0) if keep.any() else np.zeros((0, 2), np.int64)
+    comps = np.unique(labels)
+    out_deg = dict.fromkeys(comps.tolist(), 0)
+    preds = {c: [] for c in comps.tolist()}
+    for u, v in pairs.tolist():
+        out_deg[u] += 1
+        preds[v].append(u)
+    level = {}
+    frontier = [c for c in comps.tolist() if out_deg[c] == 0]
+    h = 0
+    while frontier:
+        nxt = []
+        for c in frontier:
+            level[c] = h
+        for c in frontier:
+            for u in preds[c]:
+                out_deg[u] -= 1
+                if out_deg[u] == 0:
+                    nxt.append(u)
+        frontier = nxt
+        h += 1
+    if len(level) != comps.size:
+        raise OracleInputError("condensation has a cycle")   # impossible for true SCCs
+    return np.array([level[c] for c in labels.tolist()], np.int64)
+
+
+def block_jacobi(m, b, eps, max_iter, labels=None, levels=None):
+    """Jacobi for M x = b one level of SCCs at a time, lowest level first (§6, §3.1).
+
+    Rows of level h depend only on rows of their own components and of lower levels,
+    which are already solved; so each level runs the Jacobi sweep of §3.1 on its own
+    rows, with every other row held fixed, until max|x - x'| < eps over those rows.
+    Returns (x, total sweeps, number of levels, converged).  ``max_iter`` bounds the
+    sweeps of each level.
+    """
+    m = sp.csr_matrix(m)
+    nq = m.shape[0]
+    diag = m.diagonal()
+    off = (m - sp.diags(diag)).tocsr()
+    off.sort_indices()
+    a = -off
+    if labels is None:
+        labels = scc_labels(a)
+    if levels is None:
+        levels = scc_levels(a, labels)
+    x = np.zeros(nq)
+    sweeps = 0
+    n_levels = int(levels.max()) + 1 if nq else 0
+    for h in range(n_levels):
+        rows = np.flatnonzero(levels == h)
+        sub = off[rows]
+        ok = False
+        for _ in range(max_iter):
+            new = (b[rows] - sub @ x) / diag[rows]
+            delta = float(np.max(np.abs(new - x[rows])))
+            x[rows] = new
+            sweeps += 1
+            if delta < eps:
+                ok = True
+                break
+        if not ok:
+            return x, sweeps, n_levels, False
+    return x, sweeps, n_levels, True
 
 
 # ---------------------------------------------------------------- gradients (not in the paper)

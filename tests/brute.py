@@ -94,3 +94,30 @@ def dense_to_csr(p):
     np.add.at(rowptr, rows + 1, 1)
     rowptr = np.cumsum(rowptr)
     return rowptr, cols.astype(np.int32), p[rows, cols].astype(np.float64)
+
+
+def scc_by_closure(adj):
+    """Label of every vertex's strongly connected component: the largest vertex that
+    both reaches it and is reached from it (mutual reachability, by the closure)."""
+    r = closure(adj)
+    mutual = r & r.T
+    n = adj.shape[0]
+    return np.array([max(j for j in range(n) if mutual[i, j]) for i in range(n)], np.int64)
+
+
+def condensation_height(adj, labels):
+    """Longest path, counted in edges between components, from each vertex's component
+    to a component with no edge out, by memoised depth-first recursion."""
+    n = adj.shape[0]
+    succ = {}
+    for i in range(n):
+        for j in range(n):
+            if adj[i, j] and labels[i] != labels[j]:
+                succ.setdefault(int(labels[i]), set()).add(int(labels[j]))
+    memo = {}
+
+    def height(c):
+        if c not in memo:
+            memo[c] = 1 + max((height(s) for s in succ.get(c, ())), default=-1)
+        return memo[c]
+    return np.array([height(int(labels[i])) for i in range(n)], np.int64)

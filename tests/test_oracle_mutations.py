@@ -105,3 +105,67 @@ def test_grad_wrong_index_is_caught(monkeypatch):
     _patch(monkeypatch, "grad_p", bad)
     with pytest.raises(AssertionError):
         pins.test_grad_p_matches_central_differences()
+
+
+def test_scc_label_by_smallest_row_is_caught(monkeypatch):
+    orig = R.scc_labels
+
+    def bad(a):
+        lab = orig(a)
+        out = lab.copy()
+        for c in np.unique(lab):
+            out[lab == c] = np.flatnonzero(lab == c).min()
+        return out
+    _patch(monkeypatch, "scc_labels", bad)
+    with pytest.raises(AssertionError):
+        for seed in range(25):
+            pins.test_scc_labels_and_levels_match_brute_force(seed)
+
+
+def test_scc_levels_counting_vertices_not_components_is_caught(monkeypatch):
+    """Heights over the vertex digraph (edges inside a component counted) are wrong."""
+    def bad(a, labels):
+        import scipy.sparse.csgraph as csg
+        a = sp.csr_matrix(a)
+        nq = a.shape[0]
+        h = np.zeros(nq, np.int64)
+        for _ in range(nq):
+            row = np.repeat(np.arange(nq), np.diff(a.indptr))
+            nh = np.zeros(nq, np.int64)
+            np.maximum.at(nh, row, h[a.indices] + 1)
+            nh = np.minimum(nh, nq)
+            if np.array_equal(nh, h):
+                break
+            h = nh
+        return h
+    _patch(monkeypatch, "scc_levels", bad)
+    with pytest.raises(AssertionError):
+        for seed in range(25):
+            pins.test_scc_labels_and_levels_match_brute_force(seed)
+
+
+def test_block_jacobi_highest_level_first_is_caught(monkeypatch):
+    def bad(m, b, eps, max_iter, labels=None, levels=None):
+        m = sp.csr_matrix(m)
+        nq = m.shape[0]
+        diag = m.diagonal()
+        off = (m - sp.diags(diag)).tocsr()
+        lab = R.scc_labels(-off)
+        lev = R.scc_levels(-off, lab)
+        x = np.zeros(nq)
+        nl = int(lev.max()) + 1 if nq else 0
+        sweeps = 0
+        for h in reversed(range(nl)):
+            rows = np.flatnonzero(lev == h)
+            for _ in range(max_iter):
+                new = (b[rows] - off[rows] @ x) / diag[rows]
+                d = float(np.max(np.abs(new - x[rows])))
+                x[rows] = new
+                sweeps += 1
+                if d < eps:
+                    break
+        return x, sweeps, nl, True
+    _patch(monkeypatch, "block_jacobi", bad)
+    with pytest.raises(AssertionError):
+        for seed in range(10):
+            pins.test_block_jacobi_matches_lu(seed)

@@ -304,3 +304,80 @@ def test_grad_theta_matches_central_differences():
     fd = np.array([(x_init(pc.theta + h * np.eye(8)[j]) - x_init(pc.theta - h * np.eye(8)[j])) / (2 * h)
                    for j in range(8)])
     np.testing.assert_allclose(g_t, fd, rtol=1e-5, atol=1e-9)
+
+
+# ---------------------------------------------------------------- §6: SCCs, reverse topological order
+
+def _random_digraph_system(seed, n_max=60):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(1, n_max))
+    dens = rng.uniform(0.01, 0.15)
+    adj = (rng.random((n, n)) < dens) & ~np.eye(n, dtype=bool)
+    w = adj * rng.uniform(0.05, 1.0, (n, n))
+    # substochastic rows that leak to S=1 / S=0: (I - A) is an M-matrix
+    a = w / (w.sum(axis=1, keepdims=True) + rng.uniform(0.1, 1.0, (n, 1)))
+    b = rng.uniform(0.0, 1.0, n) * (1.0 - a.sum(axis=1))
+    return adj, sp.csr_matrix(a), b
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_scc_labels_and_levels_match_brute_force(seed):
+    adj, a, _ = _random_digraph_system(seed)
+    lab = O.scc_labels(a)
+    assert np.array_equal(lab, brute.scc_by_closure(adj))
+    lev = O.scc_levels(a, lab)
+    assert np.array_equal(lev, brute.condensation_height(adj, lab))
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_scc_levels_order_every_edge(seed):
+    """Every edge goes to the same component at the same level or to a lower level."""
+    adj, a, _ = _random_digraph_system(seed, n_max=200)
+    lab = O.scc_labels(a)
+    lev = O.scc_levels(a, lab)
+    i, j = np.nonzero(adj)
+    same = lab[i] == lab[j]
+    assert np.all(lev[i][same] == lev[j][same])
+    assert np.all(lev[i][~same] > lev[j][~same])
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_block_jacobi_matches_lu(seed):
+    _, a, b = _random_digraph_system(seed, n_max=200)
+    m = sp.identity(a.shape[0], format="csr") - a
+    x, sweeps, nl, ok = O.block_jacobi(m, b, 1e-14, 100_000)
+    assert ok
+    assert np.max(np.abs(x - O.dense_solve(m, b))) < 1e-12
+    assert nl == (O.scc_levels(a, O.scc_labels(a)).max() + 1 if a.shape[0] else 0)
+
+
+def test_block_jacobi_on_a_dag_takes_two_sweeps_per_level():
+    """Acyclic system: every level is exact after one sweep and the second sees no change."""
+    rng = np.random.default_rng(77)
+    n = 300
+    adj = np.triu(rng.random((n, n)) < 0.02, k=1)          # edges only to higher rows
+    perm = rng.permutation(n)
+    adj = adj[np.ix_(perm, perm)]
+    w = adj * rng.uniform(0.1, 1.0, (n, n))
+    a = sp.csr_matrix(w / (w.sum(axis=1, keepdims=True) + 0.5))
+    b = rng.uniform(0.0, 1.0, n) * (1.0 - np.asarray(a.sum(axis=1)).ravel())
+    lab = O.scc_labels(a)
+    assert np.array_equal(lab, np.arange(n))                  # every row its own component
+    m = sp.identity(n, format="csr") - a
+    x, sweeps, nl, ok = O.block_jacobi(m, b, 1e-300, 10)
+    assert ok and sweeps == 2 * nl
+    assert np.max(np.abs(x - O.dense_solve(m, b))) < 1e-14
+    assert nl == brute.condensation_height(adj, lab).max() + 1
+
+
+def test_scc_of_the_worked_chain():
+    """S? = {s0, s2} of the worked chain form one cycle (s0 -> s2 -> s0): one component."""
+    c = synth.worked_chain()
+    cls = O.partition(*chain_arrays(c))
+    q, a, b = O.extract_system(c.n, c.rowptr, c.col, c.val, cls)
+    lab = O.scc_labels(a)
+    assert lab.tolist() == [1, 1]
+    assert O.scc_levels(a, lab).tolist() == [0, 0]
+    x, sweeps, nl, ok = O.block_jacobi(O.system_matrix(a), b, 1e-15, 10_000)
+    assert ok and nl == 1
+    assert np.max(np.abs(x - np.array([0.625, 0.25]))) < 1e-14
