@@ -360,7 +360,7 @@ def scc_labels(a):
     nq = a.shape[0]
     if nq == 0:
         return np.zeros(0, np.int64)
-    pat = sp.csr_matrix((np.ones(a.nnz), a.indices, a.indptr), shape=a.shape)
+    pat = sp.csr_matrix((np.ones(a.nnz), a.indices.copy(), a.indptr.copy()), shape=a.shape)
     pat.setdiag(0)
     pat.eliminate_zeros()
     _, comp = csg.connected_components(pat, directed=True, connection="strong")

@@ -381,3 +381,11 @@ def test_scc_of_the_worked_chain():
     x, sweeps, nl, ok = O.block_jacobi(O.system_matrix(a), b, 1e-15, 10_000)
     assert ok and nl == 1
     assert np.max(np.abs(x - np.array([0.625, 0.25]))) < 1e-14
+
+
+def test_scc_labels_leaves_its_input_alone():
+    _, a, _ = _random_digraph_system(3, n_max=80)
+    a = a + sp.identity(a.shape[0], format="csr") * 0.25        # stored diagonal
+    before = (a.indptr.copy(), a.indices.copy(), a.data.copy())
+    O.scc_labels(a)
+    assert all(np.array_equal(x, y) for x, y in zip(before, (a.indptr, a.indices, a.data)))
