@@ -44,8 +44,8 @@ K_REFINE = 16
 # DRAM bytes (read + write) per launch from ncu captures of the current kernels on this
 # workload: profiles/jacobi64_dense32768.md and profiles/mixed_dense32768.md.  Set back
 # to None whenever the kernel changes, until it is captured again.
-NCU_TRAFFIC_BYTES = 1.271852e9 + 3.255296e6
-NCU_TRAFFIC_SWEEP32_BYTES = 0.633176e9 + 3.001344e6
+NCU_TRAFFIC_BYTES = None
+NCU_TRAFFIC_SWEEP32_BYTES = None
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA per clock (ncu's
 # roofline reports 4 FP64 flop/clk/SM) x 2 flop x 2.07 GHz; matches the 1.25 TFLOP/s nominal.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -283,12 +283,12 @@ def run_ours(args):
     jac = infos["jacobi"]
     nq, mq = jac["n_q"], jac["m_q"]
     sweep_ms = jac["ms_solve"] / max(jac["iters"], 1)
-    alg_bytes = mq * 12 + nq * 40
+    alg_bytes = mq * 12 + nq * 32
     peak_hbm, peak_kind = peaks()
     # per-kernel device times, measured live on the context stream with CUDA events
     kern = kernel_times(R, n, d_in, stream)
-    kbytes = {"jacobi64": mq * 12 + nq * 40, "sweep32": mq * (6 if nq <= 65536 else 8) + nq * 24,
-              "resid_hilo": mq * (10 if nq <= 65536 else 12) + nq * 40, "bicgstab_spmv": mq * 12 + nq * 40}
+    kbytes = {"jacobi64": mq * 12 + nq * 32, "sweep32": mq * (6 if nq <= 65536 else 8) + nq * 16,
+              "resid_hilo": mq * (10 if nq <= 65536 else 12) + nq * 36, "bicgstab_spmv": mq * 12 + nq * 40}
     kernels = {}
     for k, t in kern.items():
         gbs = kbytes[k] / (t * 1e-3) / 1e9
@@ -354,13 +354,21 @@ def _timed_solves(R, torch, n, d_in, mode, eps, methods, stream):
         R.reach_precompute(ctx, mode)
         xo = torch.empty(n, dtype=torch.float64, device="cuda")
         for meth in methods:
-            if meth != "jacobi_seg":
+            extra = {}
+            if meth in ("jacobi", "mixed", "bicgstab"):
                 R.reach_autotune(ctx, meth)
+            if meth == "scc_jacobi":   # the decomposition, timed on its own, then the level sweeps
+                _, _, si = R.reach_scc(ctx, labels=False)
+                extra = {"decompose_ms": si["ms"], "n_scc": si["n_scc"], "n_levels": si["n_levels"],
+                         "largest_scc": si["largest"], "exact": si["exact"]}
             _, info = R.reach_solve(ctx, n, meth, eps=eps[meth], max_iter=2_000_000, refine_k=K_REFINE,
                                     out=xo)
-            out[meth] = {"ms": info["ms_solve"], "iters": info["iters"], "resid_inf": info["resid_inf"],
+            out[meth] = {"ms": info["ms_solve"] + extra.get("decompose_ms", 0.0), "iters": info["iters"],
+                         "resid_inf": info["resid_inf"],
                          "alg_GBps": info["bytes_moved"] / max(info["ms_solve"], 1e-9) / 1e6,
                          "n_q": info["n_q"], "m_q": info["m_q"], "precompute_ms": info["ms_precompute"]}
+            if extra:
+                out[meth].update(extra, sweeps_ms=info["ms_solve"])
     finally:
         R.reach_destroy(ctx)
     ev1.record(stream)
@@ -384,16 +392,23 @@ def run_workload(args):
     stream = torch.cuda.current_stream()
     dev = lambda *a: [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in a]
     line = {"workload": args.workload, "unit": "ms"}
-    if args.workload in ("random4096", "layered", "skewed"):
+    if args.workload in ("random4096", "layered", "layered_dag", "cascade", "skewed"):
         if args.workload == "random4096":
             c = synth.random_chain()
-            eps = {"jacobi": 1e-10, "mixed": 1e-10, "bicgstab": 1e-10}
+            eps = {"jacobi": 1e-10, "mixed": 1e-10, "bicgstab": 1e-10, "scc_jacobi": 1e-10}
         elif args.workload == "layered":
             c = synth.layered_chain()
-            eps = {"jacobi": 1e-12, "mixed": 1e-10, "bicgstab": 1e-12}
+            eps = {"jacobi": 1e-12, "mixed": 1e-10, "bicgstab": 1e-12, "scc_jacobi": 1e-12}
+        elif args.workload == "layered_dag":   # the layered chain without back-edges
+            c = synth.layered_chain(p_forward=1.0)
+            eps = {"jacobi": 1e-12, "mixed": 1e-10, "bicgstab": 1e-12, "scc_jacobi": 1e-12}
+        elif args.workload == "cascade":       # 64 strongly connected stages in a row
+            c = synth.cascade_chain(blocks=64, width=65536)
+            eps = {"jacobi": 1e-12, "mixed": 1e-10, "bicgstab": 1e-12, "scc_jacobi": 1e-12}
         else:   # row-wise vs entry-balanced sweeps on a few very long rows
             c = synth.skewed_chain(n=1_000_000, hubs=16, hub_deg=200_000)
-            eps = {"jacobi": 1e-12, "jacobi_seg": 1e-12, "mixed": 1e-10, "bicgstab": 1e-12}
+            eps = {"jacobi": 1e-11, "jacobi_seg": 1e-11, "mixed": 1e-10, "bicgstab": 1e-11,
+                   "scc_jacobi": 1e-11}
         d_in = dev(c.rowptr, c.col, c.val, c.goal)
         for _ in range(max(1, args.warmup)):
             _timed_solves(R, torch, c.n, d_in, R.REACH_PROB01, eps, list(eps), stream)
@@ -466,7 +481,8 @@ def main():
     ap.add_argument("--profile", choices=["jacobi", "mixed", "bicgstab"], default=None,
                     help="run a short fixed-length solve for ncu and exit")
     ap.add_argument("--profile-iters", type=int, default=32)
-    ap.add_argument("--workload", choices=["dense", "random4096", "layered", "skewed", "batched", "parametric"],
+    ap.add_argument("--workload", choices=["dense", "random4096", "layered", "layered_dag", "cascade", "skewed",
+                                           "batched", "parametric"],
                     default="dense", help="dense = the benchmark; the others print their own line")
     ap.add_argument("--chains", type=int, default=64, help="--workload batched: number of chains")
     args = ap.parse_args()

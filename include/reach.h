@@ -73,7 +73,16 @@ typedef enum {
    * work is split over stored entries instead of rows, by a segmented reduction over
    * the flat entry array (the related work of §8 runs Jacobi on a segmented scan), so
    * very long rows do not serialise on one warp.  Only the summation order differs. */
-  REACH_JACOBI_SEG = 3
+  REACH_JACOBI_SEG = 3,
+  /* Jacobi one level of strongly connected components at a time, in reverse
+   * topological order (the future-work idea of §6): the decomposition of reach_scc
+   * (computed on first use), then for level 0, 1, ...: a level of single-row
+   * components is exact after one sweep; any other level runs the FP64 Jacobi sweep of
+   * §3.1 on its own rows, with all other rows held fixed, until max|x' - x| < eps over
+   * them.  max_iter bounds the total sweeps over all levels (at least one per level).
+   * info->iters counts those sweeps; ms_solve includes the decomposition when this call
+   * computed it. */
+  REACH_SCC_JACOBI = 4
 } reach_method;
 
 typedef struct {
@@ -88,6 +97,21 @@ typedef struct {
   int32_t status;         /* reach_status of the solve */
   int32_t refinements;    /* JACOBI_MIXED: FP64 residual steps taken */
 } reach_info;
+
+/* Strongly connected components of the digraph of A over S? (an edge i -> j for each
+ * stored off-diagonal A_ij), from reach_scc. */
+typedef struct {
+  int64_t n_q;            /* rows of the system (|S?|) */
+  int64_t n_scc;          /* components */
+  int64_t n_levels;       /* levels of the condensation (the solve order of REACH_SCC_JACOBI) */
+  int64_t n_trivial;      /* single-row components */
+  int64_t largest;        /* rows of the largest component */
+  int32_t exact;          /* 1: the components are exact; 0: the colouring hit its round cap
+                           * and the cyclic core left after trimming is one block (still a
+                           * valid solve order, coarser than the components) */
+  int32_t rounds;         /* colouring rounds run */
+  double ms;              /* device time of the decomposition */
+} reach_scc_info;
 
 /* Create a context holding a copy of P and the goal mask (§2, §4).
  * goal: uint8[n], nonzero marks GS.  Validates the chain on the device (column
@@ -126,6 +150,19 @@ reach_status reach_get_classes(reach_ctx* ctx, uint8_t* cls, int32_t flags);
 reach_status reach_solve(reach_ctx* ctx, int32_t method, double eps, int64_t max_iter,
                          int32_t refine_k, const double* x0, double* x_out, int32_t flags,
                          reach_info* info);
+
+/* Strongly connected components of the digraph of A over S? and their levels (§6:
+ * the paper's future work takes the components in reverse topological order).  After
+ * reach_precompute (or reach_system_create).  The decomposition runs on the device
+ * once per system and is kept for REACH_SCC_JACOBI.  label: int32[n?] or NULL, the
+ * component of every S? row (rows in ascending state order, as in A), named by its
+ * largest row index; level: int32[n?] or NULL, the component's level -- 0 when no
+ * edge leaves it, else one above the highest component it has an edge to.  Host or
+ * device memory per flags.  info may be NULL.  max_rounds bounds the colouring rounds
+ * (0 = 256); past it the cyclic core is kept as one block (info->exact = 0).
+ * Synchronises the stream. */
+reach_status reach_scc(reach_ctx* ctx, int32_t* label, int32_t* level, int32_t flags, int32_t max_rounds,
+                       reach_scc_info* info);
 
 /* Autotuner for the row mapping of `method` on the current system (after
  * reach_precompute).  Times every candidate mapping of the method's dominant kernel --

@@ -22,7 +22,7 @@ __all__ = [
     "REACH_OK", "REACH_EINVAL", "REACH_ENOMEM", "REACH_ECUDA", "REACH_ESTATE", "REACH_ENOTCONV",
     "REACH_EBREAKDOWN", "REACH_ETIMEOUT", "REACH_HOST", "REACH_DEVICE", "REACH_PROB01",
     "REACH_PROB0_ONLY", "REACH_JACOBI_FP64", "REACH_JACOBI_MIXED", "REACH_BICGSTAB_FP64",
-    "REACH_JACOBI_SEG",
+    "REACH_JACOBI_SEG", "REACH_SCC_JACOBI", "reach_scc",
     "reach_create", "reach_precompute", "reach_get_classes", "reach_solve", "reach_grad",
     "reach_param_probs", "reach_param_grad_theta", "reach_last_error", "reach_destroy",
     "reach_version", "Solver", "reach_batch_create", "reach_batch_precompute",
@@ -34,13 +34,14 @@ REACH_ENOTCONV, REACH_EBREAKDOWN, REACH_ETIMEOUT = 5, 6, 7
 REACH_HOST, REACH_DEVICE = 0, 1
 REACH_PROB01, REACH_PROB0_ONLY = 0, 1
 REACH_JACOBI_FP64, REACH_JACOBI_MIXED, REACH_BICGSTAB_FP64, REACH_JACOBI_SEG = 0, 1, 2, 3
+REACH_SCC_JACOBI = 4
 
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENOTCONV",
                 6: "EBREAKDOWN", 7: "ETIMEOUT"}
 METHODS = {"jacobi": REACH_JACOBI_FP64, "jacobi_fp64": REACH_JACOBI_FP64,
            "mixed": REACH_JACOBI_MIXED, "jacobi_mixed": REACH_JACOBI_MIXED,
            "bicgstab": REACH_BICGSTAB_FP64, "bicgstab_fp64": REACH_BICGSTAB_FP64,
-           "jacobi_seg": REACH_JACOBI_SEG}
+           "jacobi_seg": REACH_JACOBI_SEG, "scc_jacobi": REACH_SCC_JACOBI}
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "reach.h")
 
 
@@ -55,6 +56,15 @@ class ReachInfo(C.Structure):
                 ("last_delta", C.c_double), ("resid_inf", C.c_double),
                 ("ms_precompute", C.c_double), ("ms_solve", C.c_double),
                 ("bytes_moved", C.c_double), ("status", C.c_int32), ("refinements", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ReachSccInfo(C.Structure):
+    _fields_ = [("n_q", C.c_int64), ("n_scc", C.c_int64), ("n_levels", C.c_int64),
+                ("n_trivial", C.c_int64), ("largest", C.c_int64), ("exact", C.c_int32),
+                ("rounds", C.c_int32), ("ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -83,6 +93,7 @@ _SIGS = {
     "reach_autotune": (_I32, [_P, _I32, C.POINTER(_I32), C.POINTER(_D), C.POINTER(_I32)]),
     "reach_system_create": (_I32, [C.POINTER(_P), _I64, _I64, _P, _P, _P, _P, _I32, _P]),
     "reach_time_kernel": (_I32, [_P, _I32, _I32, C.POINTER(_D)]),
+    "reach_scc": (_I32, [_P, _P, _P, _I32, _I32, C.POINTER(ReachSccInfo)]),
     "reach_jacobi_solve_noalloc": (_I32, [_I64, _P, _P, _P, _P, _P, _D, _I64, _I32, _P,
                                           C.POINTER(_I64), C.POINTER(_D), _P]),
 }
@@ -275,6 +286,30 @@ def reach_autotune(ctx, method=REACH_JACOBI_FP64):
     return {"lanes": lanes.value, "sweep_ms": ms.value, "check_every": k.value}
 
 
+def reach_scc(ctx, labels=True, max_rounds=0, out_label=None, out_level=None):
+    """Strongly connected components of the digraph of A over S? and their levels (§6).
+
+    Returns (label, level, info): label[i] is the largest row index of row i's component
+    and level[i] the component's level in the condensation (int32 over the S? rows in
+    ascending state order); both None when ``labels`` is false.
+    """
+    info = ReachSccInfo()
+    _check(lib().reach_scc(ctx, None, None, REACH_HOST, int(max_rounds), C.byref(info)), ctx)
+    if not labels:
+        return None, None, info.as_dict()
+    nq = info.n_q
+    if out_label is None:
+        out_label = np.empty(nq, np.int32)
+    if out_level is None:
+        out_level = np.empty(nq, np.int32)
+    lp, f1, k1 = _arg(out_label, np.int32, nq, "label")
+    vp, f2, k2 = _arg(out_level, np.int32, nq, "level")
+    if f1 != f2:
+        raise ValueError("label and level must be in the same kind of memory")
+    _check(lib().reach_scc(ctx, lp, vp, f1, int(max_rounds), C.byref(info)), ctx)
+    return out_label, out_level, info.as_dict()
+
+
 KERNELS = {"jacobi64": 0, "sweep32": 1, "resid_hilo": 2, "bicgstab_spmv": 3}
 
 
@@ -324,6 +359,9 @@ class Solver:
 
     def autotune(self, method="jacobi"):
         return reach_autotune(self.ctx, method)
+
+    def scc(self, labels=True, max_rounds=0):
+        return reach_scc(self.ctx, labels, max_rounds)
 
     def close(self):
         if self.ctx:

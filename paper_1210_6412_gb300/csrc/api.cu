@@ -108,15 +108,16 @@ void dfree(T*& p) {
 
 void free_system(reach_ctx* c) {
   dfree(c->a_rowptr); dfree(c->a_col); dfree(c->a_val); dfree(c->a_hi); dfree(c->a_lo); dfree(c->a_col16);
-  dfree(c->d); dfree(c->b); dfree(c->d32); dfree(c->qstate);
-  dfree(c->at_rowptr); dfree(c->at_col); dfree(c->at_val);
+  dfree(c->d); dfree(c->b); dfree(c->a_jv); dfree(c->bj); dfree(c->qstate);
+  dfree(c->at_rowptr); dfree(c->at_col); dfree(c->at_val); dfree(c->at_jv);
   dfree(c->x); dfree(c->x2); dfree(c->vr); dfree(c->vq); dfree(c->vp); dfree(c->vv);
   dfree(c->vs); dfree(c->vt); dfree(c->r32); dfree(c->xf); dfree(c->dl[0]); dfree(c->dl[1]);
   seg_free(c);
+  scc_free(c);
 }
 
 void drop_graphs(reach_ctx* c) {
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < 8; ++i) {
     if (c->g_exec[i]) cudaGraphExecDestroy(c->g_exec[i]);
     c->g_exec[i] = nullptr;
     c->g_key[i] = -1;
@@ -292,6 +293,7 @@ reach_status reach_system_create(reach_ctx** out, int64_t n, int64_t m, const in
   if (e == cudaSuccess) e = cudaMemcpyAsync(&verr, c->verr, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&vrow, c->vrow, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && !verr) e = build_jacobi_form(c);
   if (e == cudaSuccess && !verr) e = alloc_workspace(c);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev1, s);
   if (e == cudaSuccess) e = cudaEventSynchronize(c->ev1);
@@ -328,6 +330,7 @@ reach_status reach_precompute(reach_ctx* c, int32_t mode) {
   if (e == cudaSuccess) e = bfs_backward(c, 0, false);
   if (e == cudaSuccess && mode == REACH_PROB01) e = bfs_backward(c, 1, true);
   if (e == cudaSuccess) e = classify_and_extract(c, mode);
+  if (e == cudaSuccess) e = build_jacobi_form(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "reach_precompute");
   if ((e = alloc_workspace(c)) != cudaSuccess) return cuda_fail(c, e, "reach_precompute: workspace");
   e = cudaEventRecord(c->ev1, s);
@@ -368,7 +371,7 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
                          const double* x0, double* x_out, int32_t flags, reach_info* info) {
   if (!c) return fail(nullptr, REACH_EINVAL, "reach_solve: NULL context");
   if (!c->have_classes) return fail(c, REACH_ESTATE, "reach_solve: call reach_precompute first");
-  if (method < REACH_JACOBI_FP64 || method > REACH_JACOBI_SEG)
+  if (method < REACH_JACOBI_FP64 || method > REACH_SCC_JACOBI)
     return fail(c, REACH_EINVAL, "reach_solve: unknown method");
   if (!(eps > 0.0) || !std::isfinite(eps)) return fail(c, REACH_EINVAL, "reach_solve: eps must be > 0");
   if (max_iter < 1) return fail(c, REACH_EINVAL, "reach_solve: max_iter must be >= 1");
@@ -380,7 +383,7 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
     return fail(c, REACH_EINVAL, "reach_solve: bad output");
   cudaStream_t s = c->stream;
   const char* at = std::getenv("REACH_AUTOTUNE");
-  if (at && at[0] == '1' && c->n_q > 0 && c->tune.gm[method] == 0) {
+  if (at && at[0] == '1' && c->n_q > 0 && method <= REACH_BICGSTAB_FP64 && c->tune.gm[method] == 0) {
     int chosen = 0;
     float ms = 0.f;
     cudaError_t te = autotune(c, method, &chosen, &ms);
@@ -389,7 +392,20 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
   if (refine_k == 16 && refine_k_given == 0 && method == REACH_JACOBI_FP64 && c->tune.k_auto > 0)
     refine_k = c->tune.k_auto;
   c->tune.k = refine_k;
-  const int64_t max_bodies = method == REACH_BICGSTAB_FP64 ? max_iter + 4 : max_iter / refine_k + 4;
+  // level-by-level Jacobi: the decomposition first (it resets the solve state)
+  double ms_scc = 0.0;
+  if (method == REACH_SCC_JACOBI && c->n_q > 0 && !scc_ready(c)) {
+    bool ok = true;
+    cudaError_t de = scc_decompose(c, 256, &ok);
+    if (de != cudaSuccess) return cuda_fail(c, de, "reach_solve: SCC decomposition");
+    if (!ok) return fail(c, REACH_ETIMEOUT, "reach_solve: SCC decomposition loop bound reached");
+    reach_scc_info si;
+    if ((de = scc_outputs(c, nullptr, nullptr, cudaMemcpyDeviceToHost, &si)) != cudaSuccess)
+      return cuda_fail(c, de, "reach_solve: SCC decomposition");
+    ms_scc = si.ms;
+  }
+  const int64_t max_bodies = method == REACH_BICGSTAB_FP64 || method == REACH_SCC_JACOBI
+                                 ? max_iter + 4 : max_iter / refine_k + 4;
   reach_status rs = start_state(c, eps, max_iter, max_bodies);
   if (rs != REACH_OK) return rs;
   cudaError_t e = cudaSuccess;
@@ -404,11 +420,13 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
       x0q = c->x2;
     }
   }
+  double scc_bytes = 0.0;
   if (e == cudaSuccess) e = cudaEventRecord(c->ev0, s);
   if (e == cudaSuccess && c->n_q > 0) {
     if (method == REACH_JACOBI_FP64) e = solve_jacobi64(c, x0q, false);
     else if (method == REACH_JACOBI_MIXED) e = solve_mixed(c, x0q);
     else if (method == REACH_JACOBI_SEG) e = solve_jacobi_seg(c, x0q);
+    else if (method == REACH_SCC_JACOBI) e = solve_scc_jacobi(c, x0q, &scc_bytes);
     else e = solve_bicgstab(c, x0q);
   }
   if (e == cudaSuccess) e = scatter_full(c, c->x, c->xfull);
@@ -427,10 +445,13 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
   }
   const double mq = (double)c->m_q, nq = (double)c->n_q;
   double bytes = 0.0;
-  if (method == REACH_JACOBI_FP64 || method == REACH_JACOBI_SEG) bytes = (double)hs.iter * (mq * 12.0 + nq * 40.0);
-  else if (method == REACH_JACOBI_MIXED)
-    bytes = (double)hs.refinements * (mq * 12.0 + nq * 40.0) +
-            (double)(hs.iter - hs.refinements) * (mq * 8.0 + nq * 24.0);
+  // per sweep, Jacobi form: entries (index + value), rows (rowptr, bj, x read, x' write)
+  const double colb = c->n_q <= 65536 ? 2.0 : 4.0;   // the mixed sweeps use 16-bit indices when they fit
+  if (method == REACH_JACOBI_FP64 || method == REACH_JACOBI_SEG) bytes = (double)hs.iter * (mq * 12.0 + nq * 32.0);
+  else if (method == REACH_JACOBI_MIXED)   // FP64 residual (hi, lo; rowptr, bj, x, xf, r, d0) + FP32 sweeps
+    bytes = (double)hs.refinements * (mq * (8.0 + colb) + nq * 36.0) +
+            (double)(hs.iter - hs.refinements) * (mq * (4.0 + colb) + nq * 16.0);
+  else if (method == REACH_SCC_JACOBI) bytes = scc_bytes;
   else bytes = (double)hs.iter * (2.0 * (mq * 12.0 + nq * 40.0) + nq * 8.0 * 10.0);
   if (info) {
     info->iters = hs.iter;
@@ -439,7 +460,7 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
     info->last_delta = hs.last;
     info->resid_inf = hs.resid;
     info->ms_precompute = c->ms_precompute;
-    info->ms_solve = ms;
+    info->ms_solve = ms + ms_scc;
     info->bytes_moved = bytes;
     info->status = hs.status;
     info->refinements = hs.refinements;
@@ -453,6 +474,25 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
     set_err(c, why);
   }
   return (reach_status)hs.status;
+}
+
+reach_status reach_scc(reach_ctx* c, int32_t* label, int32_t* level, int32_t flags, int32_t max_rounds,
+                       reach_scc_info* info) {
+  if (!c) return fail(nullptr, REACH_EINVAL, "reach_scc: NULL context");
+  if (!c->have_classes) return fail(c, REACH_ESTATE, "reach_scc: call reach_precompute first");
+  if (flags != REACH_HOST && flags != REACH_DEVICE) return fail(c, REACH_EINVAL, "reach_scc: bad flags");
+  if (max_rounds < 0) return fail(c, REACH_EINVAL, "reach_scc: max_rounds must be >= 0");
+  if (max_rounds == 0) max_rounds = 256;
+  if (c->n_q == 0) {
+    if (info) std::memset(info, 0, sizeof(*info)), info->exact = 1;
+    return REACH_OK;
+  }
+  bool ok = true;
+  cudaError_t e = scc_decompose(c, max_rounds, &ok);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reach_scc");
+  if (!ok) return fail(c, REACH_ETIMEOUT, "reach_scc: loop bound reached");
+  e = scc_outputs(c, label, level, kind_from_dev(flags), info);
+  return e == cudaSuccess ? REACH_OK : cuda_fail(c, e, "reach_scc");
 }
 
 reach_status reach_autotune(reach_ctx* c, int32_t method, int32_t* lanes, double* sweep_ms,

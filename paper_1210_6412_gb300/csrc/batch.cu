@@ -160,15 +160,15 @@ __global__ void __launch_bounds__(BT) k_bresid(int64_t n, const int64_t* __restr
       for (int j = 0; j < 8; ++j) {
         if ((j % G) != rg.lane) continue;
         const bool q = (m >> j) & 1u;
-        const double r = q ? acc[j] - ds * X[s * 8 + j] : 0.0;
+        // residual of the Jacobi form (values A_sj / d_s): r_s / d_s
+        const double r = q ? acc[j] - X[s * 8 + j] : 0.0;
         if (REPORT) {
-          mx = fmax(mx, fabs(r));
+          mx = fmax(mx, fabs(ds * r));       // the residual of the system itself
         } else {
-          // absorbing states have d_s = 0 but are never in S?: divide on S? only
-          const double qd = q ? r / ds : 0.0;
-          R[s * 8 + j] = __double2float_rn(r);
-          D1[s * 8 + j] = __double2float_rn(qd);
-          mx = fmax(mx, fabs(qd));
+          const float rf = __double2float_rn(r);
+          R[s * 8 + j] = rf;
+          D1[s * 8 + j] = rf;
+          mx = fmax(mx, fabs(r));
         }
       }
     }
@@ -179,11 +179,12 @@ __global__ void __launch_bounds__(BT) k_bresid(int64_t n, const int64_t* __restr
   if (threadIdx.x == 0) atomic_max_nonneg(&st->slot[slot], a[0]);
 }
 
-// FP32 correction sweep of every right-hand side: D' = (R + A_hi D) / d on S?, 0 elsewhere.
+// FP32 correction sweep of every right-hand side on the Jacobi form (values A_sj / d_s):
+// D' = R + A_hi D on S?, 0 elsewhere.
 template <int G>
 __global__ void __launch_bounds__(BT) k_bsweep(int64_t n, const int64_t* __restrict__ rp,
                                                const int32_t* __restrict__ ci, const float* __restrict__ ah,
-                                               const float* __restrict__ d32, const uint8_t* __restrict__ sq,
+                                               const uint8_t* __restrict__ sq,
                                                const float* __restrict__ R, const float* __restrict__ Din,
                                                float* __restrict__ Dout, const SolveState* st) {
   if (st->done) return;
@@ -211,11 +212,10 @@ __global__ void __launch_bounds__(BT) k_bsweep(int64_t n, const int64_t* __restr
     for (int j = 0; j < 8; ++j) acc[j] = group_sum<G>(acc[j]);
     if (s < n) {
       const unsigned m = sq[s];
-      const float ds = d32[s];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         if ((j % G) != rg.lane) continue;
-        Dout[s * 8 + j] = ((m >> j) & 1u) ? (R[s * 8 + j] + acc[j]) / ds : 0.0f;
+        Dout[s * 8 + j] = ((m >> j) & 1u) ? R[s * 8 + j] + acc[j] : 0.0f;
       }
     }
   }
@@ -283,7 +283,7 @@ template <int G>
 static void l_bsweep(reach_batch* b, const float* din, float* dout, cudaStream_t s) {
   reach_ctx* c = b->base;
   const int grid = grid_rows(c, (const void*)k_bsweep<G>, BT, G, c->n);
-  k_bsweep<G><<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_hi, c->d32, b->sq, b->R, din, dout, c->st);
+  k_bsweep<G><<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_hi, b->sq, b->R, din, dout, c->st);
 }
 
 // Runs one backward fixed point to completion (conditional-while graph or host loop).
@@ -456,6 +456,10 @@ reach_status reach_batch_precompute(reach_batch* b, int32_t mode) {
   // system rows for every state, FP32 hi/lo split (once per batch)
   if (!c->a_rowptr) {
     e = extract_all_rows(c);
+    // the batch has no b (the goal sets enter through X); its Jacobi form divides rows by
+    // d_s, and absorbing rows (d_s = 0) have no off-diagonal entries to divide
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->b, 0, sizeof(double) * (size_t)c->n_q, s);
+    if (e == cudaSuccess) e = build_jacobi_form(c);
     if (e == cudaSuccess) e = split_hilo(c);
     if (e != cudaSuccess) return bcuda(b, e, "reach_batch_precompute: extraction");
   }

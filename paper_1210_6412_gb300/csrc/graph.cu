@@ -478,11 +478,36 @@ __global__ void k_extract_fill(int64_t n, const int64_t* __restrict__ rp, const 
   }
 }
 
-__global__ void k_d32(int64_t nq, const double* __restrict__ d, float* __restrict__ d32) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
-       i += (int64_t)gridDim.x * blockDim.x)
-    d32[i] = __double2float_rn(d[i]);
+// Jacobi form: Aj_ij = A_ij / d_i, bj_i = b_i / d_i (IEEE division, once per system).
+template <int G>
+__global__ void k_jform(int64_t nq, const int64_t* __restrict__ rp, const double* __restrict__ av,
+                        const double* __restrict__ b, const double* __restrict__ d, double* __restrict__ aj,
+                        double* __restrict__ bj) {
+  RowGroups rg = RowGroups::make<G>();
+  for (int64_t i = rg.first; i < nq; i += rg.stride) {
+    const double di = d[i];
+    for (int64_t k = rp[i] + rg.lane; k < rp[i + 1]; k += G) aj[k] = av[k] / di;
+    if (rg.lane == 0 && bj) bj[i] = b[i] / di;
+  }
 }
+
+template <int G>
+static void jform_launch(reach_ctx* c, int64_t nq, const int64_t* rp, const double* av, const double* b,
+                         double* aj, double* bj) {
+  k_jform<G><<<grid_for(c, (const void*)k_jform<G>, 256, nq * G), 256, 0, c->stream>>>(nq, rp, av, b, c->d, aj, bj);
+}
+
+static void jform_dispatch(reach_ctx* c, int g, int64_t nq, const int64_t* rp, const double* av,
+                           const double* b, double* aj, double* bj) {
+  switch (g) {
+    case 2: jform_launch<2>(c, nq, rp, av, b, aj, bj); break;
+    case 4: jform_launch<4>(c, nq, rp, av, b, aj, bj); break;
+    case 8: jform_launch<8>(c, nq, rp, av, b, aj, bj); break;
+    case 16: jform_launch<16>(c, nq, rp, av, b, aj, bj); break;
+    default: jform_launch<32>(c, nq, rp, av, b, aj, bj); break;
+  }
+}
+
 
 template <int G>
 static void extract_launch(reach_ctx* c, int64_t* acnt, int pass) {
@@ -518,6 +543,10 @@ static cudaError_t dmalloc(T** p, int64_t count) {
 
 cudaError_t exclusive_scan_u8(reach_ctx* c, const uint8_t* in, int64_t* out, int64_t n, int64_t* total_dev) {
   return exclusive_scan<uint8_t>(in, out, n, total_dev, reinterpret_cast<int64_t*>(c->part), c->stream);
+}
+
+cudaError_t exclusive_scan_u32(reach_ctx* c, const uint32_t* in, int64_t* out, int64_t n) {
+  return exclusive_scan<uint32_t>(in, out, n, nullptr, reinterpret_cast<int64_t*>(c->part), c->stream);
 }
 
 cudaError_t classify_and_extract(reach_ctx* c, int mode) {
@@ -572,9 +601,10 @@ cudaError_t extract_rows(reach_ctx* c) {
   cudaMemsetAsync(c->a_col + mq, 0, 8 * sizeof(int32_t), s);
   cudaMemsetAsync(c->a_val + mq, 0, 8 * sizeof(double), s);
   if (nq > 0) extract_dispatch(c, g, nullptr, 1);
-  if ((e = dmalloc(&c->d32, nq)) != cudaSuccess) return e;
-  if (nq > 0) k_d32<<<grid_for(c, (const void*)k_d32, 256, nq), 256, 0, s>>>(nq, c->d, c->d32);
-  // the hi/lo split and the transposed system are rebuilt on demand
+  // the Jacobi form, the hi/lo split and the transposed system are rebuilt on demand
+  if (c->a_jv) { cudaFree(c->a_jv); c->a_jv = nullptr; }
+  if (c->bj) { cudaFree(c->bj); c->bj = nullptr; }
+  if (c->at_jv) { cudaFree(c->at_jv); c->at_jv = nullptr; }
   if (c->a_hi) { cudaFree(c->a_hi); c->a_hi = nullptr; }
   if (c->a_lo) { cudaFree(c->a_lo); c->a_lo = nullptr; }
   if (c->a_col16) { cudaFree(c->a_col16); c->a_col16 = nullptr; }
@@ -608,13 +638,24 @@ cudaError_t split_hilo(reach_ctx* c) {
   cudaError_t e;
   if ((e = dmalloc(&c->a_hi, c->m_q + 8)) != cudaSuccess) return e;
   if ((e = dmalloc(&c->a_lo, c->m_q + 8)) != cudaSuccess) return e;
-  const int64_t mm = c->m_q + 8;   // slack entries are zeros of a_val
-  k_split<<<grid_for(c, (const void*)k_split, 256, mm), 256, 0, c->stream>>>(mm, c->a_val, c->a_hi, c->a_lo);
+  const int64_t mm = c->m_q + 8;   // slack entries are zeros of a_jv
+  k_split<<<grid_for(c, (const void*)k_split, 256, mm), 256, 0, c->stream>>>(mm, c->a_jv, c->a_hi, c->a_lo);
   // 16-bit column indices when every S? index fits: 2 bytes less per entry in the sweeps
   if (c->n_q <= 65536 && !c->a_col16) {
     if ((e = dmalloc(&c->a_col16, c->m_q + 8)) != cudaSuccess) return e;
     k_narrow<<<grid_for(c, (const void*)k_narrow, 256, mm), 256, 0, c->stream>>>(mm, c->a_col, c->a_col16);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t build_jacobi_form(reach_ctx* c) {
+  if (c->a_jv && c->bj) return cudaSuccess;
+  const int64_t nq = c->n_q, mq = c->m_q;
+  cudaError_t e;
+  if ((e = dmalloc(&c->a_jv, mq + 8)) != cudaSuccess) return e;
+  if ((e = dmalloc(&c->bj, nq)) != cudaSuccess) return e;
+  cudaMemsetAsync(c->a_jv + mq, 0, 8 * sizeof(double), c->stream);
+  if (nq > 0) jform_dispatch(c, pick_group(nq, mq), nq, c->a_rowptr, c->a_val, c->b, c->a_jv, c->bj);
   return cudaGetLastError();
 }
 
@@ -690,6 +731,10 @@ cudaError_t build_transposed_system(reach_ctx* c) {
     }
     k_tsort<<<grid_for(c, (const void*)k_tsort, 128, nq), 128, 0, s>>>(nq, c->at_rowptr, c->at_col, c->at_val);
   }
+  // Jacobi form of the transposed system: row j scaled by 1 / d_j
+  if ((e = dmalloc(&c->at_jv, mq + 8)) != cudaSuccess) return e;
+  cudaMemsetAsync(c->at_jv + mq, 0, 8 * sizeof(double), s);
+  if (nq > 0) jform_dispatch(c, g, nq, c->at_rowptr, c->at_val, nullptr, c->at_jv, nullptr);
 #undef TF
   return cudaGetLastError();
 }

@@ -108,12 +108,17 @@ struct reach_ctx {
   uint16_t* a_col16 = nullptr;  // a_col narrowed to 16 bits when n? <= 65536 (mixed sweeps)
   double* d = nullptr;
   double* b = nullptr;
-  float* d32 = nullptr;
+  // the Jacobi form of the system: x' = bj + Aj x with Aj_ij = A_ij / d_i, bj_i = b_i / d_i
+  // (one correctly rounded division per entry, once per system, instead of a division
+  // per row in every sweep: FP64 division is a long sequence on the narrow FP64 pipe)
+  double* a_jv = nullptr;
+  double* bj = nullptr;
 
   // transposed system for the adjoint
   int64_t* at_rowptr = nullptr;
   int32_t* at_col = nullptr;
   double* at_val = nullptr;
+  double* at_jv = nullptr;     // its Jacobi form: A_ij / d_j in row j of the transpose
 
   // solve workspace (n_q each)
   double* x = nullptr;
@@ -142,10 +147,12 @@ struct reach_ctx {
   double ms_precompute = 0.0;
 
   // cached solve graphs, keyed by method and shape
-  cudaGraphExec_t g_exec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  int64_t g_key[5] = {-1, -1, -1, -1, -1};
+  // 0-3 solvers, 4 entry-balanced Jacobi, 5-6 SCC decomposition, 7 level-by-level Jacobi
+  cudaGraphExec_t g_exec[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t g_key[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
 
   void* seg = nullptr;      // tile plan of the entry-balanced Jacobi sweep (segscan.cu)
+  void* scc = nullptr;      // components, levels and row order (scc.cu)
 };
 
 namespace reach {
@@ -159,6 +166,7 @@ cudaError_t classify_and_extract(reach_ctx* c, int mode);
 cudaError_t extract_rows(reach_ctx* c);
 cudaError_t extract_all_rows(reach_ctx* c);
 cudaError_t split_hilo(reach_ctx* c);
+cudaError_t build_jacobi_form(reach_ctx* c);
 cudaError_t build_transposed_system(reach_ctx* c);
 
 // ---- solve.cu
@@ -180,8 +188,15 @@ void launch_finalize_resid(cudaStream_t s, SolveState* st);
 // ---- segscan.cu
 cudaError_t solve_jacobi_seg(reach_ctx* c, const double* x0q);
 void seg_free(reach_ctx* c);
-// ---- more of graph.cu / solve.cu used by segscan.cu
+// ---- scc.cu
+cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok);
+cudaError_t scc_outputs(reach_ctx* c, int32_t* label, int32_t* level, cudaMemcpyKind kind, reach_scc_info* info);
+cudaError_t solve_scc_jacobi(reach_ctx* c, const double* x0q, double* bytes_out);
+bool scc_ready(const reach_ctx* c);
+void scc_free(reach_ctx* c);
+// ---- more of graph.cu / solve.cu used by segscan.cu and scc.cu
 cudaError_t exclusive_scan_u8(reach_ctx* c, const uint8_t* in, int64_t* out, int64_t n, int64_t* total_dev);
+cudaError_t exclusive_scan_u32(reach_ctx* c, const uint32_t* in, int64_t* out, int64_t n);
 cudaError_t residual_report(reach_ctx* c, const double* xq);
 
 // ---- shared host helpers (api.cu)

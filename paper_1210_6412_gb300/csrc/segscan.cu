@@ -5,6 +5,7 @@
 // entries whatever the row lengths, so a matrix with a few very long rows keeps every
 // SM busy, where a row-per-warp mapping would leave one warp with a whole long row.
 //
+// The sweep runs on the Jacobi form (Aj = D^-1 A, bj = D^-1 b: x' = bj + Aj x).
 // Per sweep: k_seg_sweep reads each entry once, finishes every row whose entries lie in
 // one tile, and leaves for each tile the sum before its first row end (head) and after
 // its last row end (tail); k_seg_fix completes the rows that span tiles by adding those
@@ -114,7 +115,7 @@ RDEV void seg_scan_cta(double& v, int& f, double* shv, int* shf) {
 
 __global__ void __launch_bounds__(SEG_NT) k_seg_sweep(int64_t mq, int64_t ntiles, const int64_t* __restrict__ rp,
                                                       const int32_t* __restrict__ ci, const double* __restrict__ av,
-                                                      const double* __restrict__ b, const double* __restrict__ d,
+                                                      const double* __restrict__ bj,
                                                       const double* __restrict__ x, double* __restrict__ xn,
                                                       const uint32_t* __restrict__ endbits,
                                                       const int64_t* __restrict__ tile_row0,
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(SEG_NT) k_seg_sweep(int64_t mq, int64_t ntiles
           head_v = run;                          // completed below, after the carry-in
         } else {
           const int64_t r = nonempty[row0 + seen];   // row entirely inside this thread
-          const double xv = (b[r] + run) / d[r];
+          const double xv = bj[r] + run;
           mx = fmax(mx, fabs(xv - x[r]));
           xn[r] = xv;
         }
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(SEG_NT) k_seg_sweep(int64_t mq, int64_t ntiles
       const double first_total = carry + head_v;
       const int64_t r = nonempty[row0];
       if (rp[r] >= t * SEG_T) {                  // the row starts inside this tile: complete
-        const double xv = (b[r] + first_total) / d[r];
+        const double xv = bj[r] + first_total;
         mx = fmax(mx, fabs(xv - x[r]));
         xn[r] = xv;
       } else {                                   // started in an earlier tile: finished by k_seg_fix
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(SEG_NT) k_seg_sweep(int64_t mq, int64_t ntiles
 __global__ void k_seg_fix(int64_t n_span, int64_t n_empty, const int64_t* __restrict__ span,
                           const int64_t* __restrict__ empty, const int64_t* __restrict__ rp,
                           const double* __restrict__ head, const double* __restrict__ tail,
-                          const double* __restrict__ b, const double* __restrict__ d,
+                          const double* __restrict__ bj,
                           const double* __restrict__ x, double* __restrict__ xn, unsigned long long* slot) {
   double mx = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_span + n_empty;
@@ -244,7 +245,7 @@ __global__ void k_seg_fix(int64_t n_span, int64_t n_empty, const int64_t* __rest
     } else {
       r = empty[i - n_span];
     }
-    const double xv = (b[r] + s) / d[r];
+    const double xv = bj[r] + s;
     mx = fmax(mx, fabs(xv - x[r]));
     xn[r] = xv;
   }
@@ -348,13 +349,13 @@ static void seg_sweep(reach_ctx* c, const double* x, double* xn, unsigned long l
   SegPlan* sp = static_cast<SegPlan*>(c->seg);
   if (sp->ntiles > 0) {
     const int grid = (int)std::min<int64_t>(sp->ntiles, grid_for(c, (const void*)k_seg_sweep, SEG_NT, INT64_MAX / 2));
-    k_seg_sweep<<<grid, SEG_NT, 0, s>>>(c->m_q, sp->ntiles, c->a_rowptr, c->a_col, c->a_val, c->b, c->d, x, xn,
+    k_seg_sweep<<<grid, SEG_NT, 0, s>>>(c->m_q, sp->ntiles, c->a_rowptr, c->a_col, c->a_jv, c->bj, x, xn,
                                          sp->endbits, sp->tile_row0, sp->nonempty, sp->head, sp->tail, slot);
   }
   const int64_t rest = sp->n_span + sp->n_empty;
   if (rest > 0)
     k_seg_fix<<<grid_for(c, (const void*)k_seg_fix, 256, rest), 256, 0, s>>>(
-        sp->n_span, sp->n_empty, sp->span, sp->empty, c->a_rowptr, sp->head, sp->tail, c->b, c->d, x, xn, slot);
+        sp->n_span, sp->n_empty, sp->span, sp->empty, c->a_rowptr, sp->head, sp->tail, c->bj, x, xn, slot);
 }
 
 // FP64 Jacobi (§3.1) with the entry-balanced sweep: same iteration and stopping rule as

@@ -171,6 +171,17 @@ RDEV double dot_hilo(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci
 
 RDEV double nan_to_inf(double v) { return v != v ? __longlong_as_double(0x7ff0000000000000LL) : v; }
 
+// |v| as its bit pattern: non-negative doubles order like their bits, so a running
+// max|x' - x| can use integer compares and keep the FP64 pipe for the sums.
+RDEV unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+RDEV unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
+// Back to a double; NaN (bits above +inf) reads as +inf.
+RDEV double bits_to_delta(unsigned long long b) {
+  return __longlong_as_double((long long)(b > 0x7ff0000000000000ull ? 0x7ff0000000000000ull : b));
+}
+
 template <int NV, bool MAX>
 RDEV void cta_to_slot(double v, unsigned long long* slot) {
   __shared__ double sh[32];
@@ -242,25 +253,24 @@ RDEV bool last_cta_reduce(double (&mine)[NS + NM], double* part, unsigned* ticke
 template <int G, bool V>
 __global__ void __launch_bounds__(NT) k_jacobi64(int64_t nq, const int64_t* __restrict__ rp,
                                                  const int32_t* __restrict__ ci,
-                                                 const double* __restrict__ av,
-                                                 const double* __restrict__ b,
-                                                 const double* __restrict__ d,
+                                                 const double* __restrict__ aj,
+                                                 const double* __restrict__ bj,
                                                  const double* __restrict__ x,
                                                  double* __restrict__ xn, unsigned long long* slot, unsigned* ctr) {
   RowGroups rg = RowGroups::make<G>();
-  double mx = 0.0;
+  unsigned long long mx = 0ull;
   auto xf = [x](int32_t j) { return __ldg(x + j); };
   for (int64_t i = row_begin<G>(rg, ctr); warp_has_row<G>(i, nq); i = row_next<G>(rg, ctr, i)) {
     double s = 0.0;
-    if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, av, xf);
+    if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, aj, xf);
     s = group_sum<G>(s);
     if (i < nq && rg.lane == 0) {
-      const double xv = (b[i] + s) / d[i];
-      mx = fmax(mx, nan_to_inf(fabs(xv - x[i])));
+      const double xv = bj[i] + s;       // (b_i + sum A_ij x_j) / d_i in the Jacobi form
+      mx = umax64(mx, abs_bits(xv - x[i]));
       xn[i] = xv;
     }
   }
-  cta_to_slot<1, true>(mx, slot);
+  cta_to_slot<1, true>(bits_to_delta(mx), slot);
 }
 
 // FP64 residual r = b - (I - A) x, max|r| into slot (reported as resid_inf).
@@ -317,25 +327,25 @@ __global__ void k_finalize_resid(SolveState* st) {
 }
 
 // ------------------------------------------------------------------ mixed precision
-// Defect correction around the same Jacobi iteration: the FP64 residual step
-// writes r (FP32) and the first correction sweep d_0 = r / d; FP32 sweeps follow on
-// (I - A) delta = r; then x += delta in FP64.  max|r_i / d_i| is exactly the
-// max|x' - x| of an FP64 Jacobi sweep from x, so the stopping rule matches.
+// Defect correction around the same Jacobi iteration, on the Jacobi form
+// (Aj = D^-1 A, bj = D^-1 b): the FP64 residual step writes r = bj + Aj x - x (FP32),
+// which is also the first correction sweep d_0; FP32 sweeps d <- r + Aj_hi d follow;
+// then x += d in FP64.  max|r_i| is exactly the max|x' - x| of an FP64 Jacobi sweep
+// from x, so the stopping rule matches.
 
 template <int G, bool V, typename IT>
 __global__ void __launch_bounds__(NT) k_resid_hilo(int64_t nq, const int64_t* __restrict__ rp,
                                                    const IT* __restrict__ ci,
                                                    const float* __restrict__ ah,
                                                    const float* __restrict__ al,
-                                                   const double* __restrict__ b,
-                                                   const double* __restrict__ d,
+                                                   const double* __restrict__ bj,
                                                    const double* __restrict__ x,
                                                    const float* __restrict__ xf,
                                                    float* __restrict__ r32, float* __restrict__ dl0,
                                                    SolveState* st, int slot_idx, unsigned* ctr) {
   if (st->done) return;
   RowGroups rg = RowGroups::make<G>();
-  double mx = 0.0;
+  unsigned long long mx = 0ull;
   for (int64_t i = row_begin<G>(rg, ctr); warp_has_row<G>(i, nq); i = row_next<G>(rg, ctr, i)) {
     double s = 0.0;
     float sl = 0.0f;
@@ -343,15 +353,15 @@ __global__ void __launch_bounds__(NT) k_resid_hilo(int64_t nq, const int64_t* __
     s = group_sum<G>(s);
     sl = group_sum<G>(sl);
     if (i < nq && rg.lane == 0) {
-      const double di = d[i];
-      const double r = b[i] + (s + (double)sl) - di * x[i];
-      const double q = r / di;
-      r32[i] = __double2float_rn(r);
-      dl0[i] = __double2float_rn(q);
-      mx = fmax(mx, nan_to_inf(fabs(q)));
+      // residual of the Jacobi form: r_i / d_i = bj_i + (Aj x)_i - x_i
+      const double r = bj[i] + (s + (double)sl) - x[i];
+      const float rf = __double2float_rn(r);
+      r32[i] = rf;
+      dl0[i] = rf;
+      mx = umax64(mx, abs_bits(r));
     }
   }
-  cta_to_slot<1, true>(mx, &st->slot[slot_idx]);
+  cta_to_slot<1, true>(bits_to_delta(mx), &st->slot[slot_idx]);
 }
 
 __global__ void k_check_mixed(SolveState* st, int slot_idx, int k) {
@@ -377,7 +387,6 @@ __global__ void __launch_bounds__(NT) k_sweep32(int64_t nq, const int64_t* __res
                                                 const IT* __restrict__ ci,
                                                 const float* __restrict__ ah,
                                                 const float* __restrict__ r32,
-                                                const float* __restrict__ d32,
                                                 const float* __restrict__ din,
                                                 float* __restrict__ dout, const SolveState* st, unsigned* ctr) {
   if (st->done) return;
@@ -386,8 +395,16 @@ __global__ void __launch_bounds__(NT) k_sweep32(int64_t nq, const int64_t* __res
     float s = 0.0f;
     if (i < nq) s = dot32<G, V, IT, U>(rp[i], rp[i + 1], rg.lane, ci, ah, din);
     s = group_sum<G>(s);
-    if (i < nq && rg.lane == 0) dout[i] = (r32[i] + s) / d32[i];
+    if (i < nq && rg.lane == 0) dout[i] = r32[i] + s;
   }
+}
+
+// out_i = v_i / d_i (the right-hand side of a Jacobi form).
+__global__ void k_div_d(int64_t nq, const double* __restrict__ v, const double* __restrict__ d,
+                        double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = v[i] / d[i];
 }
 
 // x += delta in FP64, and the FP32 copy of x used by the next residual step.
@@ -679,7 +696,7 @@ template <int G, bool V>
 static void l_jacobi(reach_ctx* c, const Sys& y, const double* x, double* xn, unsigned long long* slot,
                      cudaStream_t s, unsigned* ctr = nullptr) {
   const int grid = grid_rows(c, (const void*)k_jacobi64<G, V>, NT, G, y.nq, G == 32 && ctr);
-  k_jacobi64<G, V><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, c->d, x, xn, slot, G == 32 ? ctr : nullptr);
+  k_jacobi64<G, V><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, x, xn, slot, G == 32 ? ctr : nullptr);
 }
 
 template <int G, bool V>
@@ -693,12 +710,12 @@ static void l_resid_hilo(reach_ctx* c, int slot, cudaStream_t s, unsigned* ctr =
   unsigned* cr = G == 32 ? ctr : nullptr;
   if (V && c->a_col16) {
     const int grid = grid_rows(c, (const void*)k_resid_hilo<G, V, uint16_t>, NT, G, c->n_q, cr != nullptr);
-    k_resid_hilo<G, V, uint16_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col16, c->a_hi, c->a_lo, c->b,
-                                                     c->d, c->x, c->xf, c->r32, c->dl[1], c->st, slot, cr);
+    k_resid_hilo<G, V, uint16_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col16, c->a_hi, c->a_lo, c->bj,
+                                                     c->x, c->xf, c->r32, c->dl[1], c->st, slot, cr);
   } else {
     const int grid = grid_rows(c, (const void*)k_resid_hilo<G, V, int32_t>, NT, G, c->n_q, cr != nullptr);
-    k_resid_hilo<G, V, int32_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->a_lo, c->b,
-                                                    c->d, c->x, c->xf, c->r32, c->dl[1], c->st, slot, cr);
+    k_resid_hilo<G, V, int32_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->a_lo, c->bj,
+                                                    c->x, c->xf, c->r32, c->dl[1], c->st, slot, cr);
   }
 }
 
@@ -706,11 +723,11 @@ template <int G, bool V, int U>
 static void l_sweep32_u(reach_ctx* c, const float* din, float* dout, cudaStream_t s, unsigned* cr) {
   if (V && c->a_col16) {
     const int grid = grid_rows(c, (const void*)k_sweep32<G, V, uint16_t, U>, NT, G, c->n_q, cr != nullptr);
-    k_sweep32<G, V, uint16_t, U><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col16, c->a_hi, c->r32, c->d32,
+    k_sweep32<G, V, uint16_t, U><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col16, c->a_hi, c->r32,
                                                      din, dout, c->st, cr);
   } else {
     const int grid = grid_rows(c, (const void*)k_sweep32<G, V, int32_t, U>, NT, G, c->n_q, cr != nullptr);
-    k_sweep32<G, V, int32_t, U><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->r32, c->d32,
+    k_sweep32<G, V, int32_t, U><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->r32,
                                                     din, dout, c->st, cr);
   }
 }
@@ -816,8 +833,13 @@ cudaError_t solve_jacobi64(reach_ctx* c, const double* x0q, bool transposed) {
   double* xb = transposed ? c->vq : c->x2;
   if (x0q) cudaMemcpyAsync(xa, x0q, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
   else cudaMemsetAsync(xa, 0, sizeof(double) * nq, s);
-  Sys y = transposed ? Sys{nq, c->at_rowptr, c->at_col, c->at_val, c->vp}
-                     : Sys{nq, c->a_rowptr, c->a_col, c->a_val, c->b};
+  // the sweep runs on the Jacobi form; the final residual on the system itself
+  if (transposed)
+    k_div_d<<<ew_grid(c, (const void*)k_div_d, nq), NT, 0, s>>>(nq, c->vp, c->d, c->vv);
+  Sys y = transposed ? Sys{nq, c->at_rowptr, c->at_col, c->at_jv, c->vv}
+                     : Sys{nq, c->a_rowptr, c->a_col, c->a_jv, c->bj};
+  Sys yr = transposed ? Sys{nq, c->at_rowptr, c->at_col, c->at_val, c->vp}
+                      : Sys{nq, c->a_rowptr, c->a_col, c->a_val, c->b};
   const Lay L = transposed ? layout(c, nq, c->m_q, -1) : layout(c, nq, c->m_q, REACH_JACOBI_FP64);
   const int k = c->tune.k;
   const int gs = transposed ? 3 : 0;
@@ -831,7 +853,7 @@ cudaError_t solve_jacobi64(reach_ctx* c, const double* x0q, bool transposed) {
                              k_check<<<1, 1, 0, cs>>>(c->st, k - 1, k, k);
                            });
   if (e != cudaSuccess) return e;
-  LAY_DISPATCH(L, l_resid, c, y, xa, s);
+  LAY_DISPATCH(L, l_resid, c, yr, xa, s);
   k_finalize_resid<<<1, 1, 0, s>>>(c->st);
   return cudaGetLastError();
 }
@@ -1012,7 +1034,7 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
   // 66: warp + vector loads with four quads per trip (FP32 sweep only)
   const int codes[7] = {2, 4, 8, 16, 32, 64, 66};
   const double mean = (double)c->m_q / (double)c->n_q;
-  Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_val, c->b};
+  Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_jv, c->bj};   // Jacobi form (the FP64 sweep)
   cudaStream_t s = c->stream;
   float best = 1e30f;
   int pick = 0;
@@ -1078,7 +1100,7 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
   }
   const int method = kernel == 0 ? REACH_JACOBI_FP64 : kernel == 3 ? REACH_BICGSTAB_FP64 : REACH_JACOBI_MIXED;
   const Lay L = layout(c, c->n_q, c->m_q, method);
-  Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_val, c->b};
+  Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_jv, c->bj};   // Jacobi form (the FP64 sweep)
   SolveState hs;
   std::memset(&hs, 0, sizeof(hs));
   hs.eps = 1e-300;

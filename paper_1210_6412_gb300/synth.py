@@ -398,6 +398,40 @@ def skewed_chain(n=20000, zipf_a=1.6, max_deg=64, hubs=8, hub_deg=6000, goal_fra
     return _finish(n, _rowptr(d), col, w, rng, g, s, f"skewed n={n} zipf={zipf_a} hubs={hubs}x{hub_deg}")
 
 
+def cascade_chain(blocks=64, width=4096, dmin=2, dmax=6, p_stay=0.9, goal_frac_last=0.02,
+                  sink_frac=0.01, seed=1210_6412_8):
+    """A chain of strongly connected stages: the shape the SCC order of §6 is meant for.
+
+    States are numbered block by block.  Out-degree is uniform in dmin..dmax; each
+    successor is, with probability ``p_stay``, a uniform state of the same block, else a
+    uniform state of the next block (the last block keeps all its edges).  Weights are
+    U(0,1] normalised.  ``goal_frac_last`` of the last block are goals; ``sink_frac`` of
+    all states are absorbing.  Each block is mostly one large component, and the blocks
+    form a path in the condensation.
+    """
+    rng = np.random.default_rng(seed)
+    n = blocks * width
+    d = rng.integers(dmin, dmax + 1, size=n).astype(np.int64)
+    d = np.minimum(d, width)
+
+    def draw(r, s):
+        r = np.asarray(r, np.int64)
+        blk = r // width
+        stay = (rng.random(r.shape) < p_stay) | (blk == blocks - 1)
+        tb = np.where(stay, blk, blk + 1)
+        return tb * width + rng.integers(0, width, size=r.shape, dtype=np.int64)
+
+    col = _distinct_columns(rng, d, draw)
+    w = 1.0 - rng.random(col.size)
+    last = np.arange((blocks - 1) * width, n)
+    n_goal = max(1, int(round(goal_frac_last * width)))
+    goal_idx = np.sort(rng.choice(last, size=n_goal, replace=False))
+    pool = np.setdiff1d(np.arange(1, n), goal_idx)
+    sink_idx = np.sort(rng.choice(pool, size=int(round(sink_frac * n)), replace=False))
+    return _finish(n, _rowptr(d), col, w, rng, goal_idx, sink_idx,
+                   f"cascade {blocks}x{width} p_stay={p_stay}")
+
+
 def gamblers_ruin(N=20, p=0.4):
     """Random walk on 0..N, up with probability p, down with 1-p; 0 and N absorbing; GS={N}."""
     n = N + 1
