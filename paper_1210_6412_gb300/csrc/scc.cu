@@ -23,6 +23,7 @@
 // max|x' - x| < eps over them.
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 
 #include "common.cuh"
@@ -76,6 +77,9 @@ struct SccPlan {
   int64_t* lbase = nullptr;    // offset of the label inside its level
   uint8_t* lkind = nullptr;    // 1: the level holds a component of more than one row
   int32_t* perm = nullptr;     // position -> row, ordered by level
+  int32_t* rlev = nullptr;     // level of every row
+  double* part = nullptr;      // per-CTA partial maxima of the persistent solve (two sets)
+  unsigned* bar = nullptr;     // grid barrier: arrival count, generation, error flag
   SccState* ss = nullptr;
   bool ready = false;
   reach_scc_info info{};
@@ -514,6 +518,160 @@ __global__ void __launch_bounds__(SCC_NT) k_blk_apply(double* x, const double* _
   }
 }
 
+// ---------------------------------------------------------------- block solve, one persistent launch
+
+// Grid-wide barrier of a cooperative launch (all CTAs resident).  Bounded: a CTA that
+// waits past the limit raises the error word, and every CTA leaves at its next barrier.
+struct GridBar {
+  unsigned* count;
+  unsigned* gen;
+  unsigned* err;
+};
+
+RDEV bool grid_barrier(const GridBar& gb) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = gb.gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(gb.count, 1u) == gridDim.x - 1) {
+      atomicExch(gb.count, 0u);
+      __threadfence();
+      atomicAdd(gb.gen, 1u);
+    } else {
+      unsigned spins = 0;
+      while (*vgen == g) {
+        if (++spins > (1u << 24)) {   // about a second
+          atomicExch(gb.err, 1u);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile unsigned*)gb.err == 0u;
+}
+
+// Level-by-level Jacobi in one cooperative launch: the grid walks the levels in order,
+// with a grid barrier after every sweep instead of a kernel boundary.  A level of
+// single-row components is swept once, in place, into both buffers.  A cyclic level
+// ping-pongs between the buffers until max|x' - x| < eps over its rows; its final
+// values are then copied into the other buffer, so lower levels always read the same in
+// both.  A level with at least a quarter of all rows is swept in natural row order (rows
+// of other levels skipped), so its loads stay coalesced; smaller levels go through perm.
+template <int G>
+__global__ void __launch_bounds__(SCC_NT, 2) k_blk_persist(int64_t nq, const int64_t* __restrict__ arp,
+                                                        const int32_t* __restrict__ acol,
+                                                        const double* __restrict__ aj,
+                                                        const double* __restrict__ bj, double* xa, double* xb,
+                                                        const int32_t* __restrict__ perm,
+                                                        const int32_t* __restrict__ rlev,
+                                                        const int64_t* __restrict__ lrow,
+                                                        const int64_t* __restrict__ lnnz,
+                                                        const uint8_t* __restrict__ lkind, int32_t n_levels,
+                                                        SccState* ss, SolveState* st, double* part, GridBar gb) {
+  __shared__ double sh[32];
+  __shared__ double delta;
+  const double eps = st->eps;
+  const int64_t max_iter = st->max_iter;
+  int64_t iters = 0;
+  double bytes = 0.0, last = 0.0;
+  int32_t status = REACH_OK;
+  RowGroups rg = RowGroups::make<G>();
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gth = (int64_t)gridDim.x * blockDim.x;
+  for (int32_t h = 0; h < n_levels && status == REACH_OK; ++h) {
+    const int64_t r0 = lrow[h], nr = lrow[h + 1] - r0;
+    const bool cyc = lkind[h] != 0;
+    const bool natural = nr * 4 >= nq;
+    const int64_t span = natural ? nq : nr;
+    const double lbytes = (double)lnnz[h] * 12.0 + (double)nr * (cyc ? 48.0 : 44.0) + (natural ? 4.0 * nq : 4.0 * nr);
+    int t = 0;
+    for (;;) {
+      const double* xi = (t & 1) ? xb : xa;
+      double* xo = (t & 1) ? xa : xb;
+      unsigned long long mx = 0ull;
+      for (int64_t i = rg.first; warp_has_row<G>(i, span); i += rg.stride) {
+        int32_t v = 0;
+        bool on = false;
+        if (i < span) {
+          v = natural ? (int32_t)i : perm[r0 + i];
+          on = !natural || rlev[v] == h;
+        }
+        double s0 = 0.0, s1 = 0.0;
+        if (on) {
+          const int64_t hi = arp[v + 1];
+          int64_t k = arp[v] + rg.lane;
+          for (; k + G < hi; k += 2 * G) {
+            s0 = fma(aj[k], xi[acol[k]], s0);
+            s1 = fma(aj[k + G], xi[acol[k + G]], s1);
+          }
+          if (k < hi) s0 = fma(aj[k], xi[acol[k]], s0);
+        }
+        const double sum = group_sum<G>(s0 + s1);
+        if (on && rg.lane == 0) {
+          const double xv = bj[v] + sum;
+          if (cyc) {
+            const double dv = fabs(xv - xi[v]);
+            const unsigned long long bits =
+                dv != dv ? 0x7ff0000000000000ull : (unsigned long long)__double_as_longlong(dv);
+            mx = mx > bits ? mx : bits;
+            xo[v] = xv;
+          } else {
+            xa[v] = xv;          // exact: every column is in a lower, finished level
+            xb[v] = xv;
+          }
+        }
+      }
+      ++iters;
+      bytes += lbytes;
+      if (!cyc) {
+        if (!grid_barrier(gb)) return;
+        break;
+      }
+      double a[1] = {__longlong_as_double((long long)mx)};
+      block_reduce<1, true>(a, sh);
+      if (threadIdx.x == 0) part[(t & 1) * gridDim.x + blockIdx.x] = a[0];
+      if (!grid_barrier(gb)) return;
+      // every CTA forms the same maximum from the partials of this sweep
+      double m = 0.0;
+      for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x)
+        m = fmax(m, __ldcg(part + (t & 1) * gridDim.x + j));
+      a[0] = m;
+      block_reduce<1, true>(a, sh);
+      if (threadIdx.x == 0) delta = a[0];
+      __syncthreads();
+      last = delta;
+      ++t;
+      if (last < eps) break;
+      if (iters >= max_iter) {
+        status = REACH_ENOTCONV;
+        break;
+      }
+    }
+    if (cyc) {
+      // the last sweep wrote buffer (t & 1) ? xb : xa; make the other one agree on this level
+      const double* src = (t & 1) ? xb : xa;
+      double* dst = (t & 1) ? xa : xb;
+      for (int64_t i = gtid; i < nr; i += gth) {
+        const int32_t v = perm[r0 + i];
+        dst[v] = src[v];
+      }
+      bytes += (double)nr * 20.0;
+      if (!grid_barrier(gb)) return;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->iter = iters;
+    st->last = last;
+    st->status = status;
+    st->done = 1;
+    ss->bytes = bytes;
+  }
+}
+
 // ---------------------------------------------------------------- host side
 
 template <typename T>
@@ -527,7 +685,8 @@ void scc_free(reach_ctx* c) {
   SccPlan* sp = static_cast<SccPlan*>(c->scc);
   if (!sp) return;
   void* bufs[] = {sp->lab, sp->color, sp->indeg, sp->outdeg, sp->msize, sp->mstart, sp->mnnz, sp->mem,
-                  sp->lvl, sp->lrows, sp->lrow, sp->lnnz, sp->lfill, sp->lbase, sp->lkind, sp->perm, sp->ss};
+                  sp->lvl, sp->lrows, sp->lrow, sp->lnnz, sp->lfill, sp->lbase, sp->lkind, sp->perm, sp->ss,
+                  sp->rlev, sp->part, sp->bar};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete sp;
@@ -592,6 +751,9 @@ cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok) {
     if ((e = zalloc(&sp->lbase, nq, s)) != cudaSuccess) return e;
     if ((e = zalloc(&sp->lkind, nq + 1, s)) != cudaSuccess) return e;
     if ((e = zalloc(&sp->perm, nq, s)) != cudaSuccess) return e;
+    if ((e = zalloc(&sp->rlev, nq, s)) != cudaSuccess) return e;
+    if ((e = zalloc(&sp->part, 2 * 64 * (int64_t)c->sm_count, s)) != cudaSuccess) return e;
+    if ((e = zalloc(&sp->bar, 4, s)) != cudaSuccess) return e;
     if ((e = zalloc(&sp->ss, 1, s)) != cudaSuccess) return e;
   }
   if ((e = cudaEventRecord(c->ev0, s)) != cudaSuccess) return e;
@@ -678,6 +840,8 @@ cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok) {
   if ((e = exclusive_scan_u32(c, sp->lrows, sp->lrow, nq + 1)) != cudaSuccess) return e;
   k_perm<<<grid_for(c, (const void*)k_perm, SCC_NT, nq), SCC_NT, 0, s>>>(nq, sp->mem, sp->lab, sp->mstart,
                                                                           sp->lvl, sp->lrow, sp->lbase, sp->perm);
+  k_level_of_row<<<grid_for(c, (const void*)k_level_of_row, SCC_NT, nq), SCC_NT, 0, s>>>(nq, sp->lab, sp->lvl,
+                                                                                        sp->rlev);
   if ((e = cudaEventRecord(c->ev1, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(&hs, sp->ss, sizeof(hs), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
@@ -702,14 +866,61 @@ cudaError_t scc_outputs(reach_ctx* c, int32_t* label, int32_t* level, cudaMemcpy
   cudaError_t e = cudaSuccess;
   if (info) *info = sp->info;
   if (label && nq > 0) e = cudaMemcpyAsync(label, sp->lab, sizeof(int32_t) * (size_t)nq, kind, s);
-  if (e == cudaSuccess && level && nq > 0) {
-    int32_t* tmp = reinterpret_cast<int32_t*>(sp->color);     // free after the decomposition
-    k_level_of_row<<<grid_for(c, (const void*)k_level_of_row, SCC_NT, nq), SCC_NT, 0, s>>>(nq, sp->lab, sp->lvl,
-                                                                                          tmp);
-    e = cudaMemcpyAsync(level, tmp, sizeof(int32_t) * (size_t)nq, kind, s);
-  }
+  if (e == cudaSuccess && level && nq > 0)
+    e = cudaMemcpyAsync(level, sp->rlev, sizeof(int32_t) * (size_t)nq, kind, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e;
+}
+
+template <int G>
+static cudaError_t launch_persist(reach_ctx* c, SccPlan* sp) {
+  const void* fn = (const void*)k_blk_persist<G>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SCC_NT, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  // few CTAs per SM keep the grid barrier short; the partials hold up to 64 per SM
+  const int grid = c->sm_count * std::min(per_sm, 4);
+  int64_t nq = c->n_q;
+  int32_t nl = (int32_t)sp->info.n_levels;
+  GridBar gb{sp->bar, sp->bar + 1, sp->bar + 2};
+  void* args[] = {&nq, &c->a_rowptr, &c->a_col, &c->a_jv, &c->bj, &c->x, &c->x2, &sp->perm, &sp->rlev,
+                  &sp->lrow, &sp->lnnz, &sp->lkind, &nl, &sp->ss, &c->st, &sp->part, &gb};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(SCC_NT), args, 0, c->stream);
+}
+
+// One cooperative launch for the whole level-by-level solve.  Returns false (nothing
+// launched) when the device cannot run cooperative launches.
+static cudaError_t solve_scc_persistent(reach_ctx* c, SccPlan* sp, bool* ran) {
+  *ran = false;
+  int coop = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+  if (e != cudaSuccess || !coop) return e;
+  cudaStream_t s = c->stream;
+  const int64_t nq = c->n_q;
+  // x2 starts as a copy of x: a level's first sweep may read lower rows from either
+  cudaMemcpyAsync(c->x2, c->x, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
+  cudaMemsetAsync(sp->bar, 0, 4 * sizeof(unsigned), s);
+  const int g = scc_group(c);
+#define PERSIST(G) e = launch_persist<G>(c, sp)
+  SCC_G_DISPATCH(g, PERSIST)
+#undef PERSIST
+  if (e != cudaSuccess) return e;
+  unsigned err = 0;
+  e = cudaMemcpyAsync(&err, sp->bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  if (err) {   // a barrier gave up: report it through the solve state
+    SolveState hs;
+    e = cudaMemcpy(&hs, c->st, sizeof(hs), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    hs.status = REACH_ETIMEOUT;
+    hs.done = 1;
+    e = cudaMemcpy(c->st, &hs, sizeof(hs), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
+  *ran = true;
+  return cudaSuccess;
 }
 
 cudaError_t solve_scc_jacobi(reach_ctx* c, const double* x0q, double* bytes_out) {
@@ -718,6 +929,20 @@ cudaError_t solve_scc_jacobi(reach_ctx* c, const double* x0q, double* bytes_out)
   SccPlan* sp = static_cast<SccPlan*>(c->scc);
   if (x0q) cudaMemcpyAsync(c->x, x0q, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
   else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
+  const char* gv = std::getenv("REACH_SCC_GRAPH");
+  if (!(gv && gv[0] == '1')) {
+    bool ran = false;
+    cudaError_t pe = solve_scc_persistent(c, sp, &ran);
+    if (pe != cudaSuccess) return pe;
+    if (ran) {
+      if (bytes_out) {
+        pe = cudaMemcpyAsync(bytes_out, &sp->ss->bytes, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (pe == cudaSuccess) pe = cudaStreamSynchronize(s);
+        if (pe != cudaSuccess) return pe;
+      }
+      return residual_report(c, c->x);
+    }
+  }
   {
     int32_t zero[2] = {0, 0};
     cudaMemcpyAsync(&sp->ss->blk_level, zero, sizeof(zero), cudaMemcpyHostToDevice, s);

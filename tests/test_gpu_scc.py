@@ -57,8 +57,13 @@ def test_labels_and_levels_bit_exact(name, host_loops, monkeypatch):
 
 
 @pytest.mark.parametrize("name", sorted(CHAINS))
-def test_level_by_level_jacobi_matches_oracle(name):
+@pytest.mark.parametrize("graph", [False, True])
+def test_level_by_level_jacobi_matches_oracle(name, graph, monkeypatch):
+    """Both drivers of the level loop: one cooperative launch with grid barriers (the
+    default) and the conditional-while graph of sweep + apply (REACH_SCC_GRAPH=1)."""
     need_gpu()
+    if graph:
+        monkeypatch.setenv("REACH_SCC_GRAPH", "1")
     c = CHAINS[name]()
     cls_o, x_o = oracle_solution(c)
     with R.Solver(c.n, c.rowptr, c.col, c.val, c.goal) as s:
@@ -70,10 +75,13 @@ def test_level_by_level_jacobi_matches_oracle(name):
     assert info["iters"] == info2["iters"]
 
 
-def test_sweep_count_matches_oracle_block_jacobi():
+@pytest.mark.parametrize("graph", [False, True])
+def test_sweep_count_matches_oracle_block_jacobi(graph, monkeypatch):
     """Same levels, same stopping rule per level: the sweep counts agree (the oracle spends
     one extra confirming sweep on each level of single-row components)."""
     need_gpu()
+    if graph:
+        monkeypatch.setenv("REACH_SCC_GRAPH", "1")
     c = CHAINS["cascade"]()
     cls = O.partition(c.n, c.rowptr, c.col, c.val, c.goal)
     q, a, b = O.extract_system(c.n, c.rowptr, c.col, c.val, cls)
@@ -194,8 +202,11 @@ def test_empty_system_and_device_outputs():
     assert np.array_equal(lev_d.cpu().numpy(), lev_o)
 
 
-def test_max_iter_bounds_the_level_sweeps():
+@pytest.mark.parametrize("graph", [False, True])
+def test_max_iter_bounds_the_level_sweeps(graph, monkeypatch):
     need_gpu()
+    if graph:
+        monkeypatch.setenv("REACH_SCC_GRAPH", "1")
     c = CHAINS["cascade"]()
     with R.Solver(c.n, c.rowptr, c.col, c.val, c.goal) as s:
         with pytest.raises(R.ReachError) as ei:
