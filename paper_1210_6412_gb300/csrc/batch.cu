@@ -122,55 +122,46 @@ __global__ void k_batch_init_x(int64_t n, const uint8_t* __restrict__ one, doubl
     X[i] = (one[i >> 3] >> (i & 7)) & 1u ? 1.0 : 0.0;
 }
 
-// FP64 residual of every right-hand side with values hi + lo:
-// r_j = sum_{s'} A(s,s') x_j[s'] - d_s x_j[s] on S?_j; first correction r_j / d_s.
-// REPORT: only max|r| into the slot (the true residual after the loop).
-template <int G, bool REPORT>
+// Row mapping of the multi-RHS kernels: 8 lanes own a row, lane j the right-hand side
+// j.  Every lane walks the whole row and reads the same index and value (one request per
+// 8 lanes), and gathers its own column of X: the 8 lanes of a group read one 32-byte
+// (FP32) or 64-byte (FP64) row of X together.  No cross-lane reduction is needed, which
+// matters most in FP64, whose pipe is narrow.
+
+// FP64 residual of every right-hand side on the Jacobi form (values A_sj / d_s, read in
+// FP64): r_j = sum_{s'} Aj(s,s') x_j[s'] - x_j[s] on S?_j, 0 elsewhere; r_j is also the
+// first correction.  REPORT: only max|d_s r_j| (the residual of the system itself) into
+// the slot, after the loop.
+template <bool REPORT>
 __global__ void __launch_bounds__(BT) k_bresid(int64_t n, const int64_t* __restrict__ rp,
-                                               const int32_t* __restrict__ ci,
-                                               const float* __restrict__ ah, const float* __restrict__ al,
+                                               const int32_t* __restrict__ ci, const double* __restrict__ aj,
                                                const double* __restrict__ d, const uint8_t* __restrict__ sq,
                                                const double* __restrict__ X, float* __restrict__ R,
                                                float* __restrict__ D1, SolveState* st, int slot) {
   if (!REPORT && st->done) return;
-  RowGroups rg = RowGroups::make<G>();
+  RowGroups rg = RowGroups::make<8>();
+  const int j = rg.lane;
   double mx = 0.0;
-  for (int64_t s = rg.first; warp_has_row<G>(s, n); s += rg.stride) {
-    double acc[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = 0.0;
-    if (s < n) {
-      for (int64_t k = rp[s] + rg.lane; k < rp[s + 1]; k += G) {
-        const double v = widen(__ldcs(ah + k)) + widen(__ldcs(al + k));
-        const double2* xr = reinterpret_cast<const double2*>(X + (int64_t)__ldcs(ci + k) * 8);
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const double2 t = __ldg(xr + h);
-          acc[2 * h] = fma(v, t.x, acc[2 * h]);
-          acc[2 * h + 1] = fma(v, t.y, acc[2 * h + 1]);
-        }
-      }
+  for (int64_t s = rg.first; s < n; s += rg.stride) {
+    const int64_t hi = rp[s + 1];
+    int64_t k = rp[s];
+    double a0 = 0.0, a1 = 0.0;
+    for (; k + 1 < hi; k += 2) {
+      const int32_t c0 = __ldcs(ci + k), c1 = __ldcs(ci + k + 1);
+      const double v0 = __ldcs(aj + k), v1 = __ldcs(aj + k + 1);
+      a0 = fma(v0, __ldg(X + (int64_t)c0 * 8 + j), a0);
+      a1 = fma(v1, __ldg(X + (int64_t)c1 * 8 + j), a1);
     }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = group_sum<G>(acc[j]);
-    if (s < n) {
-      const unsigned m = sq[s];
-      const double ds = d[s];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        if ((j % G) != rg.lane) continue;
-        const bool q = (m >> j) & 1u;
-        // residual of the Jacobi form (values A_sj / d_s): r_s / d_s
-        const double r = q ? acc[j] - X[s * 8 + j] : 0.0;
-        if (REPORT) {
-          mx = fmax(mx, fabs(ds * r));       // the residual of the system itself
-        } else {
-          const float rf = __double2float_rn(r);
-          R[s * 8 + j] = rf;
-          D1[s * 8 + j] = rf;
-          mx = fmax(mx, fabs(r));
-        }
-      }
+    if (k < hi) a0 = fma(__ldcs(aj + k), __ldg(X + (int64_t)__ldcs(ci + k) * 8 + j), a0);
+    const bool q = (sq[s] >> j) & 1u;
+    const double r = q ? (a0 + a1) - X[s * 8 + j] : 0.0;
+    if (REPORT) {
+      mx = fmax(mx, fabs(d[s] * r));
+    } else {
+      const float rf = __double2float_rn(r);
+      R[s * 8 + j] = rf;
+      D1[s * 8 + j] = rf;
+      mx = fmax(mx, fabs(r));
     }
   }
   __shared__ double sh[32];
@@ -179,45 +170,31 @@ __global__ void __launch_bounds__(BT) k_bresid(int64_t n, const int64_t* __restr
   if (threadIdx.x == 0) atomic_max_nonneg(&st->slot[slot], a[0]);
 }
 
-// FP32 correction sweep of every right-hand side on the Jacobi form (values A_sj / d_s):
-// D' = R + A_hi D on S?, 0 elsewhere.
-template <int G>
+// FP32 correction sweep of every right-hand side on the Jacobi form:
+// D'_j = R_j + sum_{s'} Aj_hi(s,s') D_j[s'] on S?_j, 0 elsewhere.
 __global__ void __launch_bounds__(BT) k_bsweep(int64_t n, const int64_t* __restrict__ rp,
                                                const int32_t* __restrict__ ci, const float* __restrict__ ah,
-                                               const uint8_t* __restrict__ sq,
-                                               const float* __restrict__ R, const float* __restrict__ Din,
-                                               float* __restrict__ Dout, const SolveState* st) {
+                                               const uint8_t* __restrict__ sq, const float* __restrict__ R,
+                                               const float* __restrict__ Din, float* __restrict__ Dout,
+                                               const SolveState* st) {
   if (st->done) return;
-  RowGroups rg = RowGroups::make<G>();
-  for (int64_t s = rg.first; warp_has_row<G>(s, n); s += rg.stride) {
-    float acc[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
-    if (s < n) {
-      for (int64_t k = rp[s] + rg.lane; k < rp[s + 1]; k += G) {
-        const float v = __ldcs(ah + k);
-        const float4* dr = reinterpret_cast<const float4*>(Din + (int64_t)__ldcs(ci + k) * 8);
-        const float4 t0 = __ldg(dr), t1 = __ldg(dr + 1);
-        acc[0] = fmaf(v, t0.x, acc[0]);
-        acc[1] = fmaf(v, t0.y, acc[1]);
-        acc[2] = fmaf(v, t0.z, acc[2]);
-        acc[3] = fmaf(v, t0.w, acc[3]);
-        acc[4] = fmaf(v, t1.x, acc[4]);
-        acc[5] = fmaf(v, t1.y, acc[5]);
-        acc[6] = fmaf(v, t1.z, acc[6]);
-        acc[7] = fmaf(v, t1.w, acc[7]);
-      }
+  RowGroups rg = RowGroups::make<8>();
+  const int j = rg.lane;
+  for (int64_t s = rg.first; s < n; s += rg.stride) {
+    const int64_t hi = rp[s + 1];
+    int64_t k = rp[s];
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    for (; k + 3 < hi; k += 4) {
+      const int32_t c0 = __ldcs(ci + k), c1 = __ldcs(ci + k + 1), c2 = __ldcs(ci + k + 2), c3 = __ldcs(ci + k + 3);
+      const float v0 = __ldcs(ah + k), v1 = __ldcs(ah + k + 1), v2 = __ldcs(ah + k + 2), v3 = __ldcs(ah + k + 3);
+      a0 = fmaf(v0, __ldg(Din + (int64_t)c0 * 8 + j), a0);
+      a1 = fmaf(v1, __ldg(Din + (int64_t)c1 * 8 + j), a1);
+      a2 = fmaf(v2, __ldg(Din + (int64_t)c2 * 8 + j), a2);
+      a3 = fmaf(v3, __ldg(Din + (int64_t)c3 * 8 + j), a3);
     }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = group_sum<G>(acc[j]);
-    if (s < n) {
-      const unsigned m = sq[s];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        if ((j % G) != rg.lane) continue;
-        Dout[s * 8 + j] = ((m >> j) & 1u) ? R[s * 8 + j] + acc[j] : 0.0f;
-      }
-    }
+    for (; k < hi; ++k) a0 = fmaf(__ldcs(ah + k), __ldg(Din + (int64_t)__ldcs(ci + k) * 8 + j), a0);
+    const bool q = (sq[s] >> j) & 1u;
+    Dout[s * 8 + j] = q ? R[s * 8 + j] + ((a0 + a1) + (a2 + a3)) : 0.0f;
   }
 }
 
@@ -265,25 +242,23 @@ static void l_pull(reach_batch* b, uint8_t* bits, const uint8_t* block, cudaStre
                                    b->changed);
 }
 
-template <int G>
 static void l_bresid(reach_batch* b, bool report, cudaStream_t s) {
   reach_ctx* c = b->base;
   if (report) {
-    const int grid = grid_rows(c, (const void*)k_bresid<G, true>, BT, G, c->n);
-    k_bresid<G, true><<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_hi, c->a_lo, c->d, b->sq, b->X,
-                                          b->R, b->D[1], c->st, 63);
+    const int grid = grid_rows(c, (const void*)k_bresid<true>, BT, 8, c->n);
+    k_bresid<true><<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_jv, c->d, b->sq, b->X, b->R, b->D[1],
+                                       c->st, 63);
   } else {
-    const int grid = grid_rows(c, (const void*)k_bresid<G, false>, BT, G, c->n);
-    k_bresid<G, false><<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_hi, c->a_lo, c->d, b->sq,
-                                           b->X, b->R, b->D[1], c->st, 0);
+    const int grid = grid_rows(c, (const void*)k_bresid<false>, BT, 8, c->n);
+    k_bresid<false><<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_jv, c->d, b->sq, b->X, b->R, b->D[1],
+                                        c->st, 0);
   }
 }
 
-template <int G>
 static void l_bsweep(reach_batch* b, const float* din, float* dout, cudaStream_t s) {
   reach_ctx* c = b->base;
-  const int grid = grid_rows(c, (const void*)k_bsweep<G>, BT, G, c->n);
-  k_bsweep<G><<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_hi, b->sq, b->R, din, dout, c->st);
+  const int grid = grid_rows(c, (const void*)k_bsweep, BT, 8, c->n);
+  k_bsweep<<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_hi, b->sq, b->R, din, dout, c->st);
 }
 
 // Runs one backward fixed point to completion (conditional-while graph or host loop).
@@ -542,19 +517,19 @@ reach_status reach_batch_solve(reach_batch* b, double eps, int64_t max_iter, int
   if (e == cudaSuccess) {
     const int64_t key = (n * 1000003LL + c->m_q) * 64 + g * 4 + kref * 1000;
     e = run_loop(c, b->g_exec[2], b->g_key[2], key, [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
-      G_DISPATCH(g, l_bresid, b, false, cs);
+      l_bresid(b, false, cs);
       launch_check_mixed(cs, c->st, 0, kref);
       // kref - 1 FP32 sweeps: D[1] -> D[0] -> ...; kref even, so the last lands in D[0]
       for (int j = 1; j < kref; ++j) {
         const float* din = (j & 1) ? b->D[1] : b->D[0];
         float* dout = (j & 1) ? b->D[0] : b->D[1];
-        G_DISPATCH(g, l_bsweep, b, din, dout, cs);
+        l_bsweep(b, din, dout, cs);
       }
       k_bapply<<<grid_for(c, (const void*)k_bapply, BT, n * 8), BT, 0, cs>>>(n * 8, b->X, b->D[0], c->st);
     });
   }
   if (e == cudaSuccess) {
-    G_DISPATCH(g, l_bresid, b, true, s);
+    l_bresid(b, true, s);
     launch_finalize_resid(s, c->st);
     k_bout<<<grid_for(c, (const void*)k_bout, BT, n * b->k), BT, 0, s>>>(n, b->k, b->X, xdev);
     e = cudaEventRecord(c->ev1, s);

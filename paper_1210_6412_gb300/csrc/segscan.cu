@@ -34,6 +34,7 @@ struct SegPlan {
   int64_t* empty = nullptr;       // rows without entries
   double* head = nullptr;         // per tile
   double* tail = nullptr;         // per tile
+  int64_t* total = nullptr;       // one scan total
 };
 
 // ---- plan construction (once per system)
@@ -287,6 +288,7 @@ void seg_free(reach_ctx* c) {
   cudaFree(sp->empty);
   cudaFree(sp->head);
   cudaFree(sp->tail);
+  cudaFree(sp->total);
   delete sp;
   c->seg = nullptr;
 }
@@ -306,6 +308,7 @@ static cudaError_t seg_plan(reach_ctx* c) {
   cudaError_t e;
   if ((e = salloc(&sp->endbits, words)) != cudaSuccess || (e = salloc(&sp->tile_row0, sp->ntiles)) != cudaSuccess ||
       (e = salloc(&sp->head, sp->ntiles)) != cudaSuccess || (e = salloc(&sp->tail, sp->ntiles)) != cudaSuccess ||
+      (e = salloc(&sp->total, 1)) != cudaSuccess ||
       (e = salloc(&fne, nq)) != cudaSuccess || (e = salloc(&fspan, nq)) != cudaSuccess ||
       (e = salloc(&fempty, nq)) != cudaSuccess || (e = salloc(&pne, nq + 1)) != cudaSuccess ||
       (e = salloc(&pspan, nq + 1)) != cudaSuccess || (e = salloc(&pempty, nq + 1)) != cudaSuccess) {
@@ -317,7 +320,7 @@ static cudaError_t seg_plan(reach_ctx* c) {
   const int g = grid_for(c, (const void*)k_seg_marks, 256, nq);
   k_seg_marks<<<g, 256, 0, s>>>(nq, c->a_rowptr, sp->endbits, fne, fspan, fempty);
   int64_t counts[3] = {0, 0, 0};
-  int64_t* tot = reinterpret_cast<int64_t*>(c->st) + 2;     // scratch words
+  int64_t* tot = sp->total;     // scan totals (never the solve state: a solve may be under way)
   e = exclusive_scan_u8(c, fne, pne, nq, tot);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&counts[0], tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = exclusive_scan_u8(c, fspan, pspan, nq, tot);

@@ -164,6 +164,24 @@ def test_segmented_jacobi_matches_oracle(c1, name):
     assert abs(info["iters"] - ij["iters"]) <= 16 and info["resid_inf"] < 1e-11
 
 
+@pytest.mark.parametrize("name", ["skewed", "random"])
+@pytest.mark.parametrize("method", ["jacobi", "jacobi_seg"])
+def test_fixed_sweep_count_matches_oracle_iterate(c1, name, method):
+    """After exactly 32 sweeps from x = 0 (the first solve of a fresh context, so any
+    setup done inside that solve is covered) the iterate and the last step size match the
+    oracle's Jacobi after 32 sweeps."""
+    c = {"random": lambda: c1, "skewed": lambda: synth.skewed_chain(n=20000, hub_deg=9000)}[name]()
+    cls = O.partition(c.n, c.rowptr, c.col, c.val, c.goal)
+    q, a, b = O.extract_system(c.n, c.rowptr, c.col, c.val, cls)
+    xq, it, delta, ok = O.jacobi(O.system_matrix(a), b, 0.0, 32)
+    need_gpu()
+    with R.Solver(c.n, c.rowptr, c.col, c.val, c.goal) as s:
+        x, info = s.solve(method, eps=1e-300, max_iter=32, refine_k=16, check=False)
+    assert info["status"] == R.REACH_ENOTCONV and info["iters"] == 32
+    assert np.max(np.abs(x[q] - xq)) <= 1e-13
+    assert abs(info["last_delta"] - delta) <= 1e-9 * delta + 1e-15
+
+
 @pytest.mark.parametrize("method,tol", METHODS)
 def test_autotune_then_solve(c1, method, tol):
     """The autotuner's pick (timed on a fresh solve state, even after a finished solve)
