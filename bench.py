@@ -431,6 +431,26 @@ def run_workload(args):
                      "iters": info["iters"], "refinements": info["refinements"],
                      "resid_inf": info["resid_inf"],
                      "alg_GBps": info["bytes_moved"] / info["ms_solve"] / 1e6, "wall_ms": wall})
+        # the same answers from plain FP64 Jacobi, one (chain, goal set) at a time, same eps
+        if args.plain:
+            plain_ms, plain_pre, plain_iters, worst = 0.0, 0.0, 0, 0.0
+            for ci_, ch in enumerate(bt.chains):
+                a_, b_ = int(offs[ci_]), int(offs[ci_ + 1])
+                d_ch = dev(ch.rowptr, ch.col, ch.val)
+                for j in range(goals.shape[0]):
+                    g_ = torch.from_numpy(np.ascontiguousarray(bt.goals[ci_][j])).cuda()
+                    with R.Solver(ch.n, *d_ch, g_, stream=stream.cuda_stream) as sv:
+                        xj, ij = sv.solve("jacobi", eps=1e-8, max_iter=2_000_000)
+                    plain_ms += ij["ms_solve"]
+                    plain_pre += ij["ms_precompute"]
+                    plain_iters += ij["iters"]
+                    worst = max(worst, float(torch.max(torch.abs(torch.as_tensor(xj, device="cuda")
+                                                                 - x[j, a_:b_])).item()))
+            line.update({"plain_fp64_jacobi": {"solve_ms": plain_ms, "precompute_ms": plain_pre,
+                                               "sweeps": plain_iters, "solves": len(bt.chains) * goals.shape[0],
+                                               "max_abs_diff_vs_batched": worst},
+                         "batched_speedup_vs_plain_fp64": (plain_ms + plain_pre) /
+                                                          (info["ms_solve"] + info["ms_precompute"])})
     elif args.workload == "parametric":
         from paper_1210_6412_gb300.autograd import reach_prob
         pc = synth.parametric_chain()
@@ -485,6 +505,8 @@ def main():
                                            "batched", "parametric"],
                     default="dense", help="dense = the benchmark; the others print their own line")
     ap.add_argument("--chains", type=int, default=64, help="--workload batched: number of chains")
+    ap.add_argument("--plain", type=int, default=1,
+                    help="--workload batched: also solve every (chain, goal set) with plain FP64 Jacobi")
     args = ap.parse_args()
     if args.profile:
         return run_profile(args)

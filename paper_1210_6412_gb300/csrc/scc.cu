@@ -80,12 +80,48 @@ struct SccPlan {
   int32_t* rlev = nullptr;     // level of every row
   double* part = nullptr;      // per-CTA partial maxima of the persistent solve (two sets)
   unsigned* bar = nullptr;     // grid barrier: arrival count, generation, error flag
+  unsigned* pc = nullptr;      // counters of the persistent decomposition (frontiers, flags)
   SccState* ss = nullptr;
   bool ready = false;
   reach_scc_info info{};
 };
 
 // ---------------------------------------------------------------- decomposition
+
+// Grid-wide barrier of a cooperative launch (all CTAs resident).  Bounded: a CTA that
+// waits past the limit raises the error word, and every CTA leaves at its next barrier.
+struct GridBar {
+  unsigned* count;
+  unsigned* gen;
+  unsigned* err;
+};
+
+RDEV bool grid_barrier(const GridBar& gb) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = gb.gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(gb.count, 1u) == gridDim.x - 1) {
+      atomicExch(gb.count, 0u);
+      __threadfence();
+      atomicAdd(gb.gen, 1u);
+    } else {
+      unsigned spins = 0;
+      while (*vgen == g) {
+        if (++spins > (1u << 24)) {   // about a second
+          atomicExch(gb.err, 1u);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile unsigned*)gb.err == 0u;
+}
+
 
 RDEV uint32_t push_slot(uint32_t* count) { return atomicAdd(count, 1u); }
 
@@ -260,6 +296,221 @@ __global__ void __launch_bounds__(SCC_NT) k_scc_step(int64_t nq, const int64_t* 
   }
 }
 
+// Queue every member chunk of label L (the chunk is its first position in mem).
+RDEV void push_chunks(int32_t L, const uint32_t* msize, const int64_t* mstart, int32_t* qn, uint32_t* cnext) {
+  const uint32_t nch = (msize[L] + SCC_CHUNK - 1) / SCC_CHUNK;
+  const uint32_t base = atomicAdd(cnext, nch);
+  for (uint32_t j = 0; j < nch; ++j) qn[base + j] = (int32_t)(mstart[L] + (int64_t)j * SCC_CHUNK);
+}
+
+// ---- the same decomposition in cooperative launches (grid barriers between passes)
+//
+// Frontier bookkeeping shared by every queue-driven pass: step f reads the frontier
+// q[f & 1] of size pc[f % 3], pushes into q[(f + 1) & 1] / pc[(f + 1) % 3], and clears
+// pc[(f + 2) % 3] for the step after (that count was last read two barriers earlier).
+// Every CTA reads the same sizes after a barrier, so all of them take the same branches.
+enum : int { PC_CHG = 3, PC_CORE = 6, PC_FAIL = 7 };
+
+RDEV unsigned ld_vol(const unsigned* p) { return *(const volatile unsigned*)p; }
+
+template <int G>
+__global__ void __launch_bounds__(SCC_NT, 2) k_scc_persist(int64_t nq, const int64_t* __restrict__ arp,
+                                                          const int32_t* __restrict__ acol,
+                                                          const int64_t* __restrict__ trp,
+                                                          const int32_t* __restrict__ tcol, int32_t* lab,
+                                                          int32_t* color, uint32_t* indeg, uint32_t* outdeg,
+                                                          int32_t* q0, int32_t* q1, unsigned* pc,
+                                                          int32_t max_rounds, int64_t budget, SccState* ss,
+                                                          GridBar gb) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  RowGroups rg = RowGroups::make<G>();
+  __shared__ int any_change;
+  int64_t f = 0, seen = 0, passes = 0;
+  // step 0: trimming seeds
+  for (int64_t v = tid; v < nq; v += nth) {
+    const uint32_t od = (uint32_t)(arp[v + 1] - arp[v]);
+    const uint32_t id = (uint32_t)(trp[v + 1] - trp[v]);
+    outdeg[v] = od;
+    indeg[v] = id;
+    color[v] = -1;
+    if (od == 0 || id == 0) {
+      lab[v] = (int32_t)v;
+      q1[atomicAdd(pc + 1, 1u)] = (int32_t)v;
+    } else {
+      lab[v] = -1;
+    }
+  }
+  if (lead) pc[2] = 0u;
+  if (!grid_barrier(gb)) return;
+  f = 1;
+  // trimming steps
+  for (;;) {
+    const unsigned size = ld_vol(pc + f % 3);
+    seen += size;
+    if (size == 0 || ++passes > budget) break;
+    const int32_t* qc = (f & 1) ? q1 : q0;
+    int32_t* qn = (f & 1) ? q0 : q1;
+    unsigned* cn = pc + (f + 1) % 3;
+    if (lead) pc[(f + 2) % 3] = 0u;
+    for (int64_t i = rg.first; i < (int64_t)size; i += rg.stride) {
+      const int32_t v = qc[i];
+      for (int64_t k = arp[v] + rg.lane; k < arp[v + 1]; k += G) {
+        const int32_t u = acol[k];
+        if (__ldcg(lab + u) != -1) continue;
+        if (atomicSub(indeg + u, 1u) == 1u && atomicCAS(lab + u, -1, u) == -1) qn[atomicAdd(cn, 1u)] = u;
+      }
+      for (int64_t k = trp[v] + rg.lane; k < trp[v + 1]; k += G) {
+        const int32_t u = tcol[k];
+        if (__ldcg(lab + u) != -1) continue;
+        if (atomicSub(outdeg + u, 1u) == 1u && atomicCAS(lab + u, -1, u) == -1) qn[atomicAdd(cn, 1u)] = u;
+      }
+    }
+    if (!grid_barrier(gb)) return;
+    ++f;
+  }
+  // colouring rounds on the cyclic core
+  int32_t round = 0;
+  bool exact = true;
+  while (seen < nq && passes <= budget) {
+    if (round >= max_rounds) {       // keep the whole core as one block
+      const int32_t core = (int32_t)ld_vol(pc + PC_CORE);
+      for (int64_t v = tid; v < nq; v += nth)
+        if (color[v] >= 0) lab[v] = core;
+      exact = false;
+      if (!grid_barrier(gb)) return;
+      break;
+    }
+    for (int64_t v = tid; v < nq; v += nth) {
+      if (lab[v] != -1) continue;
+      color[v] = (int32_t)v;
+      if (round == 0) atomicMax(reinterpret_cast<int*>(pc + PC_CORE), (int)v);
+    }
+    if (lead) pc[PC_CHG] = 0u;
+    if (!grid_barrier(gb)) return;
+    for (int64_t p = 0;; ++p) {
+      if (threadIdx.x == 0) any_change = 0;
+      __syncthreads();
+      if (lead) pc[PC_CHG + (p + 1) % 3] = 0u;
+      for (int64_t v = rg.first; v < nq; v += rg.stride) {
+        if (__ldcg(lab + v) != -1) continue;
+        const int32_t cv = __ldcg(color + v);
+        for (int64_t k = arp[v] + rg.lane; k < arp[v + 1]; k += G) {
+          const int32_t u = acol[k];
+          if (__ldcg(lab + u) != -1) continue;
+          if (__ldcg(color + u) < cv) {
+            atomicMax(color + u, cv);
+            any_change = 1;
+          }
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0 && any_change) atomicExch(pc + PC_CHG + p % 3, 1u);
+      if (!grid_barrier(gb)) return;
+      if (ld_vol(pc + PC_CHG + p % 3) == 0u || ++passes > budget) break;
+    }
+    // roots seed a frontier (step f); the backward search inside each colour follows
+    {
+      int32_t* qn = (f & 1) ? q0 : q1;
+      unsigned* cn = pc + (f + 1) % 3;
+      if (lead) pc[(f + 2) % 3] = 0u;
+      for (int64_t v = tid; v < nq; v += nth) {
+        if (lab[v] == -1 && color[v] == (int32_t)v) {
+          lab[v] = (int32_t)v;
+          qn[atomicAdd(cn, 1u)] = (int32_t)v;
+        }
+      }
+      if (!grid_barrier(gb)) return;
+      ++f;
+    }
+    for (;;) {
+      const unsigned size = ld_vol(pc + f % 3);
+      seen += size;
+      if (size == 0 || ++passes > budget) break;
+      const int32_t* qc = (f & 1) ? q1 : q0;
+      int32_t* qn = (f & 1) ? q0 : q1;
+      unsigned* cn = pc + (f + 1) % 3;
+      if (lead) pc[(f + 2) % 3] = 0u;
+      for (int64_t i = rg.first; i < (int64_t)size; i += rg.stride) {
+        const int32_t v = qc[i];
+        const int32_t cv = color[v];
+        for (int64_t k = trp[v] + rg.lane; k < trp[v + 1]; k += G) {
+          const int32_t u = tcol[k];
+          if (__ldcg(lab + u) != -1 || __ldcg(color + u) != cv) continue;
+          if (atomicCAS(lab + u, -1, cv) == -1) qn[atomicAdd(cn, 1u)] = u;
+        }
+      }
+      if (!grid_barrier(gb)) return;
+      ++f;
+    }
+    ++round;
+  }
+  if (lead) {
+    ss->round = round;
+    ss->exact = exact ? 1 : 0;
+    ss->core_max = (int32_t)ld_vol(pc + PC_CORE);
+    if (passes > budget) pc[PC_FAIL] = 1u;
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(SCC_NT, 2) k_lvl_persist(int64_t nq, const int64_t* __restrict__ trp,
+                                                          const int32_t* __restrict__ tcol,
+                                                          const int32_t* __restrict__ lab,
+                                                          const uint32_t* __restrict__ msize,
+                                                          const int64_t* __restrict__ mstart,
+                                                          const int32_t* __restrict__ mem, uint32_t* out_edges,
+                                                          int32_t* lvl, int32_t* q0, int32_t* q1, unsigned* pc,
+                                                          SccState* ss, GridBar gb) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  // step 0: components without edges to others are level 0
+  for (int64_t L = tid; L < nq; L += nth) {
+    if (lab[L] != (int32_t)L) continue;
+    const uint32_t sz = msize[L];
+    atomicAdd(reinterpret_cast<unsigned long long*>(&ss->n_scc), 1ull);
+    if (sz == 1) atomicAdd(reinterpret_cast<unsigned long long*>(&ss->n_trivial), 1ull);
+    atomicMax(reinterpret_cast<unsigned long long*>(&ss->largest), (unsigned long long)sz);
+    if (out_edges[L] == 0) {
+      lvl[L] = 0;
+      push_chunks((int32_t)L, msize, mstart, q1, pc + 1);
+    }
+  }
+  if (lead) pc[2] = 0u;
+  if (!grid_barrier(gb)) return;
+  RowGroups rg = RowGroups::make<G>();
+  int64_t f = 1;
+  for (;; ++f) {
+    const unsigned size = ld_vol(pc + f % 3);
+    if (size == 0) break;
+    const int32_t h = (int32_t)(f - 1);
+    const int32_t* qc = (f & 1) ? q1 : q0;
+    int32_t* qn = (f & 1) ? q0 : q1;
+    unsigned* cn = pc + (f + 1) % 3;
+    if (lead) pc[(f + 2) % 3] = 0u;
+    for (int64_t i = rg.first; i < (int64_t)size; i += rg.stride) {
+      const int64_t p0 = qc[i];
+      const int32_t L = lab[mem[p0]];
+      const int64_t p1 = std::min<int64_t>(p0 + SCC_CHUNK, mstart[L] + msize[L]);
+      for (int64_t p = p0; p < p1; ++p) {
+        const int32_t v = mem[p];
+        for (int64_t k = trp[v] + rg.lane; k < trp[v + 1]; k += G) {
+          const int32_t Lu = lab[tcol[k]];
+          if (Lu == L) continue;
+          if (atomicSub(out_edges + Lu, 1u) == 1u) {
+            lvl[Lu] = h + 1;
+            push_chunks(Lu, msize, mstart, qn, cn);
+          }
+        }
+      }
+    }
+    if (!grid_barrier(gb)) return;
+  }
+  if (lead) ss->n_levels = (int32_t)(f - 1);
+}
+
 // Rows per label, stored entries per label, and edges leaving each label.
 template <int G>
 __global__ void __launch_bounds__(SCC_NT) k_lab_stats(int64_t nq, const int64_t* __restrict__ arp,
@@ -290,13 +541,6 @@ __global__ void k_members(int64_t nq, const int32_t* __restrict__ lab, const int
     const int32_t L = lab[v];
     mem[mstart[L] + atomicAdd(fill + L, 1u)] = (int32_t)v;
   }
-}
-
-// Queue every member chunk of label L (the chunk is its first position in mem).
-RDEV void push_chunks(int32_t L, const uint32_t* msize, const int64_t* mstart, int32_t* qn, uint32_t* cnext) {
-  const uint32_t nch = (msize[L] + SCC_CHUNK - 1) / SCC_CHUNK;
-  const uint32_t base = atomicAdd(cnext, nch);
-  for (uint32_t j = 0; j < nch; ++j) qn[base + j] = (int32_t)(mstart[L] + (int64_t)j * SCC_CHUNK);
 }
 
 // Kahn's peeling of the condensation, one level per pass.
@@ -520,40 +764,6 @@ __global__ void __launch_bounds__(SCC_NT) k_blk_apply(double* x, const double* _
 
 // ---------------------------------------------------------------- block solve, one persistent launch
 
-// Grid-wide barrier of a cooperative launch (all CTAs resident).  Bounded: a CTA that
-// waits past the limit raises the error word, and every CTA leaves at its next barrier.
-struct GridBar {
-  unsigned* count;
-  unsigned* gen;
-  unsigned* err;
-};
-
-RDEV bool grid_barrier(const GridBar& gb) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = gb.gen;
-    const unsigned g = *vgen;
-    __threadfence();
-    if (atomicAdd(gb.count, 1u) == gridDim.x - 1) {
-      atomicExch(gb.count, 0u);
-      __threadfence();
-      atomicAdd(gb.gen, 1u);
-    } else {
-      unsigned spins = 0;
-      while (*vgen == g) {
-        if (++spins > (1u << 24)) {   // about a second
-          atomicExch(gb.err, 1u);
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return *(volatile unsigned*)gb.err == 0u;
-}
-
 // Level-by-level Jacobi in one cooperative launch: the grid walks the levels in order,
 // with a grid barrier after every sweep instead of a kernel boundary.  A level of
 // single-row components is swept once, in place, into both buffers.  A cyclic level
@@ -686,7 +896,7 @@ void scc_free(reach_ctx* c) {
   if (!sp) return;
   void* bufs[] = {sp->lab, sp->color, sp->indeg, sp->outdeg, sp->msize, sp->mstart, sp->mnnz, sp->mem,
                   sp->lvl, sp->lrows, sp->lrow, sp->lnnz, sp->lfill, sp->lbase, sp->lkind, sp->perm, sp->ss,
-                  sp->rlev, sp->part, sp->bar};
+                  sp->rlev, sp->part, sp->bar, sp->pc};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete sp;
@@ -724,6 +934,36 @@ static cudaError_t loop_status(reach_ctx* c, int32_t* status) {
   return e;
 }
 
+// Cooperative launches (one resident grid, grid barriers) unless REACH_SCC_GRAPH=1 or the
+// device cannot run them; then the conditional-while graphs.
+static bool use_persistent(reach_ctx* c) {
+  const char* gv = std::getenv("REACH_SCC_GRAPH");
+  if (gv && gv[0] == '1') return false;
+  int coop = 0;
+  return cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device) == cudaSuccess && coop;
+}
+
+template <typename... A>
+static cudaError_t coop_launch(reach_ctx* c, const void* fn, A... a) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SCC_NT, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  const int grid = c->sm_count * std::min(per_sm, 2);
+  void* args[] = {(void*)&a...};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(SCC_NT), args, 0, c->stream);
+}
+
+// REACH_OK, or REACH_ETIMEOUT when a grid barrier gave up or the pass budget ran out.
+static cudaError_t coop_status(reach_ctx* c, SccPlan* sp, int32_t* status) {
+  unsigned w[2] = {0u, 0u};
+  cudaError_t e = cudaMemcpyAsync(&w[0], sp->bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&w[1], sp->pc + PC_FAIL, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  *status = (w[0] || w[1]) ? REACH_ETIMEOUT : REACH_OK;
+  return e;
+}
+
 cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok) {
   *loop_ok = true;
   SccPlan* sp = static_cast<SccPlan*>(c->scc);
@@ -754,6 +994,7 @@ cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok) {
     if ((e = zalloc(&sp->rlev, nq, s)) != cudaSuccess) return e;
     if ((e = zalloc(&sp->part, 2 * 64 * (int64_t)c->sm_count, s)) != cudaSuccess) return e;
     if ((e = zalloc(&sp->bar, 4, s)) != cudaSuccess) return e;
+    if ((e = zalloc(&sp->pc, 16, s)) != cudaSuccess) return e;
     if ((e = zalloc(&sp->ss, 1, s)) != cudaSuccess) return e;
   }
   if ((e = cudaEventRecord(c->ev0, s)) != cudaSuccess) return e;
@@ -785,16 +1026,29 @@ cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok) {
   int32_t* q0 = c->queue;
   int32_t* q1 = c->queue + c->n;
   const int64_t key_base = nq * 7919 + c->m_q;
+  const bool persistent = use_persistent(c);
+  int32_t status = 0;
+  if (persistent) {
+    cudaMemsetAsync(sp->pc, 0, 16 * sizeof(unsigned), s);
+    cudaMemsetAsync(sp->bar, 0, 4 * sizeof(unsigned), s);
+#define SCC_P(G) e = coop_launch(c, (const void*)k_scc_persist<G>, nq, c->a_rowptr, c->a_col, c->at_rowptr,    \
+                                 c->at_col, sp->lab, sp->color, sp->indeg, sp->outdeg, q0, q1, sp->pc,         \
+                                 max_rounds, bound, sp->ss, GridBar{sp->bar, sp->bar + 1, sp->bar + 2})
+    SCC_G_DISPATCH(g, SCC_P)
+#undef SCC_P
+    if (e != cudaSuccess) return e;
+    if ((e = coop_status(c, sp, &status)) != cudaSuccess) return e;
+  } else {
 #define SCC_STEP(G)                                                                                      \
   k_scc_step<G><<<grid, SCC_NT, 0, cs>>>(nq, c->a_rowptr, c->a_col, c->at_rowptr, c->at_col, sp->lab,   \
                                         sp->color, sp->indeg, sp->outdeg, q0, q1, sp->ss, c->st, c->ticket)
-  e = run_loop(c, c->g_exec[5], c->g_key[5], key_base, [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
-    SCC_G_DISPATCH(g, SCC_STEP)
-  });
+    e = run_loop(c, c->g_exec[5], c->g_key[5], key_base, [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
+      SCC_G_DISPATCH(g, SCC_STEP)
+    });
 #undef SCC_STEP
-  if (e != cudaSuccess) return e;
-  int32_t status = 0;
-  if ((e = loop_status(c, &status)) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
+    if ((e = loop_status(c, &status)) != cudaSuccess) return e;
+  }
   if (status != REACH_OK) {
     *loop_ok = false;
     return cudaSuccess;
@@ -813,26 +1067,41 @@ cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok) {
   k_members<<<grid_for(c, (const void*)k_members, SCC_NT, nq), SCC_NT, 0, s>>>(nq, sp->lab, sp->mstart, fill,
                                                                                 sp->mem);
   // levels
-  if ((e = reset_state(c, 2 * nq + 8)) != cudaSuccess) return e;
-  {
+  if (persistent) {
+    cudaMemsetAsync(sp->pc, 0, 16 * sizeof(unsigned), s);
+    cudaMemsetAsync(sp->bar, 0, 4 * sizeof(unsigned), s);
+#define LVL_P(G) e = coop_launch(c, (const void*)k_lvl_persist<G>, nq, c->at_rowptr, c->at_col, sp->lab,     \
+                                 sp->msize, sp->mstart, sp->mem, out_edges, sp->lvl, q0, q1, sp->pc, sp->ss,  \
+                                 GridBar{sp->bar, sp->bar + 1, sp->bar + 2})
+    SCC_G_DISPATCH(g, LVL_P)
+#undef LVL_P
+    if (e != cudaSuccess) return e;
+    if ((e = coop_status(c, sp, &status)) != cudaSuccess) return e;
+    if (status != REACH_OK) {
+      *loop_ok = false;
+      return cudaSuccess;
+    }
+  }
+  if (!persistent) {
+    if ((e = reset_state(c, 2 * nq + 8)) != cudaSuccess) return e;
     // the colouring left ss->phase at PH_LV_INIT with empty frontiers
     int32_t ph = PH_LV_INIT;
     cudaMemcpyAsync(&sp->ss->phase, &ph, sizeof(ph), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(sp->ss->count, 0, sizeof(hs.count), s);
     cudaMemsetAsync(&sp->ss->cur, 0, sizeof(int32_t), s);
-  }
 #define LVL_STEP(G)                                                                                       \
   k_lvl_step<G><<<grid, SCC_NT, 0, cs>>>(nq, c->at_rowptr, c->at_col, sp->lab, sp->msize, sp->mstart,    \
                                         sp->mem, out_edges, sp->lvl, q0, q1, sp->ss, c->st, c->ticket)
-  e = run_loop(c, c->g_exec[6], c->g_key[6], key_base + 1, [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
-    SCC_G_DISPATCH(g, LVL_STEP)
-  });
+    e = run_loop(c, c->g_exec[6], c->g_key[6], key_base + 1, [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
+      SCC_G_DISPATCH(g, LVL_STEP)
+    });
 #undef LVL_STEP
-  if (e != cudaSuccess) return e;
-  if ((e = loop_status(c, &status)) != cudaSuccess) return e;
-  if (status != REACH_OK) {
-    *loop_ok = false;
-    return cudaSuccess;
+    if (e != cudaSuccess) return e;
+    if ((e = loop_status(c, &status)) != cudaSuccess) return e;
+    if (status != REACH_OK) {
+      *loop_ok = false;
+      return cudaSuccess;
+    }
   }
   // order rows by level
   k_level_sizes<<<grid_for(c, (const void*)k_level_sizes, SCC_NT, nq), SCC_NT, 0, s>>>(

@@ -36,10 +36,14 @@ CHAINS = {
 
 
 @pytest.mark.parametrize("name", sorted(CHAINS))
-@pytest.mark.parametrize("host_loops", [False, True])
-def test_labels_and_levels_bit_exact(name, host_loops, monkeypatch):
+@pytest.mark.parametrize("driver", ["persistent", "graph", "host"])
+def test_labels_and_levels_bit_exact(name, driver, monkeypatch):
+    """Three drivers of the same passes: cooperative launches with grid barriers (default),
+    conditional-while graphs (REACH_SCC_GRAPH=1), and host-driven loops."""
     need_gpu()
-    if host_loops:
+    if driver != "persistent":
+        monkeypatch.setenv("REACH_SCC_GRAPH", "1")
+    if driver == "host":
         monkeypatch.setenv("REACH_HOST_LOOPS", "1")
     c = CHAINS[name]()
     a, lab_o, lev_o = _oracle_scc(c)
@@ -118,11 +122,14 @@ def _cycle_chain_system(L):
     return m, b
 
 
-def test_round_cap_merges_the_core_and_still_solves():
+@pytest.mark.parametrize("graph", [False, True])
+def test_round_cap_merges_the_core_and_still_solves(graph, monkeypatch):
     """Past the round cap the cyclic core is kept as one block: the order stays valid
     (every edge leaves a level for a lower one or stays in its block) and the solve is
     unchanged.  Without the cap every cycle is found, one per round."""
     need_gpu()
+    if graph:
+        monkeypatch.setenv("REACH_SCC_GRAPH", "1")
     L = 40
     m, b = _cycle_chain_system(L)
     lab_o = O.scc_labels(m)
