@@ -78,7 +78,7 @@ struct SccPlan {
   uint8_t* lkind = nullptr;    // 1: the level holds a component of more than one row
   int32_t* perm = nullptr;     // position -> row, ordered by level
   int32_t* rlev = nullptr;     // level of every row
-  double* part = nullptr;      // per-CTA partial maxima of the persistent solve (two sets)
+  double* part = nullptr;      // max|x' - x| slots of the persistent solve (three, as integer bits)
   unsigned* bar = nullptr;     // grid barrier: arrival count, generation, error flag
   unsigned* pc = nullptr;      // counters of the persistent decomposition (frontiers, flags)
   SccState* ss = nullptr;
@@ -772,7 +772,7 @@ __global__ void __launch_bounds__(SCC_NT) k_blk_apply(double* x, const double* _
 // both.  A level with at least a quarter of all rows is swept in natural row order (rows
 // of other levels skipped), so its loads stay coalesced; smaller levels go through perm.
 template <int G>
-__global__ void __launch_bounds__(SCC_NT, 2) k_blk_persist(int64_t nq, const int64_t* __restrict__ arp,
+__global__ void __launch_bounds__(SCC_NT, 4) k_blk_persist(int64_t nq, const int64_t* __restrict__ arp,
                                                         const int32_t* __restrict__ acol,
                                                         const double* __restrict__ aj,
                                                         const double* __restrict__ bj, double* xa, double* xb,
@@ -781,14 +781,16 @@ __global__ void __launch_bounds__(SCC_NT, 2) k_blk_persist(int64_t nq, const int
                                                         const int64_t* __restrict__ lrow,
                                                         const int64_t* __restrict__ lnnz,
                                                         const uint8_t* __restrict__ lkind, int32_t n_levels,
-                                                        SccState* ss, SolveState* st, double* part, GridBar gb) {
+                                                        SccState* ss, SolveState* st,
+                                                        unsigned long long* dslot, GridBar gb) {
   __shared__ double sh[32];
-  __shared__ double delta;
   const double eps = st->eps;
   const int64_t max_iter = st->max_iter;
   int64_t iters = 0;
   double bytes = 0.0, last = 0.0;
   int32_t status = REACH_OK;
+  int64_t tc = 0;    // cyclic sweeps so far: max|x' - x| of sweep tc goes to dslot[tc % 3]
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   RowGroups rg = RowGroups::make<G>();
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gth = (int64_t)gridDim.x * blockDim.x;
@@ -841,19 +843,15 @@ __global__ void __launch_bounds__(SCC_NT, 2) k_blk_persist(int64_t nq, const int
         if (!grid_barrier(gb)) return;
         break;
       }
+      // the grid maximum: one integer atomicMax per CTA on the bits of a non-negative
+      // double; the slot two sweeps ahead is cleared (everyone read it a barrier ago)
       double a[1] = {__longlong_as_double((long long)mx)};
       block_reduce<1, true>(a, sh);
-      if (threadIdx.x == 0) part[(t & 1) * gridDim.x + blockIdx.x] = a[0];
+      if (threadIdx.x == 0) atomicMax(dslot + tc % 3, (unsigned long long)__double_as_longlong(a[0]));
+      if (lead) dslot[(tc + 1) % 3] = 0ull;
       if (!grid_barrier(gb)) return;
-      // every CTA forms the same maximum from the partials of this sweep
-      double m = 0.0;
-      for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x)
-        m = fmax(m, __ldcg(part + (t & 1) * gridDim.x + j));
-      a[0] = m;
-      block_reduce<1, true>(a, sh);
-      if (threadIdx.x == 0) delta = a[0];
-      __syncthreads();
-      last = delta;
+      last = __longlong_as_double((long long)*(volatile unsigned long long*)(dslot + tc % 3));
+      ++tc;
       ++t;
       if (last < eps) break;
       if (iters >= max_iter) {
@@ -1153,8 +1151,9 @@ static cudaError_t launch_persist(reach_ctx* c, SccPlan* sp) {
   int64_t nq = c->n_q;
   int32_t nl = (int32_t)sp->info.n_levels;
   GridBar gb{sp->bar, sp->bar + 1, sp->bar + 2};
+  unsigned long long* dslot = reinterpret_cast<unsigned long long*>(sp->part);
   void* args[] = {&nq, &c->a_rowptr, &c->a_col, &c->a_jv, &c->bj, &c->x, &c->x2, &sp->perm, &sp->rlev,
-                  &sp->lrow, &sp->lnnz, &sp->lkind, &nl, &sp->ss, &c->st, &sp->part, &gb};
+                  &sp->lrow, &sp->lnnz, &sp->lkind, &nl, &sp->ss, &c->st, &dslot, &gb};
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(SCC_NT), args, 0, c->stream);
 }
 
@@ -1170,6 +1169,7 @@ static cudaError_t solve_scc_persistent(reach_ctx* c, SccPlan* sp, bool* ran) {
   // x2 starts as a copy of x: a level's first sweep may read lower rows from either
   cudaMemcpyAsync(c->x2, c->x, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
   cudaMemsetAsync(sp->bar, 0, 4 * sizeof(unsigned), s);
+  cudaMemsetAsync(sp->part, 0, 3 * sizeof(unsigned long long), s);
   const int g = scc_group(c);
 #define PERSIST(G) e = launch_persist<G>(c, sp)
   SCC_G_DISPATCH(g, PERSIST)
