@@ -26,6 +26,10 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <cooperative_groups.h>
+
+#include <vector>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -84,6 +88,7 @@ struct SccPlan {
   SccState* ss = nullptr;
   bool ready = false;
   reach_scc_info info{};
+  std::vector<int64_t> h_lrow, h_lnnz;   // level table on the host (plans the launches of a solve)
 };
 
 // ---------------------------------------------------------------- decomposition
@@ -762,17 +767,37 @@ __global__ void __launch_bounds__(SCC_NT) k_blk_apply(double* x, const double* _
   }
 }
 
-// ---------------------------------------------------------------- block solve, one persistent launch
+// ---------------------------------------------------------------- block solve, persistent launches
 
-// Level-by-level Jacobi in one cooperative launch: the grid walks the levels in order,
-// with a grid barrier after every sweep instead of a kernel boundary.  A level of
+constexpr int CL_SIZE = 16;       // CTAs of the cluster that runs small levels (non-portable size)
+constexpr int CL_NT = 512;
+
+// Barrier of the launch: the whole grid (cooperative launch), or one thread-block
+// cluster (hardware barrier with release / acquire semantics at cluster scope).
+template <bool CLUSTER>
+RDEV bool sync_all(const GridBar& gb) {
+  if constexpr (CLUSTER) {
+    cooperative_groups::this_cluster().sync();
+    return true;
+  } else {
+    return grid_barrier(gb);
+  }
+}
+
+// Levels [h0, h1) of the level-by-level Jacobi in one launch: the CTAs walk the levels
+// in order, with a barrier after every sweep instead of a kernel boundary.  Big levels
+// run on the whole GPU (a cooperative grid with grid barriers); runs of small levels, the
+// components §6 expects to differ most from the whole matrix, run on one cluster of 16
+// CTAs, whose hardware barrier costs far less than a grid-wide one.  A level of
 // single-row components is swept once, in place, into both buffers.  A cyclic level
 // ping-pongs between the buffers until max|x' - x| < eps over its rows; its final
 // values are then copied into the other buffer, so lower levels always read the same in
-// both.  A level with at least a quarter of all rows is swept in natural row order (rows
-// of other levels skipped), so its loads stay coalesced; smaller levels go through perm.
-template <int G>
-__global__ void __launch_bounds__(SCC_NT, 4) k_blk_persist(int64_t nq, const int64_t* __restrict__ arp,
+// both.  On the grid, a level with at least a quarter of all rows is swept in natural
+// row order (rows of other levels skipped), so its loads stay coalesced; other levels go
+// through perm.  Sweeps, bytes and the status accumulate in the solve state across
+// launches; a launch whose predecessor stopped returns at once.
+template <int G, bool CLUSTER>
+__global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 4) k_blk_persist(int64_t nq, const int64_t* __restrict__ arp,
                                                         const int32_t* __restrict__ acol,
                                                         const double* __restrict__ aj,
                                                         const double* __restrict__ bj, double* xa, double* xb,
@@ -780,24 +805,25 @@ __global__ void __launch_bounds__(SCC_NT, 4) k_blk_persist(int64_t nq, const int
                                                         const int32_t* __restrict__ rlev,
                                                         const int64_t* __restrict__ lrow,
                                                         const int64_t* __restrict__ lnnz,
-                                                        const uint8_t* __restrict__ lkind, int32_t n_levels,
+                                                        const uint8_t* __restrict__ lkind, int32_t h0, int32_t h1,
                                                         SccState* ss, SolveState* st,
                                                         unsigned long long* dslot, GridBar gb) {
   __shared__ double sh[32];
+  if (st->status != REACH_OK) return;
   const double eps = st->eps;
   const int64_t max_iter = st->max_iter;
-  int64_t iters = 0;
-  double bytes = 0.0, last = 0.0;
+  int64_t iters = st->iter;
+  double bytes = ss->bytes, last = st->last;
   int32_t status = REACH_OK;
   int64_t tc = 0;    // cyclic sweeps so far: max|x' - x| of sweep tc goes to dslot[tc % 3]
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   RowGroups rg = RowGroups::make<G>();
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gth = (int64_t)gridDim.x * blockDim.x;
-  for (int32_t h = 0; h < n_levels && status == REACH_OK; ++h) {
+  for (int32_t h = h0; h < h1 && status == REACH_OK; ++h) {
     const int64_t r0 = lrow[h], nr = lrow[h + 1] - r0;
     const bool cyc = lkind[h] != 0;
-    const bool natural = nr * 4 >= nq;
+    const bool natural = !CLUSTER && nr * 4 >= nq;
     const int64_t span = natural ? nq : nr;
     const double lbytes = (double)lnnz[h] * 12.0 + (double)nr * (cyc ? 48.0 : 44.0) + (natural ? 4.0 * nq : 4.0 * nr);
     int t = 0;
@@ -840,7 +866,7 @@ __global__ void __launch_bounds__(SCC_NT, 4) k_blk_persist(int64_t nq, const int
       ++iters;
       bytes += lbytes;
       if (!cyc) {
-        if (!grid_barrier(gb)) return;
+        if (!sync_all<CLUSTER>(gb)) return;
         break;
       }
       // the grid maximum: one integer atomicMax per CTA on the bits of a non-negative
@@ -849,7 +875,7 @@ __global__ void __launch_bounds__(SCC_NT, 4) k_blk_persist(int64_t nq, const int
       block_reduce<1, true>(a, sh);
       if (threadIdx.x == 0) atomicMax(dslot + tc % 3, (unsigned long long)__double_as_longlong(a[0]));
       if (lead) dslot[(tc + 1) % 3] = 0ull;
-      if (!grid_barrier(gb)) return;
+      if (!sync_all<CLUSTER>(gb)) return;
       last = __longlong_as_double((long long)*(volatile unsigned long long*)(dslot + tc % 3));
       ++tc;
       ++t;
@@ -868,14 +894,13 @@ __global__ void __launch_bounds__(SCC_NT, 4) k_blk_persist(int64_t nq, const int
         dst[v] = src[v];
       }
       bytes += (double)nr * 20.0;
-      if (!grid_barrier(gb)) return;
+      if (!sync_all<CLUSTER>(gb)) return;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (lead) {
     st->iter = iters;
     st->last = last;
     st->status = status;
-    st->done = 1;
     ss->bytes = bytes;
   }
 }
@@ -1114,6 +1139,14 @@ cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok) {
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  sp->h_lrow.assign((size_t)hs.n_levels + 1, 0);
+  sp->h_lnnz.assign((size_t)hs.n_levels + 1, 0);
+  if (hs.n_levels > 0) {
+    e = cudaMemcpy(sp->h_lrow.data(), sp->lrow, sizeof(int64_t) * (size_t)(hs.n_levels + 1), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(sp->h_lnnz.data(), sp->lnnz, sizeof(int64_t) * (size_t)hs.n_levels, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+  }
   sp->info.n_q = nq;
   sp->info.n_scc = hs.n_scc;
   sp->info.n_levels = hs.n_levels;
@@ -1140,24 +1173,78 @@ cudaError_t scc_outputs(reach_ctx* c, int32_t* label, int32_t* level, cudaMemcpy
 }
 
 template <int G>
-static cudaError_t launch_persist(reach_ctx* c, SccPlan* sp) {
-  const void* fn = (const void*)k_blk_persist<G>;
+static cudaError_t launch_grid_run(reach_ctx* c, SccPlan* sp, int32_t h0, int32_t h1) {
+  const void* fn = (const void*)k_blk_persist<G, false>;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SCC_NT, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-  // few CTAs per SM keep the grid barrier short; the partials hold up to 64 per SM
   const int grid = c->sm_count * std::min(per_sm, 4);
   int64_t nq = c->n_q;
-  int32_t nl = (int32_t)sp->info.n_levels;
   GridBar gb{sp->bar, sp->bar + 1, sp->bar + 2};
   unsigned long long* dslot = reinterpret_cast<unsigned long long*>(sp->part);
   void* args[] = {&nq, &c->a_rowptr, &c->a_col, &c->a_jv, &c->bj, &c->x, &c->x2, &sp->perm, &sp->rlev,
-                  &sp->lrow, &sp->lnnz, &sp->lkind, &nl, &sp->ss, &c->st, &dslot, &gb};
+                  &sp->lrow, &sp->lnnz, &sp->lkind, &h0, &h1, &sp->ss, &c->st, &dslot, &gb};
+  cudaMemsetAsync(sp->part, 0, 3 * sizeof(unsigned long long), c->stream);
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(SCC_NT), args, 0, c->stream);
 }
 
-// One cooperative launch for the whole level-by-level solve.  Returns false (nothing
+// Cluster size the device can host for the small-level kernel (16, else 8, else 0).
+template <int G>
+static int cluster_size(reach_ctx* c) {
+  const void* fn = (const void*)k_blk_persist<G, true>;
+  for (int cs : {CL_SIZE, 8}) {
+    if (cs > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(CL_NT);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n > 0) return cs;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+template <int G>
+static cudaError_t launch_cluster_run(reach_ctx* c, SccPlan* sp, int cs, int32_t h0, int32_t h1) {
+  const void* fn = (const void*)k_blk_persist<G, true>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(CL_NT);
+  cfg.stream = c->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int64_t nq = c->n_q;
+  GridBar gb{sp->bar, sp->bar + 1, sp->bar + 2};
+  unsigned long long* dslot = reinterpret_cast<unsigned long long*>(sp->part);
+  void* args[] = {&nq, &c->a_rowptr, &c->a_col, &c->a_jv, &c->bj, &c->x, &c->x2, &sp->perm, &sp->rlev,
+                  &sp->lrow, &sp->lnnz, &sp->lkind, &h0, &h1, &sp->ss, &c->st, &dslot, &gb};
+  cudaMemsetAsync(sp->part, 0, 3 * sizeof(unsigned long long), c->stream);
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+// Bytes one sweep of a level moves below which the level runs on a single cluster: a
+// grid barrier costs a few microseconds, a cluster barrier far less, and 16 SMs stream a
+// few MB from L2 in about the time of one grid barrier.
+constexpr double SMALL_LEVEL_BYTES = 8.0e6;
+
+// The level-by-level solve as a few persistent launches: maximal runs of small levels on
+// one cluster, runs of big levels on the whole grid.  Returns ran = false (nothing
 // launched) when the device cannot run cooperative launches.
 static cudaError_t solve_scc_persistent(reach_ctx* c, SccPlan* sp, bool* ran) {
   *ran = false;
@@ -1166,28 +1253,55 @@ static cudaError_t solve_scc_persistent(reach_ctx* c, SccPlan* sp, bool* ran) {
   if (e != cudaSuccess || !coop) return e;
   cudaStream_t s = c->stream;
   const int64_t nq = c->n_q;
+  const int g = scc_group(c);
+  int cs = 0;
+#define CSIZE(G) cs = cluster_size<G>(c)
+  SCC_G_DISPATCH(g, CSIZE)
+#undef CSIZE
+  const char* cv = std::getenv("REACH_SCC_CLUSTER");
+  if (cv && cv[0] == '0') cs = 0;
   // x2 starts as a copy of x: a level's first sweep may read lower rows from either
   cudaMemcpyAsync(c->x2, c->x, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
   cudaMemsetAsync(sp->bar, 0, 4 * sizeof(unsigned), s);
-  cudaMemsetAsync(sp->part, 0, 3 * sizeof(unsigned long long), s);
-  const int g = scc_group(c);
-#define PERSIST(G) e = launch_persist<G>(c, sp)
-  SCC_G_DISPATCH(g, PERSIST)
-#undef PERSIST
+  {
+    int32_t ok = REACH_OK;
+    double zero = 0.0;
+    cudaMemcpyAsync(&c->st->status, &ok, sizeof(ok), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(&sp->ss->bytes, &zero, sizeof(zero), cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+  }
+  const int32_t nl = (int32_t)sp->info.n_levels;
+  auto small = [&](int32_t h) {
+    const double b = (double)sp->h_lnnz[h] * 12.0 + (double)(sp->h_lrow[h + 1] - sp->h_lrow[h]) * 48.0;
+    return cs > 0 && b <= SMALL_LEVEL_BYTES;
+  };
+  for (int32_t h0 = 0; h0 < nl && e == cudaSuccess;) {
+    const bool sm = small(h0);
+    int32_t h1 = h0 + 1;
+    while (h1 < nl && small(h1) == sm) ++h1;
+#define RUN_C(G) e = launch_cluster_run<G>(c, sp, cs, h0, h1)
+#define RUN_G(G) e = launch_grid_run<G>(c, sp, h0, h1)
+    if (sm) {
+      SCC_G_DISPATCH(g, RUN_C)
+    } else {
+      SCC_G_DISPATCH(g, RUN_G)
+    }
+#undef RUN_C
+#undef RUN_G
+    h0 = h1;
+  }
   if (e != cudaSuccess) return e;
   unsigned err = 0;
   e = cudaMemcpyAsync(&err, sp->bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
-  if (err) {   // a barrier gave up: report it through the solve state
-    SolveState hs;
-    e = cudaMemcpy(&hs, c->st, sizeof(hs), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return e;
-    hs.status = REACH_ETIMEOUT;
-    hs.done = 1;
-    e = cudaMemcpy(c->st, &hs, sizeof(hs), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return e;
-  }
+  SolveState hs;
+  e = cudaMemcpy(&hs, c->st, sizeof(hs), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  if (err) hs.status = REACH_ETIMEOUT;   // a grid barrier gave up
+  hs.done = 1;
+  e = cudaMemcpy(c->st, &hs, sizeof(hs), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
   *ran = true;
   return cudaSuccess;
 }
