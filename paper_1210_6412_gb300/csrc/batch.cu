@@ -122,11 +122,11 @@ __global__ void k_batch_init_x(int64_t n, const uint8_t* __restrict__ one, doubl
     X[i] = (one[i >> 3] >> (i & 7)) & 1u ? 1.0 : 0.0;
 }
 
-// Row mapping of the multi-RHS kernels: 8 lanes own a row, lane j the right-hand side
-// j.  Every lane walks the whole row and reads the same index and value (one request per
-// 8 lanes), and gathers its own column of X: the 8 lanes of a group read one 32-byte
-// (FP32) or 64-byte (FP64) row of X together.  No cross-lane reduction is needed, which
-// matters most in FP64, whose pipe is narrow.
+// Row mapping of the multi-RHS kernels: 2 lanes own a row, lane h the right-hand sides
+// 4h .. 4h+3 (16 rows per warp).  Each lane walks the whole row; per entry the pair reads
+// one 32-byte row of the FP32 D (a float4 each) or one 64-byte row of the FP64 X (two
+// double2 each).  No cross-lane reduction is needed, which matters most in FP64, whose
+// pipe is narrow; 16 rows per warp keep many independent gathers in flight.
 
 // FP64 residual of every right-hand side on the Jacobi form (values A_sj / d_s, read in
 // FP64): r_j = sum_{s'} Aj(s,s') x_j[s'] - x_j[s] on S?_j, 0 elsewhere; r_j is also the
@@ -139,29 +139,34 @@ __global__ void __launch_bounds__(BT) k_bresid(int64_t n, const int64_t* __restr
                                                const double* __restrict__ X, float* __restrict__ R,
                                                float* __restrict__ D1, SolveState* st, int slot) {
   if (!REPORT && st->done) return;
-  RowGroups rg = RowGroups::make<8>();
-  const int j = rg.lane;
+  RowGroups rg = RowGroups::make<2>();
+  const int h = rg.lane;                    // right-hand sides 4h .. 4h+3
   double mx = 0.0;
   for (int64_t s = rg.first; s < n; s += rg.stride) {
     const int64_t hi = rp[s + 1];
-    int64_t k = rp[s];
-    double a0 = 0.0, a1 = 0.0;
-    for (; k + 1 < hi; k += 2) {
-      const int32_t c0 = __ldcs(ci + k), c1 = __ldcs(ci + k + 1);
-      const double v0 = __ldcs(aj + k), v1 = __ldcs(aj + k + 1);
-      a0 = fma(v0, __ldg(X + (int64_t)c0 * 8 + j), a0);
-      a1 = fma(v1, __ldg(X + (int64_t)c1 * 8 + j), a1);
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t k = rp[s]; k < hi; ++k) {
+      const double v = __ldcs(aj + k);
+      const double2* xr = reinterpret_cast<const double2*>(X + (int64_t)__ldcs(ci + k) * 8 + 4 * h);
+      const double2 t0 = __ldg(xr), t1 = __ldg(xr + 1);
+      a[0] = fma(v, t0.x, a[0]);
+      a[1] = fma(v, t0.y, a[1]);
+      a[2] = fma(v, t1.x, a[2]);
+      a[3] = fma(v, t1.y, a[3]);
     }
-    if (k < hi) a0 = fma(__ldcs(aj + k), __ldg(X + (int64_t)__ldcs(ci + k) * 8 + j), a0);
-    const bool q = (sq[s] >> j) & 1u;
-    const double r = q ? (a0 + a1) - X[s * 8 + j] : 0.0;
-    if (REPORT) {
-      mx = fmax(mx, fabs(d[s] * r));
-    } else {
-      const float rf = __double2float_rn(r);
-      R[s * 8 + j] = rf;
-      D1[s * 8 + j] = rf;
-      mx = fmax(mx, fabs(r));
+    const unsigned m = sq[s] >> (4 * h);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t o = s * 8 + 4 * h + q;
+      const double r = ((m >> q) & 1u) ? a[q] - X[o] : 0.0;
+      if (REPORT) {
+        mx = fmax(mx, fabs(d[s] * r));
+      } else {
+        const float rf = __double2float_rn(r);
+        R[o] = rf;
+        D1[o] = rf;
+        mx = fmax(mx, fabs(r));
+      }
     }
   }
   __shared__ double sh[32];
@@ -178,23 +183,33 @@ __global__ void __launch_bounds__(BT) k_bsweep(int64_t n, const int64_t* __restr
                                                const float* __restrict__ Din, float* __restrict__ Dout,
                                                const SolveState* st) {
   if (st->done) return;
-  RowGroups rg = RowGroups::make<8>();
-  const int j = rg.lane;
+  RowGroups rg = RowGroups::make<2>();
+  const int h = rg.lane;                    // right-hand sides 4h .. 4h+3
   for (int64_t s = rg.first; s < n; s += rg.stride) {
     const int64_t hi = rp[s + 1];
     int64_t k = rp[s];
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    for (; k + 3 < hi; k += 4) {
-      const int32_t c0 = __ldcs(ci + k), c1 = __ldcs(ci + k + 1), c2 = __ldcs(ci + k + 2), c3 = __ldcs(ci + k + 3);
-      const float v0 = __ldcs(ah + k), v1 = __ldcs(ah + k + 1), v2 = __ldcs(ah + k + 2), v3 = __ldcs(ah + k + 3);
-      a0 = fmaf(v0, __ldg(Din + (int64_t)c0 * 8 + j), a0);
-      a1 = fmaf(v1, __ldg(Din + (int64_t)c1 * 8 + j), a1);
-      a2 = fmaf(v2, __ldg(Din + (int64_t)c2 * 8 + j), a2);
-      a3 = fmaf(v3, __ldg(Din + (int64_t)c3 * 8 + j), a3);
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    for (; k + 1 < hi; k += 2) {
+      const int32_t c0 = __ldcs(ci + k), c1 = __ldcs(ci + k + 1);
+      const float v0 = __ldcs(ah + k), v1 = __ldcs(ah + k + 1);
+      const float4 t0 = __ldg(reinterpret_cast<const float4*>(Din + (int64_t)c0 * 8) + h);
+      const float4 t1 = __ldg(reinterpret_cast<const float4*>(Din + (int64_t)c1 * 8) + h);
+      a.x = fmaf(v0, t0.x, a.x); a.y = fmaf(v0, t0.y, a.y); a.z = fmaf(v0, t0.z, a.z); a.w = fmaf(v0, t0.w, a.w);
+      b.x = fmaf(v1, t1.x, b.x); b.y = fmaf(v1, t1.y, b.y); b.z = fmaf(v1, t1.z, b.z); b.w = fmaf(v1, t1.w, b.w);
     }
-    for (; k < hi; ++k) a0 = fmaf(__ldcs(ah + k), __ldg(Din + (int64_t)__ldcs(ci + k) * 8 + j), a0);
-    const bool q = (sq[s] >> j) & 1u;
-    Dout[s * 8 + j] = q ? R[s * 8 + j] + ((a0 + a1) + (a2 + a3)) : 0.0f;
+    if (k < hi) {
+      const float v0 = __ldcs(ah + k);
+      const float4 t0 = __ldg(reinterpret_cast<const float4*>(Din + (int64_t)__ldcs(ci + k) * 8) + h);
+      a.x = fmaf(v0, t0.x, a.x); a.y = fmaf(v0, t0.y, a.y); a.z = fmaf(v0, t0.z, a.z); a.w = fmaf(v0, t0.w, a.w);
+    }
+    const unsigned m = sq[s] >> (4 * h);
+    const float4 r = reinterpret_cast<const float4*>(R + s * 8)[h];
+    float4 o;
+    o.x = (m & 1u) ? r.x + (a.x + b.x) : 0.0f;
+    o.y = (m & 2u) ? r.y + (a.y + b.y) : 0.0f;
+    o.z = (m & 4u) ? r.z + (a.z + b.z) : 0.0f;
+    o.w = (m & 8u) ? r.w + (a.w + b.w) : 0.0f;
+    reinterpret_cast<float4*>(Dout + s * 8)[h] = o;
   }
 }
 
@@ -245,11 +260,11 @@ static void l_pull(reach_batch* b, uint8_t* bits, const uint8_t* block, cudaStre
 static void l_bresid(reach_batch* b, bool report, cudaStream_t s) {
   reach_ctx* c = b->base;
   if (report) {
-    const int grid = grid_rows(c, (const void*)k_bresid<true>, BT, 8, c->n);
+    const int grid = grid_rows(c, (const void*)k_bresid<true>, BT, 2, c->n);
     k_bresid<true><<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_jv, c->d, b->sq, b->X, b->R, b->D[1],
                                        c->st, 63);
   } else {
-    const int grid = grid_rows(c, (const void*)k_bresid<false>, BT, 8, c->n);
+    const int grid = grid_rows(c, (const void*)k_bresid<false>, BT, 2, c->n);
     k_bresid<false><<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_jv, c->d, b->sq, b->X, b->R, b->D[1],
                                         c->st, 0);
   }
@@ -257,7 +272,7 @@ static void l_bresid(reach_batch* b, bool report, cudaStream_t s) {
 
 static void l_bsweep(reach_batch* b, const float* din, float* dout, cudaStream_t s) {
   reach_ctx* c = b->base;
-  const int grid = grid_rows(c, (const void*)k_bsweep, BT, 8, c->n);
+  const int grid = grid_rows(c, (const void*)k_bsweep, BT, 2, c->n);
   k_bsweep<<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_hi, b->sq, b->R, din, dout, c->st);
 }
 
