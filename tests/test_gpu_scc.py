@@ -61,13 +61,17 @@ def test_labels_and_levels_bit_exact(name, driver, monkeypatch):
 
 
 @pytest.mark.parametrize("name", sorted(CHAINS))
-@pytest.mark.parametrize("graph", [False, True])
-def test_level_by_level_jacobi_matches_oracle(name, graph, monkeypatch):
-    """Both drivers of the level loop: one cooperative launch with grid barriers (the
-    default) and the conditional-while graph of sweep + apply (REACH_SCC_GRAPH=1)."""
+@pytest.mark.parametrize("driver", ["cluster", "grid", "graph"])
+def test_level_by_level_jacobi_matches_oracle(name, driver, monkeypatch):
+    """Three drivers of the level loop: small levels on one thread-block cluster and big
+    ones on a cooperative grid (default), the cooperative grid for every level
+    (REACH_SCC_CLUSTER=0), and the conditional-while graph of sweep + apply
+    (REACH_SCC_GRAPH=1)."""
     need_gpu()
-    if graph:
+    if driver == "graph":
         monkeypatch.setenv("REACH_SCC_GRAPH", "1")
+    if driver == "grid":
+        monkeypatch.setenv("REACH_SCC_CLUSTER", "0")
     c = CHAINS[name]()
     cls_o, x_o = oracle_solution(c)
     with R.Solver(c.n, c.rowptr, c.col, c.val, c.goal) as s:
