@@ -360,7 +360,8 @@ def _timed_solves(R, torch, n, d_in, mode, eps, methods, stream):
             if meth == "scc_jacobi":   # the decomposition, timed on its own, then the level sweeps
                 _, _, si = R.reach_scc(ctx, labels=False)
                 extra = {"decompose_ms": si["ms"], "n_scc": si["n_scc"], "n_levels": si["n_levels"],
-                         "largest_scc": si["largest"], "exact": si["exact"], "rounds": si["rounds"]}
+                         "largest_scc": si["largest"], "exact": si["exact"], "rounds": si["rounds"],
+                         "passes": si["passes"]}
             _, info = R.reach_solve(ctx, n, meth, eps=eps[meth], max_iter=2_000_000, refine_k=K_REFINE,
                                     out=xo)
             out[meth] = {"ms": info["ms_solve"] + extra.get("decompose_ms", 0.0), "iters": info["iters"],

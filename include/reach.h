@@ -111,6 +111,8 @@ typedef struct {
                            * valid solve order, coarser than the components) */
   int32_t rounds;         /* colouring rounds run */
   double ms;              /* device time of the decomposition */
+  int64_t passes;         /* passes over a frontier or over all rows (trimming, colouring,
+                           * searches and levels): the decomposition's sequential depth */
 } reach_scc_info;
 
 /* Create a context holding a copy of P and the goal mask (§2, §4).

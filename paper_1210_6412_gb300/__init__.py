@@ -64,7 +64,7 @@ class ReachInfo(C.Structure):
 class ReachSccInfo(C.Structure):
     _fields_ = [("n_q", C.c_int64), ("n_scc", C.c_int64), ("n_levels", C.c_int64),
                 ("n_trivial", C.c_int64), ("largest", C.c_int64), ("exact", C.c_int32),
-                ("rounds", C.c_int32), ("ms", C.c_double)]
+                ("rounds", C.c_int32), ("ms", C.c_double), ("passes", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

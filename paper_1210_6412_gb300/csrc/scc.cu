@@ -62,6 +62,7 @@ struct SccState {
   int32_t pad2;
   int64_t blk_sweeps;     // sweeps of the current level
   double bytes;           // algorithmic bytes of the sweeps run
+  int64_t passes;         // passes of the decomposition (its sequential depth)
 };
 
 struct SccPlan {
@@ -455,6 +456,7 @@ __global__ void __launch_bounds__(SCC_NT, 2) k_scc_persist(int64_t nq, const int
     ss->round = round;
     ss->exact = exact ? 1 : 0;
     ss->core_max = (int32_t)ld_vol(pc + PC_CORE);
+    ss->passes = passes;
     if (passes > budget) pc[PC_FAIL] = 1u;
   }
 }
@@ -513,7 +515,10 @@ __global__ void __launch_bounds__(SCC_NT, 2) k_lvl_persist(int64_t nq, const int
     }
     if (!grid_barrier(gb)) return;
   }
-  if (lead) ss->n_levels = (int32_t)(f - 1);
+  if (lead) {
+    ss->n_levels = (int32_t)(f - 1);
+    ss->passes += f;
+  }
 }
 
 // Rows per label, stored entries per label, and edges leaving each label.
@@ -951,6 +956,16 @@ static cudaError_t reset_state(reach_ctx* c, int64_t max_bodies) {
   return e;
 }
 
+// Adds the loop bodies the last graph-driven stage ran to the pass count.
+static cudaError_t add_bodies(reach_ctx* c, SccPlan* sp) {
+  int64_t bodies = 0, prev = 0;
+  cudaError_t e = cudaMemcpy(&bodies, &c->st->bodies, sizeof(int64_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&prev, &sp->ss->passes, sizeof(int64_t), cudaMemcpyDeviceToHost);
+  prev += bodies;
+  if (e == cudaSuccess) e = cudaMemcpy(&sp->ss->passes, &prev, sizeof(int64_t), cudaMemcpyHostToDevice);
+  return e;
+}
+
 static cudaError_t loop_status(reach_ctx* c, int32_t* status) {
   cudaError_t e = cudaMemcpyAsync(status, &c->st->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -1071,6 +1086,7 @@ cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok) {
 #undef SCC_STEP
     if (e != cudaSuccess) return e;
     if ((e = loop_status(c, &status)) != cudaSuccess) return e;
+    if ((e = add_bodies(c, sp)) != cudaSuccess) return e;
   }
   if (status != REACH_OK) {
     *loop_ok = false;
@@ -1121,6 +1137,7 @@ cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok) {
 #undef LVL_STEP
     if (e != cudaSuccess) return e;
     if ((e = loop_status(c, &status)) != cudaSuccess) return e;
+    if ((e = add_bodies(c, sp)) != cudaSuccess) return e;
     if (status != REACH_OK) {
       *loop_ok = false;
       return cudaSuccess;
@@ -1154,6 +1171,7 @@ cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok) {
   sp->info.largest = hs.largest;
   sp->info.exact = hs.exact;
   sp->info.rounds = hs.round;
+  sp->info.passes = hs.passes;
   sp->info.ms = ms;
   sp->ready = true;
   return cudaGetLastError();
@@ -1238,10 +1256,12 @@ static cudaError_t launch_cluster_run(reach_ctx* c, SccPlan* sp, int cs, int32_t
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-// Bytes one sweep of a level moves below which the level runs on a single cluster: a
-// grid barrier costs a few microseconds, a cluster barrier far less, and 16 SMs stream a
-// few MB from L2 in about the time of one grid barrier.
-constexpr double SMALL_LEVEL_BYTES = 8.0e6;
+// Bytes one sweep of a level moves below which the level runs on a single cluster.
+// Measured per sweep: a cluster of 16 CTAs costs about 1.3 us + rows / 1100 per us (its
+// 16 SMs are latency-bound on the dependent loads of a row), the cooperative grid about
+// 5 us + rows / 9000 per us (the grid barrier dominates); they cross near 4,600 rows,
+// about 0.35 MB of a sparse level.
+constexpr double SMALL_LEVEL_BYTES = 0.35e6;
 
 // The level-by-level solve as a few persistent launches: maximal runs of small levels on
 // one cluster, runs of big levels on the whole grid.  Returns ran = false (nothing
