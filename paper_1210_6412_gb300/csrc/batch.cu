@@ -122,16 +122,15 @@ __global__ void k_batch_init_x(int64_t n, const uint8_t* __restrict__ one, doubl
     X[i] = (one[i >> 3] >> (i & 7)) & 1u ? 1.0 : 0.0;
 }
 
-// Row mapping of the multi-RHS kernels: 2 lanes own a row, lane h the right-hand sides
-// 4h .. 4h+3 (16 rows per warp).  Each lane walks the whole row; per entry the pair reads
-// one 32-byte row of the FP32 D (a float4 each) or one 64-byte row of the FP64 X (two
-// double2 each).  No cross-lane reduction is needed, which matters most in FP64, whose
-// pipe is narrow; 16 rows per warp keep many independent gathers in flight.
+// Row mapping of the multi-RHS kernels: a group of lanes owns a row and each lane owns
+// some of the right-hand sides, so every lane walks the whole row and no cross-lane
+// reduction is needed (which matters most in FP64, whose pipe is narrow).
 
 // FP64 residual of every right-hand side on the Jacobi form (values A_sj / d_s, read in
 // FP64): r_j = sum_{s'} Aj(s,s') x_j[s'] - x_j[s] on S?_j, 0 elsewhere; r_j is also the
 // first correction.  REPORT: only max|d_s r_j| (the residual of the system itself) into
-// the slot, after the loop.
+// the slot, after the loop.  Two lanes own a row, lane h the right-hand sides 4h .. 4h+3,
+// gathering two double2 of the 64-byte row of X per entry.
 template <bool REPORT>
 __global__ void __launch_bounds__(BT) k_bresid(int64_t n, const int64_t* __restrict__ rp,
                                                const int32_t* __restrict__ ci, const double* __restrict__ aj,
@@ -176,40 +175,33 @@ __global__ void __launch_bounds__(BT) k_bresid(int64_t n, const int64_t* __restr
 }
 
 // FP32 correction sweep of every right-hand side on the Jacobi form:
-// D'_j = R_j + sum_{s'} Aj_hi(s,s') D_j[s'] on S?_j, 0 elsewhere.
+// D'_j = R_j + sum_{s'} Aj_hi(s,s') D_j[s'] on S?_j, 0 elsewhere.  Here 8 lanes own a row,
+// lane j the right-hand side j, so the 8 lanes gather one 32-byte row of D together.  (Two
+// lanes with a float4 each ran at the same speed but doubled the DRAM traffic: more rows
+// in flight per warp spread the gathers over more of D and L2 kept less of it.)
 __global__ void __launch_bounds__(BT) k_bsweep(int64_t n, const int64_t* __restrict__ rp,
                                                const int32_t* __restrict__ ci, const float* __restrict__ ah,
                                                const uint8_t* __restrict__ sq, const float* __restrict__ R,
                                                const float* __restrict__ Din, float* __restrict__ Dout,
                                                const SolveState* st) {
   if (st->done) return;
-  RowGroups rg = RowGroups::make<2>();
-  const int h = rg.lane;                    // right-hand sides 4h .. 4h+3
+  RowGroups rg = RowGroups::make<8>();
+  const int j = rg.lane;
   for (int64_t s = rg.first; s < n; s += rg.stride) {
     const int64_t hi = rp[s + 1];
     int64_t k = rp[s];
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-    for (; k + 1 < hi; k += 2) {
-      const int32_t c0 = __ldcs(ci + k), c1 = __ldcs(ci + k + 1);
-      const float v0 = __ldcs(ah + k), v1 = __ldcs(ah + k + 1);
-      const float4 t0 = __ldg(reinterpret_cast<const float4*>(Din + (int64_t)c0 * 8) + h);
-      const float4 t1 = __ldg(reinterpret_cast<const float4*>(Din + (int64_t)c1 * 8) + h);
-      a.x = fmaf(v0, t0.x, a.x); a.y = fmaf(v0, t0.y, a.y); a.z = fmaf(v0, t0.z, a.z); a.w = fmaf(v0, t0.w, a.w);
-      b.x = fmaf(v1, t1.x, b.x); b.y = fmaf(v1, t1.y, b.y); b.z = fmaf(v1, t1.z, b.z); b.w = fmaf(v1, t1.w, b.w);
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    for (; k + 3 < hi; k += 4) {
+      const int32_t c0 = __ldcs(ci + k), c1 = __ldcs(ci + k + 1), c2 = __ldcs(ci + k + 2), c3 = __ldcs(ci + k + 3);
+      const float v0 = __ldcs(ah + k), v1 = __ldcs(ah + k + 1), v2 = __ldcs(ah + k + 2), v3 = __ldcs(ah + k + 3);
+      a0 = fmaf(v0, __ldg(Din + (int64_t)c0 * 8 + j), a0);
+      a1 = fmaf(v1, __ldg(Din + (int64_t)c1 * 8 + j), a1);
+      a2 = fmaf(v2, __ldg(Din + (int64_t)c2 * 8 + j), a2);
+      a3 = fmaf(v3, __ldg(Din + (int64_t)c3 * 8 + j), a3);
     }
-    if (k < hi) {
-      const float v0 = __ldcs(ah + k);
-      const float4 t0 = __ldg(reinterpret_cast<const float4*>(Din + (int64_t)__ldcs(ci + k) * 8) + h);
-      a.x = fmaf(v0, t0.x, a.x); a.y = fmaf(v0, t0.y, a.y); a.z = fmaf(v0, t0.z, a.z); a.w = fmaf(v0, t0.w, a.w);
-    }
-    const unsigned m = sq[s] >> (4 * h);
-    const float4 r = reinterpret_cast<const float4*>(R + s * 8)[h];
-    float4 o;
-    o.x = (m & 1u) ? r.x + (a.x + b.x) : 0.0f;
-    o.y = (m & 2u) ? r.y + (a.y + b.y) : 0.0f;
-    o.z = (m & 4u) ? r.z + (a.z + b.z) : 0.0f;
-    o.w = (m & 8u) ? r.w + (a.w + b.w) : 0.0f;
-    reinterpret_cast<float4*>(Dout + s * 8)[h] = o;
+    for (; k < hi; ++k) a0 = fmaf(__ldcs(ah + k), __ldg(Din + (int64_t)__ldcs(ci + k) * 8 + j), a0);
+    const bool q = (sq[s] >> j) & 1u;
+    Dout[s * 8 + j] = q ? R[s * 8 + j] + ((a0 + a1) + (a2 + a3)) : 0.0f;
   }
 }
 
@@ -272,7 +264,7 @@ static void l_bresid(reach_batch* b, bool report, cudaStream_t s) {
 
 static void l_bsweep(reach_batch* b, const float* din, float* dout, cudaStream_t s) {
   reach_ctx* c = b->base;
-  const int grid = grid_rows(c, (const void*)k_bsweep, BT, 2, c->n);
+  const int grid = grid_rows(c, (const void*)k_bsweep, BT, 8, c->n);
   k_bsweep<<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_hi, b->sq, b->R, din, dout, c->st);
 }
 
