@@ -92,3 +92,25 @@ def test_table1_shapes(n, m):
     _well_formed(c)
     sinks = int(round(0.02 * n)) or 1
     assert abs(c.m - m) <= 2 * sinks + n // 50 + 2
+
+
+def test_cascade_chain_structure():
+    blocks, width = 12, 300
+    c = synth.cascade_chain(blocks=blocks, width=width, seed=9)
+    _well_formed(c)
+    deg = np.diff(c.rowptr)
+    row = np.repeat(np.arange(c.n), deg)
+    sink = (deg == 1) & (c.col[c.rowptr[:-1]] == np.arange(c.n)) & (c.val[c.rowptr[:-1]] == 1.0)
+    live = ~sink[row]
+    b_from, b_to = row[live] // width, c.col[live] // width
+    assert np.all((b_to == b_from) | (b_to == b_from + 1))          # same block or the next
+    stay = (b_to == b_from)[b_from < blocks - 1]
+    assert 0.85 < stay.mean() < 0.95
+    assert set(np.flatnonzero(c.goal) // width) == {blocks - 1}
+
+
+def test_skewed_chain_hubs():
+    c = synth.skewed_chain(n=5000, hubs=3, hub_deg=1500, seed=10)
+    _well_formed(c)
+    deg = np.diff(c.rowptr)
+    assert np.sum(deg == 1500) == 3 and np.sort(deg)[-4] <= 64
