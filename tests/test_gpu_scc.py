@@ -223,3 +223,38 @@ def test_max_iter_bounds_the_level_sweeps(graph, monkeypatch):
         with pytest.raises(R.ReachError) as ei:
             s.solve("scc_jacobi", eps=1e-14, max_iter=10)
     assert ei.value.status == R.REACH_ENOTCONV
+
+
+def test_scc_argument_and_state_errors():
+    need_gpu()
+    c = CHAINS["random"]()
+    ctx = R.reach_create(c.n, c.rowptr, c.col, c.val, c.goal)
+    try:
+        with pytest.raises(R.ReachError) as ei:
+            R.reach_scc(ctx)
+        assert ei.value.status == R.REACH_ESTATE            # before reach_precompute
+        R.reach_precompute(ctx)
+        with pytest.raises(R.ReachError) as ei:
+            R.reach_scc(ctx, max_rounds=-1)
+        assert ei.value.status == R.REACH_EINVAL
+        lab, lev, info = R.reach_scc(ctx)
+        assert info["exact"] == 1 and info["passes"] > 0
+        # a new precompute (another partition) drops the decomposition
+        R.reach_precompute(ctx, R.REACH_PROB0_ONLY)
+        lab2, lev2, info2 = R.reach_scc(ctx)
+        a, lab_o, lev_o = _oracle_scc(c, O.PROB0_ONLY)
+        assert np.array_equal(lab2, lab_o) and np.array_equal(lev2, lev_o)
+    finally:
+        R.reach_destroy(ctx)
+
+
+def test_level_by_level_jacobi_warm_start():
+    need_gpu()
+    c = CHAINS["cascade"]()
+    cls_o, x_o = oracle_solution(c)
+    with R.Solver(c.n, c.rowptr, c.col, c.val, c.goal) as s:
+        x, info = s.solve("scc_jacobi", eps=1e-14, max_iter=5_000_000)
+        x2, info2 = s.solve("scc_jacobi", eps=1e-12, max_iter=5_000_000, x0=x)
+    assert info2["status"] == R.REACH_OK
+    assert info2["iters"] < info["iters"]
+    assert np.max(np.abs(x2 - x_o)) <= TOL_FP64
