@@ -383,7 +383,7 @@ __global__ void k_check_mixed(SolveState* st, int slot_idx, int k) {
 }
 
 template <int G, bool V, typename IT, int U>
-__global__ void __launch_bounds__(NT, U == 2 ? 5 : 1) k_sweep32(int64_t nq, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(NT) k_sweep32(int64_t nq, const int64_t* __restrict__ rp,
                                                 const IT* __restrict__ ci,
                                                 const float* __restrict__ ah,
                                                 const float* __restrict__ r32,
