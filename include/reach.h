@@ -59,10 +59,12 @@ enum { REACH_HOST = 0, REACH_DEVICE = 1 };
 typedef enum { REACH_PROB01 = 0, REACH_PROB0_ONLY = 1 } reach_precomp_mode;
 
 /* Solvers.  JACOBI_FP64: x_i <- (b_i + sum_{j != i} A_ij x_j) / (1 - A_ii), double
- * buffered (§3.1), stop when max|x' - x| < eps.  JACOBI_MIXED: the same iteration run
- * as defect correction -- every refine_k sweeps an FP64 residual r = b - (I - A) x
- * (values as FP32 hi + lo pairs), then refine_k - 1 FP32 sweeps on (I - A) d = r,
- * then x += d in FP64; stop when max|r_i / (1 - A_ii)| < eps (the FP64 Jacobi step).
+ * buffered (§3.1), stop when max|x' - x| < eps.  The sweeps run on the Jacobi form
+ * D^-1 A, D^-1 b (d_i = 1 - A_ii), scaled once per system, so no sweep divides.
+ * JACOBI_MIXED: the same iteration run as defect correction -- every refine_k sweeps an
+ * FP64 residual r / d = D^-1 b + D^-1 A x - x (the values D^-1 A as FP32 hi + lo pairs),
+ * then refine_k - 1 FP32 sweeps on (I - D^-1 A) e = r / d, then x += e in FP64; stop when
+ * max|r_i / d_i| < eps (the FP64 Jacobi step).
  * BICGSTAB_FP64: unpreconditioned BiCGStab (§3.2) with x = 0 and shadow q = b;
  * stop when max|s| < eps after the a-step (then x += a p) or max|r| < eps. */
 typedef enum {
