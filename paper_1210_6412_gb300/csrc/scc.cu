@@ -315,7 +315,7 @@ RDEV void push_chunks(int32_t L, const uint32_t* msize, const int64_t* mstart, i
 // q[f & 1] of size pc[f % 3], pushes into q[(f + 1) & 1] / pc[(f + 1) % 3], and clears
 // pc[(f + 2) % 3] for the step after (that count was last read two barriers earlier).
 // Every CTA reads the same sizes after a barrier, so all of them take the same branches.
-enum : int { PC_CHG = 3, PC_CORE = 6, PC_FAIL = 7 };
+enum : int { PC_CHG = 3, PC_CORE = 6, PC_FAIL = 7, PC_ALLSINK = 8 };
 
 RDEV unsigned ld_vol(const unsigned* p) { return *(const volatile unsigned*)p; }
 
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(SCC_NT, 2) k_scc_persist(int64_t nq, const int
                                                           const int64_t* __restrict__ trp,
                                                           const int32_t* __restrict__ tcol, int32_t* lab,
                                                           int32_t* color, uint32_t* indeg, uint32_t* outdeg,
-                                                          int32_t* q0, int32_t* q1, unsigned* pc,
+                                                          int32_t* lvl, int32_t* q0, int32_t* q1, unsigned* pc,
                                                           int32_t max_rounds, int64_t budget, SccState* ss,
                                                           GridBar gb) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -334,15 +334,19 @@ __global__ void __launch_bounds__(SCC_NT, 2) k_scc_persist(int64_t nq, const int
   RowGroups rg = RowGroups::make<G>();
   __shared__ int any_change;
   int64_t f = 0, seen = 0, passes = 0;
-  // step 0: trimming seeds
+  // Phase 1, trimming from the sinks (Kahn's order): a row whose successors are all gone
+  // is a component of its own, and the pass that frees it is its level.  Removing such
+  // rows never changes an in-degree that matters (their successors left before them),
+  // so the in-degrees stay exact for phase 2.  On an acyclic system this alone yields
+  // every component and level.
   for (int64_t v = tid; v < nq; v += nth) {
     const uint32_t od = (uint32_t)(arp[v + 1] - arp[v]);
-    const uint32_t id = (uint32_t)(trp[v + 1] - trp[v]);
     outdeg[v] = od;
-    indeg[v] = id;
+    indeg[v] = (uint32_t)(trp[v + 1] - trp[v]);
     color[v] = -1;
-    if (od == 0 || id == 0) {
+    if (od == 0) {
       lab[v] = (int32_t)v;
+      lvl[v] = 0;
       q1[atomicAdd(pc + 1, 1u)] = (int32_t)v;
     } else {
       lab[v] = -1;
@@ -351,7 +355,57 @@ __global__ void __launch_bounds__(SCC_NT, 2) k_scc_persist(int64_t nq, const int
   if (lead) pc[2] = 0u;
   if (!grid_barrier(gb)) return;
   f = 1;
-  // trimming steps
+  for (;;) {
+    const unsigned size = ld_vol(pc + f % 3);
+    seen += size;
+    if (size == 0 || ++passes > budget) break;
+    const int32_t* qc = (f & 1) ? q1 : q0;
+    int32_t* qn = (f & 1) ? q0 : q1;
+    unsigned* cn = pc + (f + 1) % 3;
+    if (lead) pc[(f + 2) % 3] = 0u;
+    for (int64_t i = rg.first; i < (int64_t)size; i += rg.stride) {
+      const int32_t v = qc[i];
+      for (int64_t k = trp[v] + rg.lane; k < trp[v + 1]; k += G) {
+        const int32_t u = tcol[k];
+        if (__ldcg(lab + u) != -1) continue;
+        if (atomicSub(outdeg + u, 1u) == 1u && atomicCAS(lab + u, -1, u) == -1) {
+          lvl[u] = (int32_t)f;
+          qn[atomicAdd(cn, 1u)] = u;
+        }
+      }
+    }
+    if (!grid_barrier(gb)) return;
+    ++f;
+  }
+  if (seen >= nq) {   // acyclic: every component is one row, and its level is known
+    if (lead) {
+      pc[PC_ALLSINK] = 1u;
+      ss->n_levels = (int32_t)(f - 1);
+      ss->n_scc = nq;
+      ss->n_trivial = nq;
+      ss->largest = nq > 0 ? 1 : 0;
+      ss->round = 0;
+      ss->exact = 1;
+      ss->passes = passes;
+      if (passes > budget) pc[PC_FAIL] = 1u;
+    }
+    return;
+  }
+  // Phase 2, trimming from both ends on what is left: seeds are the rows without
+  // predecessors (rows without successors are gone already)
+  {
+    int32_t* qn = (f & 1) ? q0 : q1;
+    unsigned* cn = pc + (f + 1) % 3;
+    if (lead) pc[(f + 2) % 3] = 0u;
+    for (int64_t v = tid; v < nq; v += nth) {
+      if (lab[v] == -1 && indeg[v] == 0u) {
+        lab[v] = (int32_t)v;
+        qn[atomicAdd(cn, 1u)] = (int32_t)v;
+      }
+    }
+    if (!grid_barrier(gb)) return;
+    ++f;
+  }
   for (;;) {
     const unsigned size = ld_vol(pc + f % 3);
     seen += size;
@@ -1065,17 +1119,22 @@ cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok) {
   int32_t* q1 = c->queue + c->n;
   const int64_t key_base = nq * 7919 + c->m_q;
   const bool persistent = use_persistent(c);
+  bool acyclic = false;   // the sink-side trimming found every component and level
   int32_t status = 0;
   if (persistent) {
     cudaMemsetAsync(sp->pc, 0, 16 * sizeof(unsigned), s);
     cudaMemsetAsync(sp->bar, 0, 4 * sizeof(unsigned), s);
 #define SCC_P(G) e = coop_launch(c, (const void*)k_scc_persist<G>, nq, c->a_rowptr, c->a_col, c->at_rowptr,    \
-                                 c->at_col, sp->lab, sp->color, sp->indeg, sp->outdeg, q0, q1, sp->pc,         \
-                                 max_rounds, bound, sp->ss, GridBar{sp->bar, sp->bar + 1, sp->bar + 2})
+                                 c->at_col, sp->lab, sp->color, sp->indeg, sp->outdeg, sp->lvl, q0, q1,        \
+                                 sp->pc, max_rounds, bound, sp->ss, GridBar{sp->bar, sp->bar + 1, sp->bar + 2})
     SCC_G_DISPATCH(g, SCC_P)
 #undef SCC_P
     if (e != cudaSuccess) return e;
     if ((e = coop_status(c, sp, &status)) != cudaSuccess) return e;
+    unsigned allsink = 0;
+    if ((e = cudaMemcpy(&allsink, sp->pc + PC_ALLSINK, sizeof(unsigned), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return e;
+    acyclic = allsink != 0;
   } else {
 #define SCC_STEP(G)                                                                                      \
   k_scc_step<G><<<grid, SCC_NT, 0, cs>>>(nq, c->a_rowptr, c->a_col, c->at_rowptr, c->at_col, sp->lab,   \
@@ -1106,7 +1165,7 @@ cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok) {
   k_members<<<grid_for(c, (const void*)k_members, SCC_NT, nq), SCC_NT, 0, s>>>(nq, sp->lab, sp->mstart, fill,
                                                                                 sp->mem);
   // levels
-  if (persistent) {
+  if (persistent && !acyclic) {
     cudaMemsetAsync(sp->pc, 0, 16 * sizeof(unsigned), s);
     cudaMemsetAsync(sp->bar, 0, 4 * sizeof(unsigned), s);
 #define LVL_P(G) e = coop_launch(c, (const void*)k_lvl_persist<G>, nq, c->at_rowptr, c->at_col, sp->lab,     \
