@@ -332,7 +332,6 @@ __global__ void __launch_bounds__(SCC_NT, 2) k_scc_persist(int64_t nq, const int
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   RowGroups rg = RowGroups::make<G>();
-  __shared__ int any_change;
   int64_t f = 0, seen = 0, passes = 0;
   // Phase 1, trimming from the sinks (Kahn's order): a row whose successors are all gone
   // is a component of its own, and the pass that frees it is its level.  Removing such
@@ -442,33 +441,44 @@ __global__ void __launch_bounds__(SCC_NT, 2) k_scc_persist(int64_t nq, const int
       if (!grid_barrier(gb)) return;
       break;
     }
-    for (int64_t v = tid; v < nq; v += nth) {
-      if (lab[v] != -1) continue;
-      color[v] = (int32_t)v;
-      if (round == 0) atomicMax(reinterpret_cast<int*>(pc + PC_CORE), (int)v);
+    // every row left starts with its own index as colour and seeds the first
+    // propagation frontier (step f); outdeg, no longer needed, stamps queued rows
+    uint32_t* stamp = outdeg;
+    {
+      int32_t* qn = (f & 1) ? q0 : q1;
+      unsigned* cn = pc + (f + 1) % 3;
+      if (lead) pc[(f + 2) % 3] = 0u;
+      for (int64_t v = tid; v < nq; v += nth) {
+        if (lab[v] != -1) continue;
+        color[v] = (int32_t)v;
+        stamp[v] = 0xffffffffu;
+        qn[atomicAdd(cn, 1u)] = (int32_t)v;
+        if (round == 0) atomicMax(reinterpret_cast<int*>(pc + PC_CORE), (int)v);
+      }
+      if (!grid_barrier(gb)) return;
+      ++f;
     }
-    if (lead) pc[PC_CHG] = 0u;
-    if (!grid_barrier(gb)) return;
-    for (int64_t p = 0;; ++p) {
-      if (threadIdx.x == 0) any_change = 0;
-      __syncthreads();
-      if (lead) pc[PC_CHG + (p + 1) % 3] = 0u;
-      for (int64_t v = rg.first; v < nq; v += rg.stride) {
-        if (__ldcg(lab + v) != -1) continue;
+    // max-label propagation over the frontier of rows whose colour rose in the last
+    // pass; a row is queued once per pass (its stamp), and reads its latest colour
+    for (;;) {
+      const unsigned size = ld_vol(pc + f % 3);
+      if (size == 0 || ++passes > budget) break;
+      const int32_t* qc = (f & 1) ? q1 : q0;
+      int32_t* qn = (f & 1) ? q0 : q1;
+      unsigned* cn = pc + (f + 1) % 3;
+      if (lead) pc[(f + 2) % 3] = 0u;
+      for (int64_t i = rg.first; i < (int64_t)size; i += rg.stride) {
+        const int32_t v = qc[i];
         const int32_t cv = __ldcg(color + v);
         for (int64_t k = arp[v] + rg.lane; k < arp[v + 1]; k += G) {
           const int32_t u = acol[k];
-          if (__ldcg(lab + u) != -1) continue;
-          if (__ldcg(color + u) < cv) {
-            atomicMax(color + u, cv);
-            any_change = 1;
-          }
+          if (__ldcg(lab + u) != -1 || __ldcg(color + u) >= cv) continue;
+          if (atomicMax(color + u, cv) < cv && atomicExch(stamp + u, (uint32_t)f) != (uint32_t)f)
+            qn[atomicAdd(cn, 1u)] = u;
         }
       }
-      __syncthreads();
-      if (threadIdx.x == 0 && any_change) atomicExch(pc + PC_CHG + p % 3, 1u);
       if (!grid_barrier(gb)) return;
-      if (ld_vol(pc + PC_CHG + p % 3) == 0u || ++passes > budget) break;
+      ++f;
     }
     // roots seed a frontier (step f); the backward search inside each colour follows
     {
