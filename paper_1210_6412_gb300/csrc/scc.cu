@@ -309,6 +309,33 @@ RDEV void push_chunks(int32_t L, const uint32_t* msize, const int64_t* mstart, i
   for (uint32_t j = 0; j < nch; ++j) qn[base + j] = (int32_t)(mstart[L] + (int64_t)j * SCC_CHUNK);
 }
 
+// One Kahn pass: every member of every queued chunk (one thread per member) releases
+// its edges from other components; a component whose count of unreleased outgoing edges
+// reaches 0 gets level h + 1 and queues its own chunks.
+RDEV void release_chunks(uint32_t size, const int32_t* __restrict__ qc, const int32_t* __restrict__ lab,
+                         const uint32_t* __restrict__ msize, const int64_t* __restrict__ mstart,
+                         const int32_t* __restrict__ mem, const int64_t* __restrict__ trp,
+                         const int32_t* __restrict__ tcol, uint32_t* out_edges, int32_t* lvl, int32_t h,
+                         int32_t* qn, uint32_t* cn, int64_t tid, int64_t nth) {
+  const int64_t items = (int64_t)size * SCC_CHUNK;
+  for (int64_t it = tid; it < items; it += nth) {
+    const int64_t ci = it / SCC_CHUNK;
+    const int64_t p0 = qc[ci];
+    const int32_t L = lab[mem[p0]];
+    const int64_t p = p0 + (it - ci * SCC_CHUNK);
+    if (p >= mstart[L] + msize[L] || p >= p0 + SCC_CHUNK) continue;
+    const int32_t v = mem[p];
+    for (int64_t k = trp[v]; k < trp[v + 1]; ++k) {
+      const int32_t Lu = lab[tcol[k]];
+      if (Lu == L) continue;
+      if (atomicSub(out_edges + Lu, 1u) == 1u) {
+        lvl[Lu] = h + 1;
+        push_chunks(Lu, msize, mstart, qn, cn);
+      }
+    }
+  }
+}
+
 // ---- the same decomposition in cooperative launches (grid barriers between passes)
 //
 // Frontier bookkeeping shared by every queue-driven pass: step f reads the frontier
@@ -561,22 +588,7 @@ __global__ void __launch_bounds__(SCC_NT, 2) k_lvl_persist(int64_t nq, const int
     int32_t* qn = (f & 1) ? q0 : q1;
     unsigned* cn = pc + (f + 1) % 3;
     if (lead) pc[(f + 2) % 3] = 0u;
-    for (int64_t i = rg.first; i < (int64_t)size; i += rg.stride) {
-      const int64_t p0 = qc[i];
-      const int32_t L = lab[mem[p0]];
-      const int64_t p1 = std::min<int64_t>(p0 + SCC_CHUNK, mstart[L] + msize[L]);
-      for (int64_t p = p0; p < p1; ++p) {
-        const int32_t v = mem[p];
-        for (int64_t k = trp[v] + rg.lane; k < trp[v + 1]; k += G) {
-          const int32_t Lu = lab[tcol[k]];
-          if (Lu == L) continue;
-          if (atomicSub(out_edges + Lu, 1u) == 1u) {
-            lvl[Lu] = h + 1;
-            push_chunks(Lu, msize, mstart, qn, cn);
-          }
-        }
-      }
-    }
+    release_chunks(size, qc, lab, msize, mstart, mem, trp, tcol, out_edges, lvl, h, qn, cn, tid, nth);
     if (!grid_barrier(gb)) return;
   }
   if (lead) {
@@ -650,22 +662,7 @@ __global__ void __launch_bounds__(SCC_NT) k_lvl_step(int64_t nq, const int64_t* 
   } else if (ph == PH_LV_ROUND) {
     const int32_t h = ss->level;
     RowGroups rg = RowGroups::make<G>();
-    for (int64_t i = rg.first; i < (int64_t)ncur; i += rg.stride) {
-      const int64_t p0 = qc[i];
-      const int32_t L = lab[mem[p0]];
-      const int64_t p1 = std::min<int64_t>(p0 + SCC_CHUNK, mstart[L] + msize[L]);
-      for (int64_t p = p0; p < p1; ++p) {
-        const int32_t v = mem[p];
-        for (int64_t k = trp[v] + rg.lane; k < trp[v + 1]; k += G) {
-          const int32_t Lu = lab[tcol[k]];
-          if (Lu == L) continue;
-          if (atomicSub(out_edges + Lu, 1u) == 1u) {
-            lvl[Lu] = h + 1;
-            push_chunks(Lu, msize, mstart, qn, cnext);
-          }
-        }
-      }
-    }
+    release_chunks(ncur, qc, lab, msize, mstart, mem, trp, tcol, out_edges, lvl, h, qn, cnext, tid, nth);
   } else {
     return;
   }
