@@ -52,7 +52,8 @@ struct BfsState {
 };
 
 struct Tuning {
-  int g = 0;            // lanes per row for CSR kernels (0 = pick from mean degree; 64 = warp + vector loads)
+  int g = 0;            // lanes per row for CSR kernels (0 = pick from mean degree; 64 = warp + vector
+                        // loads; 128 = entry-balanced tiles, FP64 Jacobi and the mixed method only)
   int gm[3] = {0, 0, 0};  // autotuned lanes-per-row code per method (0 = none)
   int k = 16;           // sweeps between convergence checks / refinement period
   int k_auto = 0;       // autotuned sweeps between checks for FP64 Jacobi (0 = none)
@@ -187,6 +188,10 @@ void launch_finalize_resid(cudaStream_t s, SolveState* st);
 
 // ---- segscan.cu
 cudaError_t solve_jacobi_seg(reach_ctx* c, const double* x0q);
+cudaError_t seg_plan(reach_ctx* c);
+void seg_sweep(reach_ctx* c, const double* x, double* xn, unsigned long long* slot, cudaStream_t s);
+void seg_sweep32(reach_ctx* c, const float* din, float* dout, cudaStream_t s);
+void seg_resid_hilo(reach_ctx* c, unsigned long long* slot, cudaStream_t s);
 void seg_free(reach_ctx* c);
 // ---- scc.cu
 cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok);

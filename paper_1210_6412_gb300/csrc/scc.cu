@@ -309,28 +309,29 @@ RDEV void push_chunks(int32_t L, const uint32_t* msize, const int64_t* mstart, i
   for (uint32_t j = 0; j < nch; ++j) qn[base + j] = (int32_t)(mstart[L] + (int64_t)j * SCC_CHUNK);
 }
 
-// One Kahn pass: every member of every queued chunk (one thread per member) releases
-// its edges from other components; a component whose count of unreleased outgoing edges
-// reaches 0 gets level h + 1 and queues its own chunks.
+// One Kahn pass: a warp per queued chunk, a lane per member (up to 8 members a lane), so
+// a component of one row costs one warp trip and a giant component spreads over its
+// chunks.  Every member releases its edges from other components; a component whose
+// count of unreleased outgoing edges reaches 0 gets level h + 1 and queues its chunks.
 RDEV void release_chunks(uint32_t size, const int32_t* __restrict__ qc, const int32_t* __restrict__ lab,
                          const uint32_t* __restrict__ msize, const int64_t* __restrict__ mstart,
                          const int32_t* __restrict__ mem, const int64_t* __restrict__ trp,
                          const int32_t* __restrict__ tcol, uint32_t* out_edges, int32_t* lvl, int32_t h,
                          int32_t* qn, uint32_t* cn, int64_t tid, int64_t nth) {
-  const int64_t items = (int64_t)size * SCC_CHUNK;
-  for (int64_t it = tid; it < items; it += nth) {
-    const int64_t ci = it / SCC_CHUNK;
-    const int64_t p0 = qc[ci];
+  const int lane = threadIdx.x & 31;
+  for (int64_t w = tid >> 5; w < (int64_t)size; w += nth >> 5) {
+    const int64_t p0 = qc[w];
     const int32_t L = lab[mem[p0]];
-    const int64_t p = p0 + (it - ci * SCC_CHUNK);
-    if (p >= mstart[L] + msize[L] || p >= p0 + SCC_CHUNK) continue;
-    const int32_t v = mem[p];
-    for (int64_t k = trp[v]; k < trp[v + 1]; ++k) {
-      const int32_t Lu = lab[tcol[k]];
-      if (Lu == L) continue;
-      if (atomicSub(out_edges + Lu, 1u) == 1u) {
-        lvl[Lu] = h + 1;
-        push_chunks(Lu, msize, mstart, qn, cn);
+    const int64_t p1 = std::min<int64_t>(p0 + SCC_CHUNK, mstart[L] + msize[L]);
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+      const int32_t v = mem[p];
+      for (int64_t k = trp[v]; k < trp[v + 1]; ++k) {
+        const int32_t Lu = lab[tcol[k]];
+        if (Lu == L) continue;
+        if (atomicSub(out_edges + Lu, 1u) == 1u) {
+          lvl[Lu] = h + 1;
+          push_chunks(Lu, msize, mstart, qn, cn);
+        }
       }
     }
   }

@@ -79,11 +79,12 @@ __global__ void k_seg_tile_rows(int64_t nq, int64_t ntiles, const int64_t* __res
 // ---- the sweep
 
 // Inclusive segmented sum across the CTA: (v, f) then (w, g) -> (g ? w : v + w, f | g).
-RDEV void seg_scan_cta(double& v, int& f, double* shv, int* shf) {
+template <typename V>
+RDEV void seg_scan_cta(V& v, int& f, V* shv, int* shf) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const double pv = __shfl_up_sync(FULL, v, o);
+    const V pv = __shfl_up_sync(FULL, v, o);
     const int pf = __shfl_up_sync(FULL, f, o);
     if (lane >= o && !f) v += pv;
     if (lane >= o) f |= pf;
@@ -94,11 +95,11 @@ RDEV void seg_scan_cta(double& v, int& f, double* shv, int* shf) {
   }
   __syncthreads();
   if (w == 0) {
-    double a = lane < (SEG_NT / 32) ? shv[lane] : 0.0;
+    V a = lane < (SEG_NT / 32) ? shv[lane] : V(0);
     int af = lane < (SEG_NT / 32) ? shf[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const double pv = __shfl_up_sync(FULL, a, o);
+      const V pv = __shfl_up_sync(FULL, a, o);
       const int pf = __shfl_up_sync(FULL, af, o);
       if (lane >= o && !af) a += pv;
       if (lane >= o) af |= pf;
@@ -114,40 +115,128 @@ RDEV void seg_scan_cta(double& v, int& f, double* shv, int* shf) {
   __syncthreads();
 }
 
+// The three sweeps that run entry-balanced: what one stored entry contributes, and what
+// a finished row sum becomes.  finish() returns the row's contribution to the stopping
+// quantity (0 for the FP32 sweep, which has none).
+struct OpJac64 {          // FP64 Jacobi on the Jacobi form: x' = bj + Aj x, max|x' - x|
+  using V = double;
+  static constexpr bool DELTA = true;
+  const double* av;
+  const double* x;
+  const double* bj;
+  double* xn;
+  RDEV void prod8(int64_t base, const int (&cc)[8], V (&p)[8]) const {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const double2 v = __ldcs(reinterpret_cast<const double2*>(av + base + 2 * h));
+      p[2 * h] = v.x * __ldg(x + cc[2 * h]);
+      p[2 * h + 1] = v.y * __ldg(x + cc[2 * h + 1]);
+    }
+  }
+  RDEV V prod(int64_t k, int c) const { return __ldcs(av + k) * __ldg(x + c); }
+  RDEV double finish(int64_t r, V s) const {
+    const double xv = bj[r] + s;
+    xn[r] = xv;
+    return fabs(xv - x[r]);
+  }
+};
+
+struct OpSweep32 {        // FP32 correction sweep of the mixed method: d' = r + Aj_hi d
+  using V = float;
+  static constexpr bool DELTA = false;
+  const float* ah;
+  const float* din;
+  const float* r32;
+  float* dout;
+  RDEV void prod8(int64_t base, const int (&cc)[8], V (&p)[8]) const {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(ah + base + 4 * h));
+      p[4 * h] = v.x * __ldg(din + cc[4 * h]);
+      p[4 * h + 1] = v.y * __ldg(din + cc[4 * h + 1]);
+      p[4 * h + 2] = v.z * __ldg(din + cc[4 * h + 2]);
+      p[4 * h + 3] = v.w * __ldg(din + cc[4 * h + 3]);
+    }
+  }
+  RDEV V prod(int64_t k, int c) const { return __ldcs(ah + k) * __ldg(din + c); }
+  RDEV double finish(int64_t r, V s) const {
+    dout[r] = r32[r] + s;
+    return 0.0;
+  }
+};
+
+struct OpResidHilo {      // FP64 residual of the mixed method: r = bj + Aj x - x, values hi + lo
+  using V = double;
+  static constexpr bool DELTA = true;
+  const float* ah;
+  const float* al;
+  const double* x;
+  const float* xf;
+  const double* bj;
+  float* r32;
+  float* dl0;
+  // hi * x in FP64 (one FMA, with the integer widening), lo * x in FP32 (lo is below
+  // 2^-24 of the value), added in FP64
+  RDEV V one(float h, float l, int c) const { return fma(widen(h), __ldg(x + c), widen(l * __ldg(xf + c))); }
+  RDEV void prod8(int64_t base, const int (&cc)[8], V (&p)[8]) const {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float4 hv = __ldcs(reinterpret_cast<const float4*>(ah + base + 4 * h));
+      const float4 lv = __ldcs(reinterpret_cast<const float4*>(al + base + 4 * h));
+      p[4 * h] = one(hv.x, lv.x, cc[4 * h]);
+      p[4 * h + 1] = one(hv.y, lv.y, cc[4 * h + 1]);
+      p[4 * h + 2] = one(hv.z, lv.z, cc[4 * h + 2]);
+      p[4 * h + 3] = one(hv.w, lv.w, cc[4 * h + 3]);
+    }
+  }
+  RDEV V prod(int64_t k, int c) const { return one(__ldcs(ah + k), __ldcs(al + k), c); }
+  RDEV double finish(int64_t r, V s) const {
+    const double rv = bj[r] + s - x[r];
+    const float rf = __double2float_rn(rv);
+    r32[r] = rf;
+    dl0[r] = rf;
+    return fabs(rv);
+  }
+};
+
+RDEV void delta_to_slot(double mx, unsigned long long* slot) {
+  __shared__ double sh[32];
+  double a[1] = {mx != mx ? __longlong_as_double(0x7ff0000000000000LL) : mx};
+  block_reduce<1, true>(a, sh);
+  if (threadIdx.x == 0) atomic_max_nonneg(slot, a[0]);
+}
+
+template <class Op>
 __global__ void __launch_bounds__(SEG_NT) k_seg_sweep(int64_t mq, int64_t ntiles, const int64_t* __restrict__ rp,
-                                                      const int32_t* __restrict__ ci, const double* __restrict__ av,
-                                                      const double* __restrict__ bj,
-                                                      const double* __restrict__ x, double* __restrict__ xn,
+                                                      const int32_t* __restrict__ ci, Op op,
                                                       const uint32_t* __restrict__ endbits,
                                                       const int64_t* __restrict__ tile_row0,
                                                       const int64_t* __restrict__ nonempty,
-                                                      double* __restrict__ head, double* __restrict__ tail,
+                                                      typename Op::V* __restrict__ head,
+                                                      typename Op::V* __restrict__ tail,
                                                       unsigned long long* slot) {
-  __shared__ double shv[SEG_NT / 32];
+  using V = typename Op::V;
+  __shared__ V shv[SEG_NT / 32];
   __shared__ int shf[SEG_NT / 32];
   __shared__ int shc[SEG_NT / 32];
+  __shared__ V lastv[SEG_NT / 32];
   double mx = 0.0;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t base = t * SEG_T + (int64_t)threadIdx.x * SEG_ITEMS;
     // products of this thread's entries and their row-end flags
-    double p[SEG_ITEMS];
+    V p[SEG_ITEMS];
     unsigned flags = 0;
     if (base + SEG_ITEMS <= mq) {
       const int4 c0 = __ldcs(reinterpret_cast<const int4*>(ci + base));
       const int4 c1 = __ldcs(reinterpret_cast<const int4*>(ci + base + 4));
       const int cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const double2 v = __ldcs(reinterpret_cast<const double2*>(av + base + 2 * h));
-        p[2 * h] = v.x * __ldg(x + cc[2 * h]);
-        p[2 * h + 1] = v.y * __ldg(x + cc[2 * h + 1]);
-      }
+      op.prod8(base, cc, p);
       flags = (__ldg(endbits + (base >> 5)) >> (base & 31)) & 0xffu;
     } else {
 #pragma unroll
       for (int j = 0; j < SEG_ITEMS; ++j) {
         const int64_t k = base + j;
-        p[j] = k < mq ? __ldcs(av + k) * __ldg(x + __ldcs(ci + k)) : 0.0;
+        p[j] = k < mq ? op.prod(k, __ldcs(ci + k)) : V(0);
         if (k < mq && ((__ldg(endbits + (k >> 5)) >> (k & 31)) & 1u)) flags |= 1u << j;
       }
     }
@@ -169,7 +258,7 @@ __global__ void __launch_bounds__(SEG_NT) k_seg_sweep(int64_t mq, int64_t ntiles
       __syncthreads();
     }
     // thread-local pieces: head (up to the first row end), whole rows inside, tail
-    double head_v = 0.0, run = 0.0, tail_v = 0.0;
+    V head_v = V(0), run = V(0);
     int seen = 0;
     const int64_t row0 = tile_row0[t] + excl;    // nonempty index of this thread's first row
 #pragma unroll
@@ -180,37 +269,31 @@ __global__ void __launch_bounds__(SEG_NT) k_seg_sweep(int64_t mq, int64_t ntiles
           head_v = run;                          // completed below, after the carry-in
         } else {
           const int64_t r = nonempty[row0 + seen];   // row entirely inside this thread
-          const double xv = bj[r] + run;
-          mx = fmax(mx, fabs(xv - x[r]));
-          xn[r] = xv;
+          mx = fmax(mx, op.finish(r, run));
         }
         ++seen;
-        run = 0.0;
+        run = V(0);
       }
     }
-    tail_v = run;   // entries after the last row end (all of them when cnt == 0)
     // Segmented scan over threads: value = this thread's tail, a segment starts at every
     // thread with a row end.  The exclusive result is the part of this thread's first row
     // that lies in earlier threads of the tile.
     int f = cnt ? 1 : 0;
-    double incl = tail_v;
-    seg_scan_cta(incl, f, shv, shf);
-    double carry = __shfl_up_sync(FULL, incl, 1);
+    V incl = run;
+    seg_scan_cta<V>(incl, f, shv, shf);
+    V carry = __shfl_up_sync(FULL, incl, 1);
     {
       const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-      __shared__ double lastv[SEG_NT / 32];
       if (lane == 31) lastv[w] = incl;
       __syncthreads();
-      if (lane == 0) carry = w > 0 ? lastv[w - 1] : 0.0;
+      if (lane == 0) carry = w > 0 ? lastv[w - 1] : V(0);
       __syncthreads();
     }
     if (cnt) {
-      const double first_total = carry + head_v;
+      const V first_total = carry + head_v;
       const int64_t r = nonempty[row0];
       if (rp[r] >= t * SEG_T) {                  // the row starts inside this tile: complete
-        const double xv = bj[r] + first_total;
-        mx = fmax(mx, fabs(xv - x[r]));
-        xn[r] = xv;
+        mx = fmax(mx, op.finish(r, first_total));
       } else {                                   // started in an earlier tile: finished by k_seg_fix
         head[t] = first_total;
       }
@@ -219,24 +302,22 @@ __global__ void __launch_bounds__(SEG_NT) k_seg_sweep(int64_t mq, int64_t ntiles
     if (threadIdx.x == SEG_NT - 1) tail[t] = incl;
     __syncthreads();
   }
-  __shared__ double sh[32];
-  double a[1] = {mx != mx ? __longlong_as_double(0x7ff0000000000000LL) : mx};
-  block_reduce<1, true>(a, sh);
-  if (threadIdx.x == 0) atomic_max_nonneg(slot, a[0]);
+  if constexpr (Op::DELTA) delta_to_slot(mx, slot);
 }
 
 // Rows spanning tiles: tail of the first tile + whole middle tiles + head of the last
 // tile, in tile order.  Threads past the spanning rows handle rows without entries.
+template <class Op>
 __global__ void k_seg_fix(int64_t n_span, int64_t n_empty, const int64_t* __restrict__ span,
-                          const int64_t* __restrict__ empty, const int64_t* __restrict__ rp,
-                          const double* __restrict__ head, const double* __restrict__ tail,
-                          const double* __restrict__ bj,
-                          const double* __restrict__ x, double* __restrict__ xn, unsigned long long* slot) {
+                          const int64_t* __restrict__ empty, const int64_t* __restrict__ rp, Op op,
+                          const typename Op::V* __restrict__ head, const typename Op::V* __restrict__ tail,
+                          unsigned long long* slot) {
+  using V = typename Op::V;
   double mx = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_span + n_empty;
        i += (int64_t)gridDim.x * blockDim.x) {
     int64_t r;
-    double s = 0.0;
+    V s = V(0);
     if (i < n_span) {
       r = span[i];
       const int64_t t0 = rp[r] / SEG_T, t1 = (rp[r + 1] - 1) / SEG_T;
@@ -246,14 +327,9 @@ __global__ void k_seg_fix(int64_t n_span, int64_t n_empty, const int64_t* __rest
     } else {
       r = empty[i - n_span];
     }
-    const double xv = bj[r] + s;
-    mx = fmax(mx, fabs(xv - x[r]));
-    xn[r] = xv;
+    mx = fmax(mx, op.finish(r, s));
   }
-  __shared__ double sh[32];
-  double a[1] = {mx != mx ? __longlong_as_double(0x7ff0000000000000LL) : mx};
-  block_reduce<1, true>(a, sh);
-  if (threadIdx.x == 0) atomic_max_nonneg(slot, a[0]);
+  if constexpr (Op::DELTA) delta_to_slot(mx, slot);
 }
 
 __global__ void k_seg_check(SolveState* st, int slot_idx, int sweeps, int reset_n) {
@@ -295,7 +371,7 @@ void seg_free(reach_ctx* c) {
 
 // Tile plan of the current system: row-end bits, the row of each tile's first entry,
 // the rows spanning tiles and the rows without entries.
-static cudaError_t seg_plan(reach_ctx* c) {
+cudaError_t seg_plan(reach_ctx* c) {
   if (c->seg) return cudaSuccess;
   cudaStream_t s = c->stream;
   const int64_t nq = c->n_q, mq = c->m_q;
@@ -348,17 +424,35 @@ static cudaError_t seg_plan(reach_ctx* c) {
   return e;
 }
 
-static void seg_sweep(reach_ctx* c, const double* x, double* xn, unsigned long long* slot, cudaStream_t s) {
+template <class Op>
+static void seg_run(reach_ctx* c, const Op& op, unsigned long long* slot, cudaStream_t s) {
   SegPlan* sp = static_cast<SegPlan*>(c->seg);
+  using V = typename Op::V;
+  V* head = reinterpret_cast<V*>(sp->head);
+  V* tail = reinterpret_cast<V*>(sp->tail);
   if (sp->ntiles > 0) {
-    const int grid = (int)std::min<int64_t>(sp->ntiles, grid_for(c, (const void*)k_seg_sweep, SEG_NT, INT64_MAX / 2));
-    k_seg_sweep<<<grid, SEG_NT, 0, s>>>(c->m_q, sp->ntiles, c->a_rowptr, c->a_col, c->a_jv, c->bj, x, xn,
-                                         sp->endbits, sp->tile_row0, sp->nonempty, sp->head, sp->tail, slot);
+    const int grid =
+        (int)std::min<int64_t>(sp->ntiles, grid_for(c, (const void*)k_seg_sweep<Op>, SEG_NT, INT64_MAX / 2));
+    k_seg_sweep<Op><<<grid, SEG_NT, 0, s>>>(c->m_q, sp->ntiles, c->a_rowptr, c->a_col, op, sp->endbits,
+                                             sp->tile_row0, sp->nonempty, head, tail, slot);
   }
   const int64_t rest = sp->n_span + sp->n_empty;
   if (rest > 0)
-    k_seg_fix<<<grid_for(c, (const void*)k_seg_fix, 256, rest), 256, 0, s>>>(
-        sp->n_span, sp->n_empty, sp->span, sp->empty, c->a_rowptr, sp->head, sp->tail, c->bj, x, xn, slot);
+    k_seg_fix<Op><<<grid_for(c, (const void*)k_seg_fix<Op>, 256, rest), 256, 0, s>>>(
+        sp->n_span, sp->n_empty, sp->span, sp->empty, c->a_rowptr, op, head, tail, slot);
+}
+
+void seg_sweep(reach_ctx* c, const double* x, double* xn, unsigned long long* slot, cudaStream_t s) {
+  seg_run(c, OpJac64{c->a_jv, x, c->bj, xn}, slot, s);
+}
+
+// Entry-balanced forms of the mixed method's two kernels (FP32 sweep, FP64 residual).
+void seg_sweep32(reach_ctx* c, const float* din, float* dout, cudaStream_t s) {
+  seg_run(c, OpSweep32{c->a_hi, din, c->r32, dout}, nullptr, s);
+}
+
+void seg_resid_hilo(reach_ctx* c, unsigned long long* slot, cudaStream_t s) {
+  seg_run(c, OpResidHilo{c->a_hi, c->a_lo, c->x, c->xf, c->bj, c->r32, c->dl[1]}, slot, s);
 }
 
 // FP64 Jacobi (§3.1) with the entry-balanced sweep: same iteration and stopping rule as

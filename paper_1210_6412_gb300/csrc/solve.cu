@@ -658,9 +658,15 @@ __global__ void __launch_bounds__(NT) k_bi_x(int64_t nq, double* __restrict__ x,
 struct Lay {
   int g;
   bool vec;
+  bool seg = false;     // entry-balanced tiles (segscan.cu) instead of a row mapping
 };
 
-static Lay lay_of(int code) { return code >= 64 ? Lay{32, true} : Lay{code, false}; }
+constexpr int LAY_SEG = 128;
+
+static Lay lay_of(int code) {
+  if (code == LAY_SEG) return Lay{32, true, true};
+  return code >= 64 ? Lay{32, true} : Lay{code, false};
+}
 
 // Row mapping of `method`'s kernels: the autotuned choice if there is one, else the
 // REACH_LANES override, else lanes from the mean row length (warp + 16-byte loads from 96).
@@ -823,10 +829,12 @@ cudaError_t run_loop(reach_ctx* c, cudaGraphExec_t& exec, int64_t& exec_key, int
 }
 
 static int64_t shape_key(reach_ctx* c, const Lay& L, int k) {
-  return (c->n_q * 1000003LL + c->m_q) * 131 + L.g * 7 + (L.vec ? 1 : 0) + 1000LL * k;
+  return (c->n_q * 1000003LL + c->m_q) * 131 + L.g * 7 + (L.vec ? 1 : 0) + (L.seg ? 3 : 0) + 1000LL * k +
+         100000LL * c->tune.sweep_u;
 }
 
 cudaError_t solve_jacobi64(reach_ctx* c, const double* x0q, bool transposed) {
+  if (!transposed && layout(c, c->n_q, c->m_q, REACH_JACOBI_FP64).seg) return solve_jacobi_seg(c, x0q);
   cudaStream_t s = c->stream;
   const int64_t nq = c->n_q;
   double* xa = transposed ? c->vr : c->x;
@@ -867,15 +875,18 @@ cudaError_t solve_mixed(reach_ctx* c, const double* x0q) {
   else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
   k_apply<<<ew_grid(c, (const void*)k_apply, nq), NT, 0, s>>>(nq, c->x, c->xf, nullptr, c->st, 0);
   const Lay L = layout(c, nq, c->m_q, REACH_JACOBI_MIXED);
+  if (L.seg && (e = seg_plan(c)) != cudaSuccess) return e;
   const int k = c->tune.k;
   e = run_loop(c, c->g_exec[1], c->g_key[1], shape_key(c, L, k), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
-    LAY_DISPATCH(L, l_resid_hilo, c, 0, cs, &c->st->rowctr[0]);
+    if (L.seg) seg_resid_hilo(c, &c->st->slot[0], cs);
+    else LAY_DISPATCH(L, l_resid_hilo, c, 0, cs, &c->st->rowctr[0]);
     k_check_mixed<<<1, 1, 0, cs>>>(c->st, 0, k);
     // k - 1 FP32 sweeps: dl[1] -> dl[0] -> dl[1] ... ; k even, so the last lands in dl[0]
     for (int j = 1; j < k; ++j) {
       const float* din = (j & 1) ? c->dl[1] : c->dl[0];
       float* dout = (j & 1) ? c->dl[0] : c->dl[1];
-      LAY_DISPATCH(L, l_sweep32, c, din, dout, cs, &c->st->rowctr[j]);
+      if (L.seg) seg_sweep32(c, din, dout, cs);
+      else LAY_DISPATCH(L, l_sweep32, c, din, dout, cs, &c->st->rowctr[j]);
     }
     k_apply<<<ew_grid(c, (const void*)k_apply, nq), NT, 0, cs>>>(nq, c->x, c->xf, c->dl[0], c->st, k);
   });
@@ -1031,8 +1042,9 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return e;
   }
-  // 66: warp + vector loads with four quads per trip (FP32 sweep only)
-  const int codes[7] = {2, 4, 8, 16, 32, 64, 66};
+  // 66: warp + vector loads with four quads per trip (FP32 sweep only); 128: entry-balanced
+  // tiles (FP64 Jacobi and the FP32 sweep), which wins when a few rows are very long
+  const int codes[8] = {2, 4, 8, 16, 32, 64, 66, LAY_SEG};
   const double mean = (double)c->m_q / (double)c->n_q;
   Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_jv, c->bj};   // Jacobi form (the FP64 sweep)
   cudaStream_t s = c->stream;
@@ -1041,7 +1053,9 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
   for (int code : codes) {
     const Lay L = lay_of(code);
     if (code == 66 && method != REACH_JACOBI_MIXED) continue;
-    if (L.vec && mean < 16) continue;            // nothing to vectorise
+    if (L.seg && method == REACH_BICGSTAB_FP64) continue;
+    if (L.seg && (e = seg_plan(c)) != cudaSuccess) return e;
+    if (L.vec && !L.seg && mean < 16) continue;  // nothing to vectorise
     if (!L.vec && L.g > 4 * mean + 4) continue;  // mostly idle lanes
     if (method == REACH_JACOBI_MIXED) c->tune.sweep_u = code == 66 ? 4 : 2;
     unsigned* ctr = &c->st->rowctr[0];
@@ -1049,7 +1063,11 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
     for (int rep = 0; rep < 4; ++rep) {
       cudaMemsetAsync(ctr, 0, sizeof(unsigned), s);
       e = cudaEventRecord(c->ev0, s);
-      if (method == REACH_JACOBI_MIXED) {
+      if (L.seg && method == REACH_JACOBI_MIXED) {
+        seg_sweep32(c, c->dl[0], c->dl[1], s);
+      } else if (L.seg) {
+        seg_sweep(c, c->x, c->x2, &c->st->slot[62], s);
+      } else if (method == REACH_JACOBI_MIXED) {
         LAY_DISPATCH(L, l_sweep32, c, c->dl[0], c->dl[1], s, ctr);
       } else {
         LAY_DISPATCH(L, l_jacobi, c, y, c->x, c->x2, &c->st->slot[62], s, ctr);
@@ -1100,6 +1118,7 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
   }
   const int method = kernel == 0 ? REACH_JACOBI_FP64 : kernel == 3 ? REACH_BICGSTAB_FP64 : REACH_JACOBI_MIXED;
   const Lay L = layout(c, c->n_q, c->m_q, method);
+  if (L.seg && kernel != 3 && (e = seg_plan(c)) != cudaSuccess) return e;
   Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_jv, c->bj};   // Jacobi form (the FP64 sweep)
   SolveState hs;
   std::memset(&hs, 0, sizeof(hs));
@@ -1117,7 +1136,10 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
     unsigned* ctr = &c->st->rowctr[0];
     cudaMemsetAsync(ctr, 0, sizeof(unsigned), s);   // fresh row counter for every launch
     cudaMemsetAsync(&c->st->done, 0, sizeof(int32_t), s);
-    if (kernel == 0) LAY_DISPATCH(L, l_jacobi, c, y, c->x, c->x2, &c->st->slot[0], s, ctr);
+    if (L.seg && kernel == 0) seg_sweep(c, c->x, c->x2, &c->st->slot[0], s);
+    else if (L.seg && kernel == 1) seg_sweep32(c, c->dl[0], c->dl[1], s);
+    else if (L.seg && kernel == 2) seg_resid_hilo(c, &c->st->slot[0], s);
+    else if (kernel == 0) LAY_DISPATCH(L, l_jacobi, c, y, c->x, c->x2, &c->st->slot[0], s, ctr);
     else if (kernel == 1) LAY_DISPATCH(L, l_sweep32, c, c->dl[0], c->dl[1], s, ctr);
     else if (kernel == 2) LAY_DISPATCH(L, l_resid_hilo, c, 0, s, ctr);
     else LAY_DISPATCH(L, l_bi_v, c, s);
