@@ -356,7 +356,7 @@ def _timed_solves(R, torch, n, d_in, mode, eps, methods, stream):
         for meth in methods:
             extra = {}
             if meth in ("jacobi", "mixed", "bicgstab"):
-                R.reach_autotune(ctx, meth)
+                extra["lanes"] = R.reach_autotune(ctx, meth)["lanes"]
             if meth == "scc_jacobi":   # the decomposition, timed on its own, then the level sweeps
                 _, _, si = R.reach_scc(ctx, labels=False)
                 extra = {"decompose_ms": si["ms"], "n_scc": si["n_scc"], "n_levels": si["n_levels"],
