@@ -309,21 +309,25 @@ RDEV void push_chunks(int32_t L, const uint32_t* msize, const int64_t* mstart, i
   for (uint32_t j = 0; j < nch; ++j) qn[base + j] = (int32_t)(mstart[L] + (int64_t)j * SCC_CHUNK);
 }
 
-// One Kahn pass: a warp per queued chunk, a lane per member (up to 8 members a lane), so
-// a component of one row costs one warp trip and a giant component spreads over its
-// chunks.  Every member releases its edges from other components; a component whose
-// count of unreleased outgoing edges reaches 0 gets level h + 1 and queues its chunks.
+// One Kahn pass: a group of g lanes per queued chunk, the lanes taking the chunk's members
+// in turn.  g is the largest power of two up to 32 that still gives every chunk its own
+// group in one trip, so a pass of many one-row components (an acyclic chain) runs in one
+// trip while a few big chunks get a warp each.  Every member releases its edges from other
+// components; a component whose count of unreleased outgoing edges reaches 0 gets level
+// h + 1 and queues its chunks.
 RDEV void release_chunks(uint32_t size, const int32_t* __restrict__ qc, const int32_t* __restrict__ lab,
                          const uint32_t* __restrict__ msize, const int64_t* __restrict__ mstart,
                          const int32_t* __restrict__ mem, const int64_t* __restrict__ trp,
                          const int32_t* __restrict__ tcol, uint32_t* out_edges, int32_t* lvl, int32_t h,
                          int32_t* qn, uint32_t* cn, int64_t tid, int64_t nth) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t w = tid >> 5; w < (int64_t)size; w += nth >> 5) {
+  int g = 32;
+  while (g > 1 && (int64_t)size * g > nth) g >>= 1;
+  const int lane = (int)(tid & (g - 1));
+  for (int64_t w = tid / g; w < (int64_t)size; w += nth / g) {
     const int64_t p0 = qc[w];
     const int32_t L = lab[mem[p0]];
     const int64_t p1 = std::min<int64_t>(p0 + SCC_CHUNK, mstart[L] + msize[L]);
-    for (int64_t p = p0 + lane; p < p1; p += 32) {
+    for (int64_t p = p0 + lane; p < p1; p += g) {
       const int32_t v = mem[p];
       for (int64_t k = trp[v]; k < trp[v + 1]; ++k) {
         const int32_t Lu = lab[tcol[k]];
