@@ -678,6 +678,16 @@ static Lay layout(reach_ctx* c, int64_t rows, int64_t nnz, int method = 0) {
   return {g, vec};
 }
 
+// Row mapping for a kernel that has no entry-balanced form (the reported FP64
+// residual): the method's mapping, or the default one from the mean row length when
+// the method runs on entry-balanced tiles.
+static Lay row_layout(reach_ctx* c, int method) {
+  const Lay L = layout(c, c->n_q, c->m_q, method);
+  if (!L.seg) return L;
+  const int g = pick_group(c->n_q, c->m_q);
+  return {g, g == 32 && c->n_q > 0 && c->m_q / c->n_q >= 96};
+}
+
 #define LAY_DISPATCH(L, FN, ...)                          \
   do {                                                    \
     if ((L).vec) FN<32, true>(__VA_ARGS__);               \
@@ -848,7 +858,7 @@ cudaError_t solve_jacobi64(reach_ctx* c, const double* x0q, bool transposed) {
                      : Sys{nq, c->a_rowptr, c->a_col, c->a_jv, c->bj};
   Sys yr = transposed ? Sys{nq, c->at_rowptr, c->at_col, c->at_val, c->vp}
                       : Sys{nq, c->a_rowptr, c->a_col, c->a_val, c->b};
-  const Lay L = transposed ? layout(c, nq, c->m_q, -1) : layout(c, nq, c->m_q, REACH_JACOBI_FP64);
+  const Lay L = transposed ? row_layout(c, -1) : layout(c, nq, c->m_q, REACH_JACOBI_FP64);
   const int k = c->tune.k;
   const int gs = transposed ? 3 : 0;
   cudaError_t e = run_loop(c, c->g_exec[gs], c->g_key[gs], shape_key(c, L, k),
@@ -892,14 +902,15 @@ cudaError_t solve_mixed(reach_ctx* c, const double* x0q) {
   });
   if (e != cudaSuccess) return e;
   Sys y{nq, c->a_rowptr, c->a_col, c->a_val, c->b};
-  LAY_DISPATCH(L, l_resid, c, y, c->x, s);
+  const Lay LR = row_layout(c, REACH_JACOBI_MIXED);
+  LAY_DISPATCH(LR, l_resid, c, y, c->x, s);
   k_finalize_resid<<<1, 1, 0, s>>>(c->st);
   return cudaGetLastError();
 }
 
 // FP64 max|b - (I - A) x| of the final iterate into SolveState::resid.
 cudaError_t residual_report(reach_ctx* c, const double* xq) {
-  const Lay L = layout(c, c->n_q, c->m_q, REACH_JACOBI_FP64);
+  const Lay L = row_layout(c, REACH_JACOBI_FP64);
   Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_val, c->b};
   LAY_DISPATCH(L, l_resid, c, y, xq, c->stream);
   k_finalize_resid<<<1, 1, 0, c->stream>>>(c->st);
@@ -911,7 +922,7 @@ cudaError_t solve_bicgstab(reach_ctx* c, const double* x0q) {
   const int64_t nq = c->n_q;
   if (x0q) cudaMemcpyAsync(c->x, x0q, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
   else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
-  const Lay L = layout(c, nq, c->m_q, REACH_BICGSTAB_FP64);
+  const Lay L = row_layout(c, REACH_BICGSTAB_FP64);
   LAY_DISPATCH(L, l_bi_init, c, s);
   cudaError_t e = run_loop(c, c->g_exec[2], c->g_key[2], shape_key(c, L, 1), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
     k_bi_p<<<ew_grid(c, (const void*)k_bi_p, nq), NT, 0, cs>>>(nq, c->vr, c->vp, c->vv, c->vq, c->bi, c->st);
@@ -1129,8 +1140,8 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
     k_apply<<<ew_grid(c, (const void*)k_apply, c->n_q), NT, 0, s>>>(c->n_q, c->x, c->xf, nullptr, c->st, 0);
   }
   const int method = kernel == 0 ? REACH_JACOBI_FP64 : kernel == 3 ? REACH_BICGSTAB_FP64 : REACH_JACOBI_MIXED;
-  const Lay L = layout(c, c->n_q, c->m_q, method);
-  if (L.seg && kernel != 3 && (e = seg_plan(c)) != cudaSuccess) return e;
+  const Lay L = kernel == 3 ? row_layout(c, method) : layout(c, c->n_q, c->m_q, method);
+  if (L.seg && (e = seg_plan(c)) != cudaSuccess) return e;
   Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_jv, c->bj};   // Jacobi form (the FP64 sweep)
   SolveState hs;
   std::memset(&hs, 0, sizeof(hs));
