@@ -20,7 +20,7 @@
 namespace reach {
 
 constexpr int SEG_NT = 256;
-constexpr int SEG_ITEMS = 8;
+constexpr int SEG_ITEMS = 16;   // stored entries per thread (a multiple of 4, at most 32)
 constexpr int64_t SEG_T = SEG_NT * SEG_ITEMS;   // entries per tile
 
 struct SegPlan {
@@ -115,25 +115,26 @@ RDEV void seg_scan_cta(V& v, int& f, V* shv, int* shf) {
   __syncthreads();
 }
 
-// The three sweeps that run entry-balanced: what one stored entry contributes, and what
-// a finished row sum becomes.  finish() returns the row's contribution to the stopping
-// quantity (0 for the FP32 sweep, which has none).
+// The three sweeps that run entry-balanced: how a stored entry adds into a running row
+// sum (one FMA in the accumulation type, so a sum costs one FP64 instruction per entry
+// in the FP64 sweeps), and what a finished row sum becomes.  finish() returns the row's
+// contribution to the stopping quantity (0 for the FP32 sweep, which has none).
 struct OpJac64 {          // FP64 Jacobi on the Jacobi form: x' = bj + Aj x, max|x' - x|
   using V = double;
+  struct Q { double2 a, b; };
   static constexpr bool DELTA = true;
   const double* av;
   const double* x;
   const double* bj;
   double* xn;
-  RDEV void prod8(int64_t base, const int (&cc)[8], V (&p)[8]) const {
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      const double2 v = __ldcs(reinterpret_cast<const double2*>(av + base + 2 * h));
-      p[2 * h] = v.x * __ldg(x + cc[2 * h]);
-      p[2 * h + 1] = v.y * __ldg(x + cc[2 * h + 1]);
-    }
+  RDEV Q load4(int64_t k) const {
+    return {__ldcs(reinterpret_cast<const double2*>(av + k)), __ldcs(reinterpret_cast<const double2*>(av + k + 2))};
   }
-  RDEV V prod(int64_t k, int c) const { return __ldcs(av + k) * __ldg(x + c); }
+  RDEV V acc(V run, const Q& q, int u, int c) const {
+    const double v = u == 0 ? q.a.x : u == 1 ? q.a.y : u == 2 ? q.b.x : q.b.y;
+    return fma(v, __ldg(x + c), run);
+  }
+  RDEV V acc1(V run, int64_t k, int c) const { return fma(__ldcs(av + k), __ldg(x + c), run); }
   RDEV double finish(int64_t r, V s) const {
     const double xv = bj[r] + s;
     xn[r] = xv;
@@ -143,22 +144,18 @@ struct OpJac64 {          // FP64 Jacobi on the Jacobi form: x' = bj + Aj x, max
 
 struct OpSweep32 {        // FP32 correction sweep of the mixed method: d' = r + Aj_hi d
   using V = float;
+  using Q = float4;
   static constexpr bool DELTA = false;
   const float* ah;
   const float* din;
   const float* r32;
   float* dout;
-  RDEV void prod8(int64_t base, const int (&cc)[8], V (&p)[8]) const {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const float4 v = __ldcs(reinterpret_cast<const float4*>(ah + base + 4 * h));
-      p[4 * h] = v.x * __ldg(din + cc[4 * h]);
-      p[4 * h + 1] = v.y * __ldg(din + cc[4 * h + 1]);
-      p[4 * h + 2] = v.z * __ldg(din + cc[4 * h + 2]);
-      p[4 * h + 3] = v.w * __ldg(din + cc[4 * h + 3]);
-    }
+  RDEV Q load4(int64_t k) const { return __ldcs(reinterpret_cast<const float4*>(ah + k)); }
+  RDEV V acc(V run, const Q& q, int u, int c) const {
+    const float v = u == 0 ? q.x : u == 1 ? q.y : u == 2 ? q.z : q.w;
+    return fmaf(v, __ldg(din + c), run);
   }
-  RDEV V prod(int64_t k, int c) const { return __ldcs(ah + k) * __ldg(din + c); }
+  RDEV V acc1(V run, int64_t k, int c) const { return fmaf(__ldcs(ah + k), __ldg(din + c), run); }
   RDEV double finish(int64_t r, V s) const {
     dout[r] = r32[r] + s;
     return 0.0;
@@ -167,6 +164,7 @@ struct OpSweep32 {        // FP32 correction sweep of the mixed method: d' = r +
 
 struct OpResidHilo {      // FP64 residual of the mixed method: r = bj + Aj x - x, values hi + lo
   using V = double;
+  struct Q { float4 h, l; };
   static constexpr bool DELTA = true;
   const float* ah;
   const float* al;
@@ -175,21 +173,18 @@ struct OpResidHilo {      // FP64 residual of the mixed method: r = bj + Aj x - 
   const double* bj;
   float* r32;
   float* dl0;
-  // hi * x in FP64 (one FMA, with the integer widening), lo * x in FP32 (lo is below
-  // 2^-24 of the value), added in FP64
-  RDEV V one(float h, float l, int c) const { return fma(widen(h), __ldg(x + c), widen(l * __ldg(xf + c))); }
-  RDEV void prod8(int64_t base, const int (&cc)[8], V (&p)[8]) const {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const float4 hv = __ldcs(reinterpret_cast<const float4*>(ah + base + 4 * h));
-      const float4 lv = __ldcs(reinterpret_cast<const float4*>(al + base + 4 * h));
-      p[4 * h] = one(hv.x, lv.x, cc[4 * h]);
-      p[4 * h + 1] = one(hv.y, lv.y, cc[4 * h + 1]);
-      p[4 * h + 2] = one(hv.z, lv.z, cc[4 * h + 2]);
-      p[4 * h + 3] = one(hv.w, lv.w, cc[4 * h + 3]);
-    }
+  // hi * x in FP64 (the FMA, with the integer widening), lo * x in FP32 (lo is below
+  // 2^-24 of the value) and widened, added to the running sum in FP64
+  RDEV V one(V run, float h, float l, int c) const { return fma(widen(h), __ldg(x + c), run + widen(l * __ldg(xf + c))); }
+  RDEV Q load4(int64_t k) const {
+    return {__ldcs(reinterpret_cast<const float4*>(ah + k)), __ldcs(reinterpret_cast<const float4*>(al + k))};
   }
-  RDEV V prod(int64_t k, int c) const { return one(__ldcs(ah + k), __ldcs(al + k), c); }
+  RDEV V acc(V run, const Q& q, int u, int c) const {
+    const float h = u == 0 ? q.h.x : u == 1 ? q.h.y : u == 2 ? q.h.z : q.h.w;
+    const float l = u == 0 ? q.l.x : u == 1 ? q.l.y : u == 2 ? q.l.z : q.l.w;
+    return one(run, h, l, c);
+  }
+  RDEV V acc1(V run, int64_t k, int c) const { return one(run, __ldcs(ah + k), __ldcs(al + k), c); }
   RDEV double finish(int64_t r, V s) const {
     const double rv = bj[r] + s - x[r];
     const float rf = __double2float_rn(rv);
@@ -223,20 +218,15 @@ __global__ void __launch_bounds__(SEG_NT) k_seg_sweep(int64_t mq, int64_t ntiles
   double mx = 0.0;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t base = t * SEG_T + (int64_t)threadIdx.x * SEG_ITEMS;
-    // products of this thread's entries and their row-end flags
-    V p[SEG_ITEMS];
+    // this thread's row-end flags
     unsigned flags = 0;
-    if (base + SEG_ITEMS <= mq) {
-      const int4 c0 = __ldcs(reinterpret_cast<const int4*>(ci + base));
-      const int4 c1 = __ldcs(reinterpret_cast<const int4*>(ci + base + 4));
-      const int cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-      op.prod8(base, cc, p);
-      flags = (__ldg(endbits + (base >> 5)) >> (base & 31)) & 0xffu;
+    const bool full = base + SEG_ITEMS <= mq;
+    if (full) {
+      flags = (__ldg(endbits + (base >> 5)) >> (base & 31)) & ((1u << SEG_ITEMS) - 1u);
     } else {
 #pragma unroll
       for (int j = 0; j < SEG_ITEMS; ++j) {
         const int64_t k = base + j;
-        p[j] = k < mq ? op.prod(k, __ldcs(ci + k)) : V(0);
         if (k < mq && ((__ldg(endbits + (k >> 5)) >> (k & 31)) & 1u)) flags |= 1u << j;
       }
     }
@@ -257,13 +247,12 @@ __global__ void __launch_bounds__(SEG_NT) k_seg_sweep(int64_t mq, int64_t ntiles
       excl += off - cnt;
       __syncthreads();
     }
-    // thread-local pieces: head (up to the first row end), whole rows inside, tail
+    // running sums over this thread's entries: head (up to the first row end), whole rows
+    // inside, tail
     V head_v = V(0), run = V(0);
     int seen = 0;
     const int64_t row0 = tile_row0[t] + excl;    // nonempty index of this thread's first row
-#pragma unroll
-    for (int j = 0; j < SEG_ITEMS; ++j) {
-      run += p[j];
+    auto row_end = [&](int j) {
       if ((flags >> j) & 1u) {
         if (seen == 0) {
           head_v = run;                          // completed below, after the carry-in
@@ -273,6 +262,28 @@ __global__ void __launch_bounds__(SEG_NT) k_seg_sweep(int64_t mq, int64_t ntiles
         }
         ++seen;
         run = V(0);
+      }
+    };
+    if (full) {
+#pragma unroll
+      for (int q = 0; q < SEG_ITEMS / 4; ++q) {
+        const int4 c4 = __ldcs(reinterpret_cast<const int4*>(ci + base + 4 * q));
+        const typename Op::Q v4 = op.load4(base + 4 * q);
+        run = op.acc(run, v4, 0, c4.x);
+        row_end(4 * q);
+        run = op.acc(run, v4, 1, c4.y);
+        row_end(4 * q + 1);
+        run = op.acc(run, v4, 2, c4.z);
+        row_end(4 * q + 2);
+        run = op.acc(run, v4, 3, c4.w);
+        row_end(4 * q + 3);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < SEG_ITEMS; ++j) {
+        const int64_t k = base + j;
+        if (k < mq) run = op.acc1(run, k, __ldcs(ci + k));
+        row_end(j);
       }
     }
     // Segmented scan over threads: value = this thread's tail, a segment starts at every
