@@ -191,6 +191,7 @@ cudaError_t solve_jacobi_seg(reach_ctx* c, const double* x0q);
 cudaError_t seg_plan(reach_ctx* c);
 void seg_sweep(reach_ctx* c, const double* x, double* xn, unsigned long long* slot, cudaStream_t s);
 void seg_sweep32(reach_ctx* c, const float* din, float* dout, cudaStream_t s);
+void seg_spmv64(reach_ctx* c, const double* u, double* y, cudaStream_t s);
 void seg_resid_hilo(reach_ctx* c, unsigned long long* slot, cudaStream_t s);
 void seg_free(reach_ctx* c);
 // ---- scc.cu

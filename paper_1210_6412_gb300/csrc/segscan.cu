@@ -142,6 +142,27 @@ struct OpJac64 {          // FP64 Jacobi on the Jacobi form: x' = bj + Aj x, max
   }
 };
 
+struct OpSpmv64 {         // y = A u with the system's own values (the products of BiCGStab)
+  using V = double;
+  struct Q { double2 a, b; };
+  static constexpr bool DELTA = false;
+  const double* av;
+  const double* u;
+  double* y;
+  RDEV Q load4(int64_t k) const {
+    return {__ldcs(reinterpret_cast<const double2*>(av + k)), __ldcs(reinterpret_cast<const double2*>(av + k + 2))};
+  }
+  RDEV V acc(V run, const Q& q, int i, int c) const {
+    const double v = i == 0 ? q.a.x : i == 1 ? q.a.y : i == 2 ? q.b.x : q.b.y;
+    return fma(v, __ldg(u + c), run);
+  }
+  RDEV V acc1(V run, int64_t k, int c) const { return fma(__ldcs(av + k), __ldg(u + c), run); }
+  RDEV double finish(int64_t r, V s) const {
+    y[r] = s;
+    return 0.0;
+  }
+};
+
 struct OpSweep32 {        // FP32 correction sweep of the mixed method: d' = r + Aj_hi d
   using V = float;
   using Q = float4;
@@ -460,6 +481,10 @@ void seg_sweep(reach_ctx* c, const double* x, double* xn, unsigned long long* sl
 // Entry-balanced forms of the mixed method's two kernels (FP32 sweep, FP64 residual).
 void seg_sweep32(reach_ctx* c, const float* din, float* dout, cudaStream_t s) {
   seg_run(c, OpSweep32{c->a_hi, din, c->r32, dout}, nullptr, s);
+}
+
+void seg_spmv64(reach_ctx* c, const double* u, double* y, cudaStream_t s) {
+  seg_run(c, OpSpmv64{c->a_val, u, y}, nullptr, s);
 }
 
 void seg_resid_hilo(reach_ctx* c, unsigned long long* slot, cudaStream_t s) {

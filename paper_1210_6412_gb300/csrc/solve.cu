@@ -515,6 +515,33 @@ RDEV bool bi_restart_or_fail(BiState* bi, SolveState* st) {
   return true;
 }
 
+// After v = M p and q.v: a = y / q.v, or a breakdown restart.
+RDEV void bi_v_done(const double (&tot)[1], BiState* bi, SolveState* st) {
+  bi->qv = tot[0];
+  bi->restart = 0;
+  if (tot[0] == 0.0 || !(fabs(tot[0]) <= DBL_MAX)) {
+    if (bi_restart_or_fail(bi, st)) bi->skip = 1;
+  } else {
+    bi->a = bi->y / tot[0];
+  }
+}
+
+// After t = M s with t.s, t.t and max|s|: finish with x += a p when max|s| < eps, else
+// w = t.s / t.t.
+RDEV void bi_t_done(const double (&tot)[3], BiState* bi, SolveState* st) {
+  bi->ts = tot[0];
+  bi->tt = tot[1];
+  bi->snorm = tot[2];
+  if (tot[2] < st->eps) {
+    bi->s_done = 1;
+  } else if (tot[1] == 0.0) {
+    st->done = 1;
+    st->status = REACH_EBREAKDOWN;
+  } else {
+    bi->w = tot[0] / tot[1];
+  }
+}
+
 template <int G, bool V>
 __global__ void __launch_bounds__(NT) k_bi_v(int64_t nq, const int64_t* __restrict__ rp,
                                              const int32_t* __restrict__ ci,
@@ -539,15 +566,24 @@ __global__ void __launch_bounds__(NT) k_bi_v(int64_t nq, const int64_t* __restri
     }
   }
   double tot[1];
-  if (last_cta_reduce<1, 0>(acc, part, ticket, tot) && threadIdx.x == 0) {
-    bi->qv = tot[0];
-    bi->restart = 0;
-    if (tot[0] == 0.0 || !(fabs(tot[0]) <= DBL_MAX)) {
-      if (bi_restart_or_fail(bi, st)) bi->skip = 1;
-    } else {
-      bi->a = bi->y / tot[0];
-    }
+  if (last_cta_reduce<1, 0>(acc, part, ticket, tot) && threadIdx.x == 0) bi_v_done(tot, bi, st);
+}
+
+// v = M p from y = A p of the entry-balanced product: v_i = d_i p_i - y_i, q.v fused.
+__global__ void __launch_bounds__(NT) k_bi_v_ew(int64_t nq, const double* __restrict__ d,
+                                                const double* __restrict__ p, const double* __restrict__ y,
+                                                const double* __restrict__ q, double* __restrict__ v,
+                                                double* part, unsigned* ticket, BiState* bi, SolveState* st) {
+  if (st->done) return;
+  double acc[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double vi = d[i] * p[i] - y[i];
+    v[i] = vi;
+    acc[0] = fma(q[i], vi, acc[0]);
   }
+  double tot[1];
+  if (last_cta_reduce<1, 0>(acc, part, ticket, tot) && threadIdx.x == 0) bi_v_done(tot, bi, st);
 }
 
 // s = r - a v (elementwise; formed once here instead of at every gather of the next
@@ -587,19 +623,28 @@ __global__ void __launch_bounds__(NT) k_bi_t(int64_t nq, const int64_t* __restri
     }
   }
   double tot[3];
-  if (last_cta_reduce<2, 1>(acc, part, ticket, tot) && threadIdx.x == 0) {
-    bi->ts = tot[0];
-    bi->tt = tot[1];
-    bi->snorm = tot[2];
-    if (tot[2] < st->eps) {
-      bi->s_done = 1;
-    } else if (tot[1] == 0.0) {
-      st->done = 1;
-      st->status = REACH_EBREAKDOWN;
-    } else {
-      bi->w = tot[0] / tot[1];
-    }
+  if (last_cta_reduce<2, 1>(acc, part, ticket, tot) && threadIdx.x == 0) bi_t_done(tot, bi, st);
+}
+
+// t = M s from y = A s of the entry-balanced product: t_i = d_i s_i - y_i, with t.s, t.t
+// and max|s| fused.
+__global__ void __launch_bounds__(NT) k_bi_t_ew(int64_t nq, const double* __restrict__ d,
+                                                const double* __restrict__ sv, const double* __restrict__ y,
+                                                double* __restrict__ t, double* part, unsigned* ticket,
+                                                BiState* bi, SolveState* st) {
+  if (st->done || bi->skip) return;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double si = sv[i];
+    const double ti = d[i] * si - y[i];
+    t[i] = ti;
+    acc[0] = fma(ti, si, acc[0]);
+    acc[1] = fma(ti, ti, acc[1]);
+    acc[2] = fmax(acc[2], nan_to_inf(fabs(si)));
   }
+  double tot[3];
+  if (last_cta_reduce<2, 1>(acc, part, ticket, tot) && threadIdx.x == 0) bi_t_done(tot, bi, st);
 }
 
 __global__ void __launch_bounds__(NT) k_bi_x(int64_t nq, double* __restrict__ x,
@@ -922,13 +967,30 @@ cudaError_t solve_bicgstab(reach_ctx* c, const double* x0q) {
   const int64_t nq = c->n_q;
   if (x0q) cudaMemcpyAsync(c->x, x0q, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
   else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
+  const Lay LS = layout(c, nq, c->m_q, REACH_BICGSTAB_FP64);
   const Lay L = row_layout(c, REACH_BICGSTAB_FP64);
+  cudaError_t e = cudaSuccess;
+  if (LS.seg && (e = seg_plan(c)) != cudaSuccess) return e;
   LAY_DISPATCH(L, l_bi_init, c, s);
-  cudaError_t e = run_loop(c, c->g_exec[2], c->g_key[2], shape_key(c, L, 1), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
+  // entry-balanced products write y = A u into x2 (free during BiCGStab); the M u epilogue
+  // with its fused dots is then elementwise
+  e = run_loop(c, c->g_exec[2], c->g_key[2], shape_key(c, LS, 1), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
     k_bi_p<<<ew_grid(c, (const void*)k_bi_p, nq), NT, 0, cs>>>(nq, c->vr, c->vp, c->vv, c->vq, c->bi, c->st);
-    LAY_DISPATCH(L, l_bi_v, c, cs);
+    if (LS.seg) {
+      seg_spmv64(c, c->vp, c->x2, cs);
+      k_bi_v_ew<<<ew_grid(c, (const void*)k_bi_v_ew, nq), NT, 0, cs>>>(nq, c->d, c->vp, c->x2, c->vq, c->vv,
+                                                                       c->part, c->ticket, c->bi, c->st);
+    } else {
+      LAY_DISPATCH(L, l_bi_v, c, cs);
+    }
     k_bi_s<<<ew_grid(c, (const void*)k_bi_s, nq), NT, 0, cs>>>(nq, c->vr, c->vv, c->vs, c->bi, c->st);
-    LAY_DISPATCH(L, l_bi_t, c, cs);
+    if (LS.seg) {
+      seg_spmv64(c, c->vs, c->x2, cs);
+      k_bi_t_ew<<<ew_grid(c, (const void*)k_bi_t_ew, nq), NT, 0, cs>>>(nq, c->d, c->vs, c->x2, c->vt, c->part,
+                                                                       c->ticket, c->bi, c->st);
+    } else {
+      LAY_DISPATCH(L, l_bi_t, c, cs);
+    }
     k_bi_x<<<ew_grid(c, (const void*)k_bi_x, nq), NT, 0, cs>>>(nq, c->x, c->vp, c->vs, c->vt, c->vr, c->vq,
                                                                c->part, c->ticket, c->bi, c->st);
   });
@@ -1067,7 +1129,6 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
   for (int code : codes) {
     const Lay L = lay_of(code);
     if (code == 66 && method != REACH_JACOBI_MIXED) continue;
-    if (L.seg && method == REACH_BICGSTAB_FP64) continue;
     if (L.seg && (e = seg_plan(c)) != cudaSuccess) return e;
     if (L.vec && !L.seg && mean < 16) continue;  // nothing to vectorise
     if (!L.vec && L.g > 4 * mean + 4) continue;  // mostly idle lanes
@@ -1080,6 +1141,7 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
     for (int part = 0; part < parts; ++part) {
       for (int rep = 0; rep < 4; ++rep) {
         cudaMemsetAsync(ctr, 0, sizeof(unsigned), s);
+        cudaMemsetAsync(&c->st->done, 0, sizeof(int32_t), s);   // a candidate must never see a finished state
         e = cudaEventRecord(c->ev0, s);
         if (part == 1 && L.seg) {
           seg_resid_hilo(c, &c->st->slot[62], s);
@@ -1087,6 +1149,11 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
           LAY_DISPATCH(L, l_resid_hilo, c, 62, s, ctr);
         } else if (L.seg && method == REACH_JACOBI_MIXED) {
           seg_sweep32(c, c->dl[0], c->dl[1], s);
+        } else if (L.seg && method == REACH_BICGSTAB_FP64) {
+          seg_spmv64(c, c->b, c->x2, s);
+          k_bi_v_ew<<<ew_grid(c, (const void*)k_bi_v_ew, c->n_q), NT, 0, s>>>(c->n_q, c->d, c->b, c->x2, c->b,
+                                                                             c->vv, c->part, c->ticket, c->bi,
+                                                                             c->st);
         } else if (L.seg) {
           seg_sweep(c, c->x, c->x2, &c->st->slot[62], s);
         } else if (method == REACH_JACOBI_MIXED) {
@@ -1140,7 +1207,7 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
     k_apply<<<ew_grid(c, (const void*)k_apply, c->n_q), NT, 0, s>>>(c->n_q, c->x, c->xf, nullptr, c->st, 0);
   }
   const int method = kernel == 0 ? REACH_JACOBI_FP64 : kernel == 3 ? REACH_BICGSTAB_FP64 : REACH_JACOBI_MIXED;
-  const Lay L = kernel == 3 ? row_layout(c, method) : layout(c, c->n_q, c->m_q, method);
+  const Lay L = layout(c, c->n_q, c->m_q, method);
   if (L.seg && (e = seg_plan(c)) != cudaSuccess) return e;
   Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_jv, c->bj};   // Jacobi form (the FP64 sweep)
   SolveState hs;
@@ -1162,6 +1229,11 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
     if (L.seg && kernel == 0) seg_sweep(c, c->x, c->x2, &c->st->slot[0], s);
     else if (L.seg && kernel == 1) seg_sweep32(c, c->dl[0], c->dl[1], s);
     else if (L.seg && kernel == 2) seg_resid_hilo(c, &c->st->slot[0], s);
+    else if (L.seg && kernel == 3) {
+      seg_spmv64(c, c->vp, c->x2, s);
+      k_bi_v_ew<<<ew_grid(c, (const void*)k_bi_v_ew, c->n_q), NT, 0, s>>>(c->n_q, c->d, c->vp, c->x2, c->vq, c->vv,
+                                                                         c->part, c->ticket, c->bi, c->st);
+    }
     else if (kernel == 0) LAY_DISPATCH(L, l_jacobi, c, y, c->x, c->x2, &c->st->slot[0], s, ctr);
     else if (kernel == 1) LAY_DISPATCH(L, l_sweep32, c, c->dl[0], c->dl[1], s, ctr);
     else if (kernel == 2) LAY_DISPATCH(L, l_resid_hilo, c, 0, s, ctr);

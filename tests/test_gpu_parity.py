@@ -297,17 +297,17 @@ def test_injected_allocation_failure(monkeypatch):
 
 
 @pytest.mark.parametrize("name", ["skewed", "random", "dense", "gambler"])
-@pytest.mark.parametrize("method,tol", [("jacobi", TOL_FP64), ("mixed", TOL_MIXED)])
+@pytest.mark.parametrize("method,tol", [("jacobi", TOL_FP64), ("mixed", TOL_MIXED), ("bicgstab", TOL_FP64)])
 def test_entry_balanced_layout_matches_oracle(c1, name, method, tol, monkeypatch):
-    """REACH_LANES=128: FP64 Jacobi and both kernels of the mixed method (FP64 residual,
-    FP32 sweep) on entry-balanced tiles instead of a row mapping."""
+    """REACH_LANES=128: FP64 Jacobi, both kernels of the mixed method (FP64 residual, FP32
+    sweep) and the two BiCGStab products on entry-balanced tiles instead of a row mapping."""
     monkeypatch.setenv("REACH_LANES", "128")
     c = {"random": lambda: c1,
          "skewed": lambda: synth.skewed_chain(n=20000, hub_deg=9000),
          "dense": lambda: synth.dense_random_chain(n=2000, density=0.1, sink_frac=0.02, seed=5),
          "gambler": lambda: synth.gamblers_ruin(40, 0.45)}[name]()
     cls_o, x_o = oracle_solution(c)
-    cls, x, info = gpu_solve(c, O.PROB01, method, 1e-13 if method == "jacobi" else 1e-11)
+    cls, x, info = gpu_solve(c, O.PROB01, method, 1e-11 if method == "mixed" else 1e-13)
     assert np.array_equal(cls, cls_o)
     assert info["status"] == R.REACH_OK
     assert np.max(np.abs(x - x_o)) <= tol
@@ -320,9 +320,10 @@ def test_autotuner_may_pick_entry_balanced_tiles():
     cls_o = O.partition(c.n, c.rowptr, c.col, c.val, c.goal)
     need_gpu()
     with R.Solver(c.n, c.rowptr, c.col, c.val, c.goal) as s:
-        picks = {m: s.autotune(m)["lanes"] for m in ("jacobi", "mixed")}
+        picks = {m: s.autotune(m)["lanes"] for m in ("jacobi", "mixed", "bicgstab")}
         xj, ij = s.solve("jacobi", eps=1e-12, max_iter=1_000_000)
         xm, im = s.solve("mixed", eps=1e-11, max_iter=1_000_000)
+        xb, ib = s.solve("bicgstab", eps=1e-12, max_iter=10_000)
     assert all(p in (2, 4, 8, 16, 32, 64, 66, 128) for p in picks.values())
-    assert ij["status"] == R.REACH_OK and im["status"] == R.REACH_OK
-    assert np.max(np.abs(xj - xm)) <= TOL_MIXED
+    assert ij["status"] == R.REACH_OK and im["status"] == R.REACH_OK and ib["status"] == R.REACH_OK
+    assert np.max(np.abs(xj - xm)) <= TOL_MIXED and np.max(np.abs(xj - xb)) <= 1e-9
