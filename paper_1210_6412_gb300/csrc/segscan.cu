@@ -223,7 +223,7 @@ RDEV void delta_to_slot(double mx, unsigned long long* slot) {
 }
 
 template <class Op>
-__global__ void __launch_bounds__(SEG_NT, 4) k_seg_sweep(int64_t mq, int64_t ntiles, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(SEG_NT) k_seg_sweep(int64_t mq, int64_t ntiles, const int64_t* __restrict__ rp,
                                                       const int32_t* __restrict__ ci, Op op,
                                                       const uint32_t* __restrict__ endbits,
                                                       const int64_t* __restrict__ tile_row0,
@@ -269,23 +269,20 @@ __global__ void __launch_bounds__(SEG_NT, 4) k_seg_sweep(int64_t mq, int64_t nti
       __syncthreads();
     }
     // running sums over this thread's entries: head (up to the first row end), whole rows
-    // inside, tail.  Even and odd entries go to two sums, which halves the dependent FMA
-    // chain; a row end adds the two.
-    V head_v = V(0), ra = V(0), rb = V(0);
+    // inside, tail
+    V head_v = V(0), run = V(0);
     int seen = 0;
     const int64_t row0 = tile_row0[t] + excl;    // nonempty index of this thread's first row
     auto row_end = [&](int j) {
       if ((flags >> j) & 1u) {
-        const V tot = ra + rb;
         if (seen == 0) {
-          head_v = tot;                          // completed below, after the carry-in
+          head_v = run;                          // completed below, after the carry-in
         } else {
           const int64_t r = nonempty[row0 + seen];   // row entirely inside this thread
-          mx = fmax(mx, op.finish(r, tot));
+          mx = fmax(mx, op.finish(r, run));
         }
         ++seen;
-        ra = V(0);
-        rb = V(0);
+        run = V(0);
       }
     };
     if (full) {
@@ -293,27 +290,23 @@ __global__ void __launch_bounds__(SEG_NT, 4) k_seg_sweep(int64_t mq, int64_t nti
       for (int q = 0; q < SEG_ITEMS / 4; ++q) {
         const int4 c4 = __ldcs(reinterpret_cast<const int4*>(ci + base + 4 * q));
         const typename Op::Q v4 = op.load4(base + 4 * q);
-        ra = op.acc(ra, v4, 0, c4.x);
+        run = op.acc(run, v4, 0, c4.x);
         row_end(4 * q);
-        rb = op.acc(rb, v4, 1, c4.y);
+        run = op.acc(run, v4, 1, c4.y);
         row_end(4 * q + 1);
-        ra = op.acc(ra, v4, 2, c4.z);
+        run = op.acc(run, v4, 2, c4.z);
         row_end(4 * q + 2);
-        rb = op.acc(rb, v4, 3, c4.w);
+        run = op.acc(run, v4, 3, c4.w);
         row_end(4 * q + 3);
       }
     } else {
 #pragma unroll
       for (int j = 0; j < SEG_ITEMS; ++j) {
         const int64_t k = base + j;
-        if (k < mq) {
-          if (j & 1) rb = op.acc1(rb, k, __ldcs(ci + k));
-          else ra = op.acc1(ra, k, __ldcs(ci + k));
-        }
+        if (k < mq) run = op.acc1(run, k, __ldcs(ci + k));
         row_end(j);
       }
     }
-    const V run = ra + rb;
     // Segmented scan over threads: value = this thread's tail, a segment starts at every
     // thread with a row end.  The exclusive result is the part of this thread's first row
     // that lies in earlier threads of the tile.
