@@ -129,21 +129,6 @@ RDEV bool grid_barrier(const GridBar& gb) {
 }
 
 
-constexpr int CL_SIZE = 16;       // CTAs of the cluster that runs small levels (non-portable size)
-constexpr int CL_NT = 512;
-
-// Barrier of the launch: the whole grid (cooperative launch), or one thread-block
-// cluster (hardware barrier with release / acquire semantics at cluster scope).
-template <bool CLUSTER>
-RDEV bool sync_all(const GridBar& gb) {
-  if constexpr (CLUSTER) {
-    cooperative_groups::this_cluster().sync();
-    return true;
-  } else {
-    return grid_barrier(gb);
-  }
-}
-
 RDEV uint32_t push_slot(uint32_t* count) { return atomicAdd(count, 1u); }
 
 // One pass of the decomposition phase stored in ss->phase; the last CTA to finish
@@ -366,8 +351,8 @@ enum : int { PC_CHG = 3, PC_CORE = 6, PC_FAIL = 7, PC_ALLSINK = 8 };
 
 RDEV unsigned ld_vol(const unsigned* p) { return *(const volatile unsigned*)p; }
 
-template <int G, bool CLUSTER>
-__global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 2) k_scc_persist(int64_t nq, const int64_t* __restrict__ arp,
+template <int G>
+__global__ void __launch_bounds__(SCC_NT, 2) k_scc_persist(int64_t nq, const int64_t* __restrict__ arp,
                                                           const int32_t* __restrict__ acol,
                                                           const int64_t* __restrict__ trp,
                                                           const int32_t* __restrict__ tcol, int32_t* lab,
@@ -399,7 +384,7 @@ __global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 2) k_s
     }
   }
   if (lead) pc[2] = 0u;
-  if (!sync_all<CLUSTER>(gb)) return;
+  if (!grid_barrier(gb)) return;
   f = 1;
   for (;;) {
     const unsigned size = ld_vol(pc + f % 3);
@@ -420,7 +405,7 @@ __global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 2) k_s
         }
       }
     }
-    if (!sync_all<CLUSTER>(gb)) return;
+    if (!grid_barrier(gb)) return;
     ++f;
   }
   if (seen >= nq) {   // acyclic: every component is one row, and its level is known
@@ -449,7 +434,7 @@ __global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 2) k_s
         qn[atomicAdd(cn, 1u)] = (int32_t)v;
       }
     }
-    if (!sync_all<CLUSTER>(gb)) return;
+    if (!grid_barrier(gb)) return;
     ++f;
   }
   for (;;) {
@@ -473,7 +458,7 @@ __global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 2) k_s
         if (atomicSub(outdeg + u, 1u) == 1u && atomicCAS(lab + u, -1, u) == -1) qn[atomicAdd(cn, 1u)] = u;
       }
     }
-    if (!sync_all<CLUSTER>(gb)) return;
+    if (!grid_barrier(gb)) return;
     ++f;
   }
   // colouring rounds on the cyclic core
@@ -485,7 +470,7 @@ __global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 2) k_s
       for (int64_t v = tid; v < nq; v += nth)
         if (color[v] >= 0) lab[v] = core;
       exact = false;
-      if (!sync_all<CLUSTER>(gb)) return;
+      if (!grid_barrier(gb)) return;
       break;
     }
     // every row left starts with its own index as colour and seeds the first
@@ -502,7 +487,7 @@ __global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 2) k_s
         qn[atomicAdd(cn, 1u)] = (int32_t)v;
         if (round == 0) atomicMax(reinterpret_cast<int*>(pc + PC_CORE), (int)v);
       }
-      if (!sync_all<CLUSTER>(gb)) return;
+      if (!grid_barrier(gb)) return;
       ++f;
     }
     // max-label propagation over the frontier of rows whose colour rose in the last
@@ -524,7 +509,7 @@ __global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 2) k_s
             qn[atomicAdd(cn, 1u)] = u;
         }
       }
-      if (!sync_all<CLUSTER>(gb)) return;
+      if (!grid_barrier(gb)) return;
       ++f;
     }
     // roots seed a frontier (step f); the backward search inside each colour follows
@@ -538,7 +523,7 @@ __global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 2) k_s
           qn[atomicAdd(cn, 1u)] = (int32_t)v;
         }
       }
-      if (!sync_all<CLUSTER>(gb)) return;
+      if (!grid_barrier(gb)) return;
       ++f;
     }
     for (;;) {
@@ -558,7 +543,7 @@ __global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 2) k_s
           if (atomicCAS(lab + u, -1, cv) == -1) qn[atomicAdd(cn, 1u)] = u;
         }
       }
-      if (!sync_all<CLUSTER>(gb)) return;
+      if (!grid_barrier(gb)) return;
       ++f;
     }
     ++round;
@@ -572,8 +557,8 @@ __global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 2) k_s
   }
 }
 
-template <int G, bool CLUSTER>
-__global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 2) k_lvl_persist(int64_t nq, const int64_t* __restrict__ trp,
+template <int G>
+__global__ void __launch_bounds__(SCC_NT, 2) k_lvl_persist(int64_t nq, const int64_t* __restrict__ trp,
                                                           const int32_t* __restrict__ tcol,
                                                           const int32_t* __restrict__ lab,
                                                           const uint32_t* __restrict__ msize,
@@ -597,7 +582,7 @@ __global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 2) k_l
     }
   }
   if (lead) pc[2] = 0u;
-  if (!sync_all<CLUSTER>(gb)) return;
+  if (!grid_barrier(gb)) return;
   RowGroups rg = RowGroups::make<G>();
   int64_t f = 1;
   for (;; ++f) {
@@ -609,7 +594,7 @@ __global__ void __launch_bounds__(CLUSTER ? CL_NT : SCC_NT, CLUSTER ? 1 : 2) k_l
     unsigned* cn = pc + (f + 1) % 3;
     if (lead) pc[(f + 2) % 3] = 0u;
     release_chunks(size, qc, lab, msize, mstart, mem, trp, tcol, out_edges, lvl, h, qn, cn, tid, nth);
-    if (!sync_all<CLUSTER>(gb)) return;
+    if (!grid_barrier(gb)) return;
   }
   if (lead) {
     ss->n_levels = (int32_t)(f - 1);
@@ -855,6 +840,21 @@ __global__ void __launch_bounds__(SCC_NT) k_blk_apply(double* x, const double* _
 
 // ---------------------------------------------------------------- block solve, persistent launches
 
+constexpr int CL_SIZE = 16;       // CTAs of the cluster that runs small levels (non-portable size)
+constexpr int CL_NT = 512;
+
+// Barrier of the launch: the whole grid (cooperative launch), or one thread-block
+// cluster (hardware barrier with release / acquire semantics at cluster scope).
+template <bool CLUSTER>
+RDEV bool sync_all(const GridBar& gb) {
+  if constexpr (CLUSTER) {
+    cooperative_groups::this_cluster().sync();
+    return true;
+  } else {
+    return grid_barrier(gb);
+  }
+}
+
 // Levels [h0, h1) of the level-by-level Jacobi in one launch: the CTAs walk the levels
 // in order, with a barrier after every sweep instead of a kernel boundary.  Big levels
 // run on the whole GPU (a cooperative grid with grid barriers); runs of small levels, the
@@ -1047,49 +1047,6 @@ static bool use_persistent(reach_ctx* c) {
   return cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device) == cudaSuccess && coop;
 }
 
-// Largest cluster (16, else 8, else 0) of CL_NT-thread CTAs the device can host for fn.
-static int cluster_size_of(const void* fn) {
-  for (int cs : {CL_SIZE, 8}) {
-    if (cs > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cs);
-    cfg.blockDim = dim3(CL_NT);
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = cs;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n > 0) return cs;
-    cudaGetLastError();
-  }
-  return 0;
-}
-
-// One thread-block cluster of cs CTAs running fn (a kernel that synchronises with the
-// cluster barrier).
-template <typename... A>
-static cudaError_t cluster_launch(reach_ctx* c, const void* fn, int cs, A... a) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cs);
-  cfg.blockDim = dim3(CL_NT);
-  cfg.stream = c->stream;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = cs;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  void* args[] = {(void*)&a...};
-  return cudaLaunchKernelExC(&cfg, fn, args);
-}
-
 template <typename... A>
 static cudaError_t coop_launch(reach_ctx* c, const void* fn, A... a) {
   int per_sm = 0;
@@ -1174,28 +1131,14 @@ cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok) {
   int32_t* q1 = c->queue + c->n;
   const int64_t key_base = nq * 7919 + c->m_q;
   const bool persistent = use_persistent(c);
-  // the persistent passes run on one thread-block cluster (a barrier of about 0.2 us
-  // against 3-5 us for the whole grid: most passes are narrow frontiers), unless
-  // REACH_SCC_CLUSTER=0
-  const char* cv = std::getenv("REACH_SCC_CLUSTER");
-  const bool cluster_ok = !(cv && cv[0] == '0');
   bool acyclic = false;   // the sink-side trimming found every component and level
   int32_t status = 0;
   if (persistent) {
     cudaMemsetAsync(sp->pc, 0, 16 * sizeof(unsigned), s);
     cudaMemsetAsync(sp->bar, 0, 4 * sizeof(unsigned), s);
-#define SCC_P(G)                                                                                            \
-  do {                                                                                                      \
-    const int cs = cluster_ok ? cluster_size_of((const void*)k_scc_persist<G, true>) : 0;                  \
-    if (cs > 0)                                                                                             \
-      e = cluster_launch(c, (const void*)k_scc_persist<G, true>, cs, nq, c->a_rowptr, c->a_col,            \
-                         c->at_rowptr, c->at_col, sp->lab, sp->color, sp->indeg, sp->outdeg, sp->lvl, q0,   \
-                         q1, sp->pc, max_rounds, bound, sp->ss, GridBar{sp->bar, sp->bar + 1, sp->bar + 2}); \
-    else                                                                                                    \
-      e = coop_launch(c, (const void*)k_scc_persist<G, false>, nq, c->a_rowptr, c->a_col, c->at_rowptr,    \
-                      c->at_col, sp->lab, sp->color, sp->indeg, sp->outdeg, sp->lvl, q0, q1, sp->pc,        \
-                      max_rounds, bound, sp->ss, GridBar{sp->bar, sp->bar + 1, sp->bar + 2});               \
-  } while (0)
+#define SCC_P(G) e = coop_launch(c, (const void*)k_scc_persist<G>, nq, c->a_rowptr, c->a_col, c->at_rowptr,    \
+                                 c->at_col, sp->lab, sp->color, sp->indeg, sp->outdeg, sp->lvl, q0, q1,        \
+                                 sp->pc, max_rounds, bound, sp->ss, GridBar{sp->bar, sp->bar + 1, sp->bar + 2})
     SCC_G_DISPATCH(g, SCC_P)
 #undef SCC_P
     if (e != cudaSuccess) return e;
@@ -1237,18 +1180,9 @@ cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok) {
   if (persistent && !acyclic) {
     cudaMemsetAsync(sp->pc, 0, 16 * sizeof(unsigned), s);
     cudaMemsetAsync(sp->bar, 0, 4 * sizeof(unsigned), s);
-#define LVL_P(G)                                                                                            \
-  do {                                                                                                      \
-    const int cs = cluster_ok ? cluster_size_of((const void*)k_lvl_persist<G, true>) : 0;                  \
-    if (cs > 0)                                                                                             \
-      e = cluster_launch(c, (const void*)k_lvl_persist<G, true>, cs, nq, c->at_rowptr, c->at_col, sp->lab, \
-                         sp->msize, sp->mstart, sp->mem, out_edges, sp->lvl, q0, q1, sp->pc, sp->ss,        \
-                         GridBar{sp->bar, sp->bar + 1, sp->bar + 2});                                       \
-    else                                                                                                    \
-      e = coop_launch(c, (const void*)k_lvl_persist<G, false>, nq, c->at_rowptr, c->at_col, sp->lab,       \
-                      sp->msize, sp->mstart, sp->mem, out_edges, sp->lvl, q0, q1, sp->pc, sp->ss,           \
-                      GridBar{sp->bar, sp->bar + 1, sp->bar + 2});                                          \
-  } while (0)
+#define LVL_P(G) e = coop_launch(c, (const void*)k_lvl_persist<G>, nq, c->at_rowptr, c->at_col, sp->lab,     \
+                                 sp->msize, sp->mstart, sp->mem, out_edges, sp->lvl, q0, q1, sp->pc, sp->ss,  \
+                                 GridBar{sp->bar, sp->bar + 1, sp->bar + 2})
     SCC_G_DISPATCH(g, LVL_P)
 #undef LVL_P
     if (e != cudaSuccess) return e;
@@ -1347,7 +1281,27 @@ static cudaError_t launch_grid_run(reach_ctx* c, SccPlan* sp, int32_t h0, int32_
 // Cluster size the device can host for the small-level kernel (16, else 8, else 0).
 template <int G>
 static int cluster_size(reach_ctx* c) {
-  return cluster_size_of((const void*)k_blk_persist<G, true>);
+  const void* fn = (const void*)k_blk_persist<G, true>;
+  for (int cs : {CL_SIZE, 8}) {
+    if (cs > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(CL_NT);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n > 0) return cs;
+    cudaGetLastError();
+  }
+  return 0;
 }
 
 template <int G>

@@ -36,15 +36,12 @@ CHAINS = {
 
 
 @pytest.mark.parametrize("name", sorted(CHAINS))
-@pytest.mark.parametrize("driver", ["cluster", "grid", "graph", "host"])
+@pytest.mark.parametrize("driver", ["persistent", "graph", "host"])
 def test_labels_and_levels_bit_exact(name, driver, monkeypatch):
-    """Four drivers of the same passes: persistent launches on one thread-block cluster
-    (default), persistent cooperative grids (REACH_SCC_CLUSTER=0), conditional-while graphs
-    (REACH_SCC_GRAPH=1), and host-driven loops."""
+    """Three drivers of the same passes: cooperative launches with grid barriers (default),
+    conditional-while graphs (REACH_SCC_GRAPH=1), and host-driven loops."""
     need_gpu()
-    if driver == "grid":
-        monkeypatch.setenv("REACH_SCC_CLUSTER", "0")
-    if driver in ("graph", "host"):
+    if driver != "persistent":
         monkeypatch.setenv("REACH_SCC_GRAPH", "1")
     if driver == "host":
         monkeypatch.setenv("REACH_HOST_LOOPS", "1")
