@@ -53,7 +53,7 @@ struct BfsState {
 
 struct Tuning {
   int g = 0;            // lanes per row for CSR kernels (0 = pick from mean degree; 64 = warp + vector
-                        // loads; 128 = entry-balanced tiles, FP64 Jacobi and the mixed method only)
+                        // loads; 80 = FP32 sweep staged by bulk copies; 128 = entry-balanced tiles)
   int gm[3] = {0, 0, 0};  // autotuned lanes-per-row code per method (0 = none)
   int k = 16;           // sweeps between convergence checks / refinement period
   int k_auto = 0;       // autotuned sweeps between checks for FP64 Jacobi (0 = none)
@@ -194,6 +194,8 @@ void seg_sweep32(reach_ctx* c, const float* din, float* dout, cudaStream_t s);
 void seg_spmv64(reach_ctx* c, const double* u, double* y, cudaStream_t s);
 void seg_resid_hilo(reach_ctx* c, unsigned long long* slot, cudaStream_t s);
 void seg_free(reach_ctx* c);
+// ---- tma.cu
+void sweep32_tma(reach_ctx* c, const float* din, float* dout, cudaStream_t s, unsigned* ctr);
 // ---- scc.cu
 cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok);
 cudaError_t scc_outputs(reach_ctx* c, int32_t* label, int32_t* level, cudaMemcpyKind kind, reach_scc_info* info);

@@ -704,12 +704,15 @@ struct Lay {
   int g;
   bool vec;
   bool seg = false;     // entry-balanced tiles (segscan.cu) instead of a row mapping
+  bool tma = false;     // FP32 sweep with rows staged by bulk copies (tma.cu); others as 64
 };
 
 constexpr int LAY_SEG = 128;
+constexpr int LAY_TMA = 80;
 
 static Lay lay_of(int code) {
   if (code == LAY_SEG) return Lay{32, true, true};
+  if (code == LAY_TMA) return Lay{32, true, false, true};
   return code >= 64 ? Lay{32, true} : Lay{code, false};
 }
 
@@ -884,7 +887,8 @@ cudaError_t run_loop(reach_ctx* c, cudaGraphExec_t& exec, int64_t& exec_key, int
 }
 
 static int64_t shape_key(reach_ctx* c, const Lay& L, int k) {
-  return (c->n_q * 1000003LL + c->m_q) * 131 + L.g * 7 + (L.vec ? 1 : 0) + (L.seg ? 3 : 0) + 1000LL * k +
+  return (c->n_q * 1000003LL + c->m_q) * 131 + L.g * 7 + (L.vec ? 1 : 0) + (L.seg ? 3 : 0) + (L.tma ? 5 : 0) +
+         1000LL * k +
          100000LL * c->tune.sweep_u;
 }
 
@@ -941,6 +945,7 @@ cudaError_t solve_mixed(reach_ctx* c, const double* x0q) {
       const float* din = (j & 1) ? c->dl[1] : c->dl[0];
       float* dout = (j & 1) ? c->dl[0] : c->dl[1];
       if (L.seg) seg_sweep32(c, din, dout, cs);
+      else if (L.tma) sweep32_tma(c, din, dout, cs, &c->st->rowctr[j]);
       else LAY_DISPATCH(L, l_sweep32, c, din, dout, cs, &c->st->rowctr[j]);
     }
     k_apply<<<ew_grid(c, (const void*)k_apply, nq), NT, 0, cs>>>(nq, c->x, c->xf, c->dl[0], c->st, k);
@@ -1120,7 +1125,7 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
   }
   // 66: warp + vector loads with four quads per trip (FP32 sweep only); 128: entry-balanced
   // tiles (FP64 Jacobi and the FP32 sweep), which wins when a few rows are very long
-  const int codes[8] = {2, 4, 8, 16, 32, 64, 66, LAY_SEG};
+  const int codes[9] = {2, 4, 8, 16, 32, 64, 66, LAY_TMA, LAY_SEG};
   const double mean = (double)c->m_q / (double)c->n_q;
   Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_jv, c->bj};   // Jacobi form (the FP64 sweep)
   cudaStream_t s = c->stream;
@@ -1128,7 +1133,8 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
   int pick = 0;
   for (int code : codes) {
     const Lay L = lay_of(code);
-    if (code == 66 && method != REACH_JACOBI_MIXED) continue;
+    if ((code == 66 || code == LAY_TMA) && method != REACH_JACOBI_MIXED) continue;
+    if (code == LAY_TMA && mean < 64) continue;  // segments of 512 entries want long rows
     if (L.seg && (e = seg_plan(c)) != cudaSuccess) return e;
     if (L.vec && !L.seg && mean < 16) continue;  // nothing to vectorise
     if (!L.vec && L.g > 4 * mean + 4) continue;  // mostly idle lanes
@@ -1147,6 +1153,8 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
           seg_resid_hilo(c, &c->st->slot[62], s);
         } else if (part == 1) {
           LAY_DISPATCH(L, l_resid_hilo, c, 62, s, ctr);
+        } else if (L.tma) {
+          sweep32_tma(c, c->dl[0], c->dl[1], s, ctr);
         } else if (L.seg && method == REACH_JACOBI_MIXED) {
           seg_sweep32(c, c->dl[0], c->dl[1], s);
         } else if (L.seg && method == REACH_BICGSTAB_FP64) {
@@ -1228,6 +1236,7 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
     cudaMemsetAsync(&c->st->done, 0, sizeof(int32_t), s);
     if (L.seg && kernel == 0) seg_sweep(c, c->x, c->x2, &c->st->slot[0], s);
     else if (L.seg && kernel == 1) seg_sweep32(c, c->dl[0], c->dl[1], s);
+    else if (L.tma && kernel == 1) sweep32_tma(c, c->dl[0], c->dl[1], s, ctr);
     else if (L.seg && kernel == 2) seg_resid_hilo(c, &c->st->slot[0], s);
     else if (L.seg && kernel == 3) {
       seg_spmv64(c, c->vp, c->x2, s);

@@ -327,3 +327,21 @@ def test_autotuner_may_pick_entry_balanced_tiles():
     assert all(p in (2, 4, 8, 16, 32, 64, 66, 128) for p in picks.values())
     assert ij["status"] == R.REACH_OK and im["status"] == R.REACH_OK and ib["status"] == R.REACH_OK
     assert np.max(np.abs(xj - xm)) <= TOL_MIXED and np.max(np.abs(xj - xb)) <= 1e-9
+
+
+@pytest.mark.parametrize("name", ["dense", "random", "skewed", "gambler"])
+def test_bulk_copy_staged_sweep_matches_oracle(c1, name, monkeypatch):
+    """REACH_LANES=80: the mixed method's FP32 sweep with each row staged through shared
+    memory by bulk copies (segments aligned to 8 entries, neighbour entries masked)."""
+    monkeypatch.setenv("REACH_LANES", "80")
+    c = {"random": lambda: c1,
+         "skewed": lambda: synth.skewed_chain(n=20000, hub_deg=9000),
+         "dense": lambda: synth.dense_random_chain(n=3000, density=0.1, sink_frac=0.02, seed=6),
+         "gambler": lambda: synth.gamblers_ruin(40, 0.45)}[name]()
+    cls_o, x_o = oracle_solution(c)
+    cls, x, info = gpu_solve(c, O.PROB01, "mixed", 1e-11)
+    assert info["status"] == R.REACH_OK
+    assert np.max(np.abs(x - x_o)) <= TOL_MIXED
+    with R.Solver(c.n, c.rowptr, c.col, c.val, c.goal) as s:
+        ms = R.reach_time_kernel(s.ctx, "sweep32", 3)
+    assert ms > 0.0
