@@ -115,10 +115,17 @@ __global__ void __launch_bounds__(TMA_WARPS * 32, 2) k_sweep32_tma(int64_t nq, c
       const int cnt = (int)min((int64_t)TMA_SEG, a1 - k0);
       const float* sh = reinterpret_cast<const float*>(ring + s * STAGE_B);
       const IT* sc = reinterpret_cast<const IT*>(ring + s * STAGE_B + HI_B);
-      for (int j = lane; j < cnt; j += 32) {
+      // every lane owns slots lane, lane + 32, ... of the segment: all 16 gathers of d are
+      // independent and in flight together (the row's own entries only)
+      float part[TMA_SEG / 32];
+#pragma unroll
+      for (int u = 0; u < TMA_SEG / 32; ++u) {
+        const int j = lane + 32 * u;
         const int64_t k = k0 + j;
-        if (k >= lo && k < hi) acc = fmaf(sh[j], __ldg(din + (int)sc[j]), acc);
+        part[u] = (j < cnt && k >= lo && k < hi) ? sh[j] * __ldg(din + (int)sc[j]) : 0.0f;
       }
+#pragma unroll
+      for (int u = 0; u < TMA_SEG / 32; ++u) acc += part[u];
       __syncwarp();
       if (g + TMA_ST < nseg) {
         if (lane == 0) issue(s, a0, a1, g + TMA_ST);
