@@ -1125,7 +1125,9 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
   }
   // 66: warp + vector loads with four quads per trip (FP32 sweep only); 128: entry-balanced
   // tiles (FP64 Jacobi and the FP32 sweep), which wins when a few rows are very long
-  const int codes[9] = {2, 4, 8, 16, 32, 64, 66, LAY_TMA, LAY_SEG};
+  // (LAY_TMA, the FP32 sweep staged by bulk copies, is not a candidate: it measured 1.7x
+  // slower than 64 on the dense system, with each row's first segments arriving cold)
+  const int codes[8] = {2, 4, 8, 16, 32, 64, 66, LAY_SEG};
   const double mean = (double)c->m_q / (double)c->n_q;
   Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_jv, c->bj};   // Jacobi form (the FP64 sweep)
   cudaStream_t s = c->stream;
@@ -1133,8 +1135,7 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
   int pick = 0;
   for (int code : codes) {
     const Lay L = lay_of(code);
-    if ((code == 66 || code == LAY_TMA) && method != REACH_JACOBI_MIXED) continue;
-    if (code == LAY_TMA && mean < 64) continue;  // segments of 512 entries want long rows
+    if (code == 66 && method != REACH_JACOBI_MIXED) continue;
     if (L.seg && (e = seg_plan(c)) != cudaSuccess) return e;
     if (L.vec && !L.seg && mean < 16) continue;  // nothing to vectorise
     if (!L.vec && L.g > 4 * mean + 4) continue;  // mostly idle lanes
