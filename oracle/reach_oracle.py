@@ -18,8 +18,8 @@ paper's order and notation:
   (none)     adjoint solve and parameter gradients                -> adjoint, grad_p,
                                                                      softmax_probs, grad_theta
   (none)     a-posteriori error bound                             -> error_bound
-  §6         strongly connected components of the digraph of A, solved in reverse
-             topological order (the future-work idea of §6)      -> scc_labels, scc_levels,
+  §8         strongly connected components of the digraph of A, solved in reverse
+             topological order (the future-work idea of §8)      -> scc_labels, scc_levels,
                                                                      block_jacobi
 
 Where the paper is silent or ambiguous the oracle takes these readings:
@@ -344,10 +344,10 @@ def error_bound(m, b, x):
     return float(np.max(tau) * np.max(np.abs(r))) if r.size else 0.0
 
 
-# ---------------------------------------------------------------- §6: SCCs in reverse topological order
+# ---------------------------------------------------------------- §8: SCCs in reverse topological order
 
 def scc_labels(a):
-    """Strongly connected component of every row of the digraph of A (§6).
+    """Strongly connected component of every row of the digraph of A (§8).
 
     The digraph has an edge i -> j for every off-diagonal A_ij != 0 (the diagonal sits
     in d and links a state only to itself).  Rows i and j share a component exactly when
@@ -370,12 +370,12 @@ def scc_labels(a):
 
 
 def scc_levels(a, labels):
-    """Level of every row: its component's height in the condensation DAG (§6).
+    """Level of every row: its component's height in the condensation DAG (§8).
 
     A component without edges to other components has level 0; any other component
     sits one above the highest component it has an edge to.  Components of one level
     never link to each other, and every edge leaves a level for a lower one, so solving
-    level 0, 1, 2, ... in turn is the reverse topological order of §6.  Computed by
+    level 0, 1, 2, ... in turn is the reverse topological order of §8.  Computed by
     peeling the condensation from its sinks, one level per pass.
     """
     a = sp.csr_matrix(a)
@@ -411,7 +411,7 @@ def scc_levels(a, labels):
 
 
 def block_jacobi(m, b, eps, max_iter, labels=None, levels=None):
-    """Jacobi for M x = b one level of SCCs at a time, lowest level first (§6, §3.1).
+    """Jacobi for M x = b one level of SCCs at a time, lowest level first (§8, §3.1).
 
     Rows of level h depend only on rows of their own components and of lower levels,
     which are already solved; so each level runs the Jacobi sweep of §3.1 on its own

@@ -1,5 +1,5 @@
 // Strongly connected components of the digraph of A over S?, their levels in the
-// condensation, and the Jacobi iteration run one level at a time (§6: the paper
+// condensation, and the Jacobi iteration run one level at a time (§8: the paper
 // proposes taking the SCCs of the chain in reverse topological order, since the
 // matrices of single components differ in size and density from the whole).
 //
@@ -858,7 +858,7 @@ RDEV bool sync_all(const GridBar& gb) {
 // Levels [h0, h1) of the level-by-level Jacobi in one launch: the CTAs walk the levels
 // in order, with a barrier after every sweep instead of a kernel boundary.  Big levels
 // run on the whole GPU (a cooperative grid with grid barriers); runs of small levels, the
-// components §6 expects to differ most from the whole matrix, run on one cluster of 16
+// components §8 expects to differ most from the whole matrix, run on one cluster of 16
 // CTAs, whose hardware barrier costs far less than a grid-wide one.  A level of
 // single-row components is swept once, in place, into both buffers.  A cyclic level
 // ping-pongs between the buffers until max|x' - x| < eps over its rows; its final

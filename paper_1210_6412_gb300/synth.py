@@ -400,7 +400,7 @@ def skewed_chain(n=20000, zipf_a=1.6, max_deg=64, hubs=8, hub_deg=6000, goal_fra
 
 def cascade_chain(blocks=64, width=4096, dmin=2, dmax=6, p_stay=0.9, goal_frac_last=0.02,
                   sink_frac=0.01, seed=1210_6412_8):
-    """A chain of strongly connected stages: the shape the SCC order of §6 is meant for.
+    """A chain of strongly connected stages: the shape the SCC order of §8 is meant for.
 
     States are numbered block by block.  Out-degree is uniform in dmin..dmax; each
     successor is, with probability ``p_stay``, a uniform state of the same block, else a

@@ -1,4 +1,4 @@
-"""Components, levels and the level-by-level Jacobi (§6) of the CUDA path vs the oracle.
+"""Components, levels and the level-by-level Jacobi (§8) of the CUDA path vs the oracle.
 
 Labels and levels are unique (a component is named by its largest row index, and its
 level is its height in the condensation), so they are compared bit for bit; x is

@@ -306,7 +306,7 @@ def test_grad_theta_matches_central_differences():
     np.testing.assert_allclose(g_t, fd, rtol=1e-5, atol=1e-9)
 
 
-# ---------------------------------------------------------------- §6: SCCs, reverse topological order
+# ---------------------------------------------------------------- §8: SCCs, reverse topological order
 
 def _random_digraph_system(seed, n_max=60):
     rng = np.random.default_rng(500 + seed)
