@@ -57,7 +57,26 @@ RDEV double dot64(int64_t lo, int64_t hi, int lane, const int32_t* __restrict__ 
     s = (s + s1) + (s2 + s3);
     if (e + lane < hi) s = fma(__ldcs(av + e + lane), xf(__ldcs(ci + e + lane)), s);
   } else {
-    for (int64_t k = lo + lane; k < hi; k += G) s = fma(__ldcs(av + k), xf(__ldcs(ci + k)), s);
+    // B entries per lane per trip (4 with one lane per row, else 2), every load of a trip
+    // issued before its first use: a short row costs one memory round trip per level
+    // (index, gather), not one per entry.  One accumulator: a slot past the row end adds
+    // 0 * 0, and no partial sums are combined -- an SM of GB300 completes two FP64 lanes
+    // per clock, so every warp-wide FP64 instruction costs 16 clocks of it.
+    constexpr int B = G == 1 ? 4 : 2;
+    for (int64_t k = lo + lane; k < hi; k += B * G) {
+      int32_t c[B];
+      double v[B], xg[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        const bool ok = k + u * G < hi;
+        c[u] = ok ? __ldcs(ci + k + u * G) : 0;
+        v[u] = ok ? __ldcs(av + k + u * G) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < B; ++u) xg[u] = k + u * G < hi ? xf(c[u]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < B; ++u) s = fma(v[u], xg[u], s);
+    }
   }
   return s;
 }
@@ -115,7 +134,25 @@ RDEV float dot32(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
     for (int u = 0; u < U; ++u) s += acc[u];
     if (e + lane < hi) s = fmaf(__ldcs(av + e + lane), __ldg(x + ld_idx(ci + e + lane)), s);
   } else {
-    for (int64_t k = lo + lane; k < hi; k += G) s = fmaf(__ldcs(av + k), __ldg(x + ld_idx(ci + k)), s);
+    // four entries per lane per trip, loads first (see dot64)
+    float s1 = 0.0f;
+    for (int64_t k = lo + lane; k < hi; k += 4 * G) {
+      int c[4];
+      float v[4], xg[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool ok = k + u * G < hi;
+        c[u] = ok ? ld_idx(ci + k + u * G) : 0;
+        v[u] = ok ? __ldcs(av + k + u * G) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xg[u] = k + u * G < hi ? __ldg(x + c[u]) : 0.0f;
+      s = fmaf(v[0], xg[0], s);
+      s1 = fmaf(v[1], xg[1], s1);
+      s = fmaf(v[2], xg[2], s);
+      s1 = fmaf(v[3], xg[3], s1);
+    }
+    s += s1;
   }
   return s;
 }
@@ -160,10 +197,30 @@ RDEV double dot_hilo(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci
       sl = fmaf(__ldcs(al + k), __ldg(xf + c), sl);
     }
   } else {
-    for (int64_t k = lo + lane; k < hi; k += G) {
-      const int c = ld_idx(ci + k);
-      s = fma(widen(__ldcs(ah + k)), __ldg(x + c), s);
-      sl = fmaf(__ldcs(al + k), __ldg(xf + c), sl);
+    // B entries per lane per trip, loads first, one FP64 accumulator (see dot64)
+    constexpr int B = G == 1 ? 4 : 2;
+    for (int64_t k = lo + lane; k < hi; k += B * G) {
+      int c[B];
+      float h[B], l[B], xl[B];
+      double xg[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        const bool ok = k + u * G < hi;
+        c[u] = ok ? ld_idx(ci + k + u * G) : 0;
+        h[u] = ok ? __ldcs(ah + k + u * G) : 0.0f;
+        l[u] = ok ? __ldcs(al + k + u * G) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        const bool ok = k + u * G < hi;
+        xg[u] = ok ? __ldg(x + c[u]) : 0.0;
+        xl[u] = ok ? __ldg(xf + c[u]) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        s = fma(widen(h[u]), xg[u], s);
+        sl = fmaf(l[u], xl[u], sl);
+      }
     }
   }
   return s;
@@ -261,12 +318,22 @@ __global__ void __launch_bounds__(NT) k_jacobi64(int64_t nq, const int64_t* __re
   unsigned long long mx = 0ull;
   auto xf = [x](int32_t j) { return __ldg(x + j); };
   for (int64_t i = row_begin<G>(rg, ctr); warp_has_row<G>(i, nq); i = row_next<G>(rg, ctr, i)) {
-    double s = 0.0;
+    double s = 0.0, bv = 0.0, xo = 0.0;
+    // short rows: row-side loads issued ahead of the row's entries (long vector rows
+    // would only hold the registers)
+    if (!V && i < nq && rg.lane == 0) {
+      bv = bj[i];
+      xo = x[i];
+    }
     if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, aj, xf);
     s = group_sum<G>(s);
     if (i < nq && rg.lane == 0) {
-      const double xv = bj[i] + s;       // (b_i + sum A_ij x_j) / d_i in the Jacobi form
-      mx = umax64(mx, abs_bits(xv - x[i]));
+      if (V) {
+        bv = bj[i];
+        xo = x[i];
+      }
+      const double xv = bv + s;          // (b_i + sum A_ij x_j) / d_i in the Jacobi form
+      mx = umax64(mx, abs_bits(xv - xo));
       xn[i] = xv;
     }
   }
@@ -347,14 +414,22 @@ __global__ void __launch_bounds__(NT) k_resid_hilo(int64_t nq, const int64_t* __
   RowGroups rg = RowGroups::make<G>();
   unsigned long long mx = 0ull;
   for (int64_t i = row_begin<G>(rg, ctr); warp_has_row<G>(i, nq); i = row_next<G>(rg, ctr, i)) {
-    double s = 0.0;
+    double s = 0.0, bv = 0.0, xo = 0.0;
     float sl = 0.0f;
+    if (!V && i < nq && rg.lane == 0) {  // short rows: row-side loads issued early
+      bv = bj[i];
+      xo = x[i];
+    }
     if (i < nq) s = dot_hilo<G, V, IT>(rp[i], rp[i + 1], rg.lane, ci, ah, al, x, xf, sl);
     s = group_sum<G>(s);
     sl = group_sum<G>(sl);
     if (i < nq && rg.lane == 0) {
+      if (V) {
+        bv = bj[i];
+        xo = x[i];
+      }
       // residual of the Jacobi form: r_i / d_i = bj_i + (Aj x)_i - x_i
-      const double r = bj[i] + (s + (double)sl) - x[i];
+      const double r = bv + (s + (double)sl) - xo;
       const float rf = __double2float_rn(r);
       r32[i] = rf;
       dl0[i] = rf;
@@ -392,10 +467,11 @@ __global__ void __launch_bounds__(NT) k_sweep32(int64_t nq, const int64_t* __res
   if (st->done) return;
   RowGroups rg = RowGroups::make<G>();
   for (int64_t i = row_begin<G>(rg, ctr); warp_has_row<G>(i, nq); i = row_next<G>(rg, ctr, i)) {
-    float s = 0.0f;
+    float s = 0.0f, rv = 0.0f;
+    if (!V && i < nq && rg.lane == 0) rv = r32[i];  // short rows: issued early
     if (i < nq) s = dot32<G, V, IT, U>(rp[i], rp[i + 1], rg.lane, ci, ah, din);
     s = group_sum<G>(s);
-    if (i < nq && rg.lane == 0) dout[i] = r32[i] + s;
+    if (i < nq && rg.lane == 0) dout[i] = (V ? r32[i] : rv) + s;
   }
 }
 
@@ -718,10 +794,16 @@ static Lay lay_of(int code) {
 
 // Row mapping of `method`'s kernels: the autotuned choice if there is one, else the
 // REACH_LANES override, else lanes from the mean row length (warp + 16-byte loads from 96).
+// Lanes per row of the solver kernels when nothing is tuned: one lane for rows of at most
+// three entries on average (a model checker's state spaces), else from pick_group.
+static int solver_group(int64_t rows, int64_t nnz) {
+  return rows > 0 && nnz <= 3 * rows ? 1 : pick_group(rows, nnz);
+}
+
 static Lay layout(reach_ctx* c, int64_t rows, int64_t nnz, int method = 0) {
   if (method >= 0 && method < 3 && c->tune.gm[method] > 0) return lay_of(c->tune.gm[method]);
   if (c->tune.g > 0) return lay_of(c->tune.g);
-  const int g = pick_group(rows, nnz);
+  const int g = solver_group(rows, nnz);
   const bool vec = g == 32 && rows > 0 && nnz / rows >= 96;
   return {g, vec};
 }
@@ -732,7 +814,7 @@ static Lay layout(reach_ctx* c, int64_t rows, int64_t nnz, int method = 0) {
 static Lay row_layout(reach_ctx* c, int method) {
   const Lay L = layout(c, c->n_q, c->m_q, method);
   if (!L.seg) return L;
-  const int g = pick_group(c->n_q, c->m_q);
+  const int g = solver_group(c->n_q, c->m_q);
   return {g, g == 32 && c->n_q > 0 && c->m_q / c->n_q >= 96};
 }
 
@@ -740,6 +822,7 @@ static Lay row_layout(reach_ctx* c, int method) {
   do {                                                    \
     if ((L).vec) FN<32, true>(__VA_ARGS__);               \
     else switch ((L).g) {                                 \
+        case 1: FN<1, false>(__VA_ARGS__); break;         \
         case 2: FN<2, false>(__VA_ARGS__); break;         \
         case 4: FN<4, false>(__VA_ARGS__); break;         \
         case 8: FN<8, false>(__VA_ARGS__); break;         \
@@ -1127,7 +1210,7 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
   // tiles (FP64 Jacobi and the FP32 sweep), which wins when a few rows are very long
   // (LAY_TMA, the FP32 sweep staged by bulk copies, is not a candidate: it measured 1.7x
   // slower than 64 on the dense system, with each row's first segments arriving cold)
-  const int codes[8] = {2, 4, 8, 16, 32, 64, 66, LAY_SEG};
+  const int codes[9] = {1, 2, 4, 8, 16, 32, 64, 66, LAY_SEG};
   const double mean = (double)c->m_q / (double)c->n_q;
   Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_jv, c->bj};   // Jacobi form (the FP64 sweep)
   cudaStream_t s = c->stream;
@@ -1139,6 +1222,7 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
     if (L.seg && (e = seg_plan(c)) != cudaSuccess) return e;
     if (L.vec && !L.seg && mean < 16) continue;  // nothing to vectorise
     if (!L.vec && L.g > 4 * mean + 4) continue;  // mostly idle lanes
+    if (!L.vec && L.g == 1 && mean > 8) continue;  // one lane walking long rows
     if (method == REACH_JACOBI_MIXED) c->tune.sweep_u = code == 66 ? 4 : 2;
     unsigned* ctr = &c->st->rowctr[0];
     // the mixed method also times its FP64 residual step (same mapping), which runs once

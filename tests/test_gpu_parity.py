@@ -191,7 +191,7 @@ def test_autotune_then_solve(c1, method, tol):
     with R.Solver(c1.n, c1.rowptr, c1.col, c1.val, c1.goal) as s:
         s.solve("jacobi", eps=1e-12)                 # leaves the device state 'done'
         t = s.autotune(method)
-        assert t["lanes"] in (2, 4, 8, 16, 32, 64, 66) and t["sweep_ms"] > 0
+        assert t["lanes"] in (1, 2, 4, 8, 16, 32, 64, 66, 128) and t["sweep_ms"] > 0
         x, info = s.solve(method, eps=_eps(method))
         assert np.max(np.abs(x - x_o)) <= tol
         for k in ("jacobi64", "sweep32", "resid_hilo", "bicgstab_spmv"):
@@ -313,6 +313,24 @@ def test_entry_balanced_layout_matches_oracle(c1, name, method, tol, monkeypatch
     assert np.max(np.abs(x - x_o)) <= tol
 
 
+@pytest.mark.parametrize("lanes", ["1", "2", "4"])
+@pytest.mark.parametrize("name", ["layered", "random", "gambler"])
+@pytest.mark.parametrize("method,tol", [("jacobi", TOL_FP64), ("mixed", TOL_MIXED), ("bicgstab", TOL_FP64)])
+def test_short_row_mappings_match_oracle(c1, name, lanes, method, tol, monkeypatch):
+    """REACH_LANES=1 (one thread per row, as in §5.1), 2 and 4 on short rows: the row
+    dots load a batch of entries per lane before using them, with the slots past the row
+    end predicated off; rows of 1 to 4 entries and rows longer than one batch both occur."""
+    monkeypatch.setenv("REACH_LANES", lanes)
+    c = {"random": lambda: c1,
+         "layered": lambda: synth.layered_chain(layers=40, width=300, seed=11),
+         "gambler": lambda: synth.gamblers_ruin(40, 0.45)}[name]()
+    cls_o, x_o = oracle_solution(c)
+    cls, x, info = gpu_solve(c, O.PROB01, method, 1e-11 if method == "mixed" else 1e-13)
+    assert np.array_equal(cls, cls_o)
+    assert info["status"] == R.REACH_OK
+    assert np.max(np.abs(x - x_o)) <= tol
+
+
 def test_autotuner_may_pick_entry_balanced_tiles():
     """On a chain with a few very long rows the entry-balanced tiles are a candidate of the
     autotuner for the FP32 sweep and the FP64 sweep; whatever it picks solves correctly."""
@@ -324,7 +342,7 @@ def test_autotuner_may_pick_entry_balanced_tiles():
         xj, ij = s.solve("jacobi", eps=1e-12, max_iter=1_000_000)
         xm, im = s.solve("mixed", eps=1e-11, max_iter=1_000_000)
         xb, ib = s.solve("bicgstab", eps=1e-12, max_iter=10_000)
-    assert all(p in (2, 4, 8, 16, 32, 64, 66, 128) for p in picks.values())
+    assert all(p in (1, 2, 4, 8, 16, 32, 64, 66, 128) for p in picks.values())
     assert ij["status"] == R.REACH_OK and im["status"] == R.REACH_OK and ib["status"] == R.REACH_OK
     assert np.max(np.abs(xj - xm)) <= TOL_MIXED and np.max(np.abs(xj - xb)) <= 1e-9
 
