@@ -419,17 +419,25 @@ def run_workload(args):
         bt = synth.batched_chains(n_chains=args.chains, sink_frac=0.02)
         n, rowptr, col, val, goals, offs = bt.concat()
         d_in = dev(rowptr, col, val, goals)
+        # each chain stops on its own unless --global-stop (one rule over the whole union)
+        chains = None if args.global_stop else offs
         for rep in range(max(1, args.warmup) + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with R.BatchSolver(n, *d_in) as bs:
+            with R.BatchSolver(n, *d_in, chains=chains) as bs:
                 x, info = bs.solve(eps=1e-8, out=torch.empty((goals.shape[0], n), dtype=torch.float64,
                                                               device="cuda"))
+                citers, _ = bs.chain_info()
             torch.cuda.synchronize()
             wall = (time.perf_counter() - t0) * 1e3
         line.update({"chains": args.chains, "n": n, "nnz": int(rowptr[-1]), "k": int(goals.shape[0]),
+                     "stopping": "global" if args.global_stop else "per chain",
                      "precompute_ms": info["ms_precompute"], "solve_ms": info["ms_solve"],
                      "iters": info["iters"], "refinements": info["refinements"],
+                     "chain_sweeps": {"min": int(citers.min()), "median": float(np.median(citers)),
+                                      "max": int(citers.max()),
+                                      "row_weighted_mean": float(np.sum(citers * np.diff(offs)) / n)}
+                     if chains is not None else None,
                      "resid_inf": info["resid_inf"],
                      "alg_GBps": info["bytes_moved"] / info["ms_solve"] / 1e6, "wall_ms": wall})
         # the same answers from plain FP64 Jacobi, one (chain, goal set) at a time, same eps
@@ -474,15 +482,20 @@ def run_workload(args):
 
 
 def run_profile(args):
-    """Small fixed run for ncu: the bench workload, one context, `--profile-iters`
-    iterations of one method (no stopping test can end it early)."""
+    """Small fixed run for ncu: the bench workload (or `--workload layered`, the
+    model-checker-like chain), one context, `--profile-iters` iterations of one method
+    (no stopping test can end it early)."""
     import torch
     import paper_1210_6412_gb300 as R
-    chain = make_chain()
+    from paper_1210_6412_gb300 import synth
+    if args.workload == "layered":
+        chain, mode = synth.layered_chain(), R.REACH_PROB01
+    else:
+        chain, mode = make_chain(), R.REACH_PROB0_ONLY
     dev = torch.device("cuda", 0)
     d_in = [torch.from_numpy(a).to(dev) for a in (chain.rowptr, chain.col, chain.val, chain.goal)]
     out = torch.empty(chain.n, dtype=torch.float64, device=dev)
-    with R.Solver(chain.n, *d_in, mode=R.REACH_PROB0_ONLY) as s:
+    with R.Solver(chain.n, *d_in, mode=mode) as s:
         del d_in                    # the context holds its own copy; keep the footprint small
         torch.cuda.empty_cache()
         _, info = s.solve(args.profile, eps=1e-300, max_iter=args.profile_iters, refine_k=K_REFINE,
@@ -506,6 +519,8 @@ def main():
                                            "batched", "parametric"],
                     default="dense", help="dense = the benchmark; the others print their own line")
     ap.add_argument("--chains", type=int, default=64, help="--workload batched: number of chains")
+    ap.add_argument("--global-stop", action="store_true",
+                    help="--workload batched: one stopping rule over the whole union instead of one per chain")
     ap.add_argument("--plain", type=int, default=1,
                     help="--workload batched: also solve every (chain, goal set) with plain FP64 Jacobi")
     args = ap.parse_args()

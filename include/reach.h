@@ -77,7 +77,7 @@ typedef enum {
    * very long rows do not serialise on one warp.  Only the summation order differs. */
   REACH_JACOBI_SEG = 3,
   /* Jacobi one level of strongly connected components at a time, in reverse
-   * topological order (the future-work idea of §6): the decomposition of reach_scc
+   * topological order (the future-work idea of §8): the decomposition of reach_scc
    * (computed on first use), then for level 0, 1, ...: a level of single-row
    * components is exact after one sweep; any other level runs the FP64 Jacobi sweep of
    * §3.1 on its own rows, with all other rows held fixed, until max|x' - x| < eps over
@@ -155,7 +155,7 @@ reach_status reach_solve(reach_ctx* ctx, int32_t method, double eps, int64_t max
                          int32_t refine_k, const double* x0, double* x_out, int32_t flags,
                          reach_info* info);
 
-/* Strongly connected components of the digraph of A over S? and their levels (§6:
+/* Strongly connected components of the digraph of A over S? and their levels (§8:
  * the paper's future work takes the components in reverse topological order).  After
  * reach_precompute (or reach_system_create).  The decomposition runs on the device
  * once per system and is kept for REACH_SCC_JACOBI.  label: int32[n?] or NULL, the
@@ -170,7 +170,8 @@ reach_status reach_scc(reach_ctx* ctx, int32_t* label, int32_t* level, int32_t f
 
 /* Autotuner for the row mapping of `method` on the current system (after
  * reach_precompute).  Times every candidate mapping of the method's dominant kernel --
- * lanes per row 2, 4, 8, 16, 32, a warp with 16-byte vector loads (reported as 64; 66
+ * lanes per row 1 (the paper's one thread per row, §5.1; tried only when rows average at
+ * most 8 entries), 2, 4, 8, 16, 32, a warp with 16-byte vector loads (reported as 64; 66
  * for the FP32 sweep with four quads per trip), or entry-balanced tiles of 4096 stored
  * entries (reported as 128: the segmented sweep of REACH_JACOBI_SEG, and for BiCGStab a
  * segmented product followed by the elementwise M u with its dot products; it wins when
@@ -180,8 +181,8 @@ reach_status reach_scc(reach_ctx* ctx, int32_t* label, int32_t* level, int32_t f
  * reach_solve gets refine_k = 0.  Setting REACH_AUTOTUNE=1 in the environment makes the
  * first reach_solve of each method run it.  Outputs (host, may be NULL): the chosen
  * mapping, its time per sweep in ms, and the sweeps between checks.  Rows of this
- * library's kernels are cut the same way for every method, so there is no paper
- * counterpart beyond the one-thread-per-row mapping of §5.1. */
+ * library's kernels are cut the same way for every method; the paper itself fixes the
+ * one-thread-per-row mapping. */
 reach_status reach_autotune(reach_ctx* ctx, int32_t method, int32_t* lanes, double* sweep_ms,
                             int32_t* check_every);
 
@@ -238,9 +239,28 @@ reach_status reach_batch_get_classes(reach_batch* b, uint8_t* cls, int32_t flags
  * correction every refine_k sweeps (even, in [2, 62]; 0 = 16):
  * x_j[s] <- sum_{s' != s} P(s,s') x_j[s'] / (1 - P(s,s)) on S?_j, with x_j = 1 on
  * S=1_j and 0 on S=0_j.  Stops when the largest FP64 Jacobi step over all S?_j is
- * below eps.  x_out: float64[k * n], goal-set major.  Synchronises the stream. */
+ * below eps -- per chain once reach_batch_set_chains has named the chains; info->iters
+ * is then the sweep count of the slowest chain and info->last_delta the largest last
+ * step.  x_out: float64[k * n], goal-set major.  Synchronises the stream. */
 reach_status reach_batch_solve(reach_batch* b, double eps, int64_t max_iter, int32_t refine_k,
                                double* x_out, int32_t flags, reach_info* info);
+
+/* The chains of a batch whose matrix is the block-diagonal union of independent chains:
+ * chain c owns states [offsets[c], offsets[c+1]) and no positive entry of P leaves it.
+ * With chains set, reach_batch_solve applies its stopping rule to each chain on its own
+ * (the largest FP64 Jacobi step over the chain's S?_j, all goal sets): a chain that
+ * meets it leaves the later sweeps untouched, so its x is exactly the x of solving that
+ * chain alone with the same eps and refine_k.  Until this is called the whole batch is
+ * one chain.  offsets: int64[n_chains + 1] in host memory, offsets[0] = 0,
+ * non-decreasing, offsets[n_chains] = n.  REACH_EINVAL (and the chains stay as they
+ * were) for bad offsets or a positive entry of P that crosses a chain boundary.
+ * Synchronises the stream. */
+reach_status reach_batch_set_chains(reach_batch* b, int32_t n_chains, const int64_t* offsets);
+
+/* Per chain, after reach_batch_solve: iters[c] = the sweep count at which chain c met
+ * the stopping rule (-1 if it did not within max_iter), last[c] = its last FP64 Jacobi
+ * step (max over its S?_j).  Host arrays of n_chains entries; either may be NULL. */
+reach_status reach_batch_chain_info(reach_batch* b, int64_t* iters, double* last);
 
 /* Release the batch.  NULL is a no-op. */
 void reach_batch_destroy(reach_batch* b);

@@ -27,6 +27,7 @@ __all__ = [
     "reach_param_probs", "reach_param_grad_theta", "reach_last_error", "reach_destroy",
     "reach_version", "Solver", "reach_batch_create", "reach_batch_precompute",
     "reach_batch_get_classes", "reach_batch_solve", "reach_batch_destroy", "BatchSolver",
+    "reach_batch_set_chains", "reach_batch_chain_info",
 ]
 
 REACH_OK, REACH_EINVAL, REACH_ENOMEM, REACH_ECUDA, REACH_ESTATE = 0, 1, 2, 3, 4
@@ -90,6 +91,8 @@ _SIGS = {
     "reach_batch_get_classes": (_I32, [_P, _P, _I32]),
     "reach_batch_solve": (_I32, [_P, _D, _I64, _I32, _P, _I32, C.POINTER(ReachInfo)]),
     "reach_batch_destroy": (None, [_P]),
+    "reach_batch_set_chains": (_I32, [_P, _I32, _P]),
+    "reach_batch_chain_info": (_I32, [_P, _P, _P]),
     "reach_autotune": (_I32, [_P, _I32, C.POINTER(_I32), C.POINTER(_D), C.POINTER(_I32)]),
     "reach_system_create": (_I32, [C.POINTER(_P), _I64, _I64, _P, _P, _P, _P, _I32, _P]),
     "reach_time_kernel": (_I32, [_P, _I32, _I32, C.POINTER(_D)]),
@@ -287,7 +290,7 @@ def reach_autotune(ctx, method=REACH_JACOBI_FP64):
 
 
 def reach_scc(ctx, labels=True, max_rounds=0, out_label=None, out_level=None):
-    """Strongly connected components of the digraph of A over S? and their levels (§6).
+    """Strongly connected components of the digraph of A over S? and their levels (§8).
 
     Returns (label, level, info): label[i] is the largest row index of row i's component
     and level[i] the component's level in the condensation (int32 over the S? rows in
@@ -426,6 +429,22 @@ def reach_batch_solve(b, n, k, eps=1e-8, max_iter=1_000_000, refine_k=0, out=Non
     return out, info.as_dict()
 
 
+def reach_batch_set_chains(b, offsets):
+    """Chains of a block-diagonal batch: chain c owns states [offsets[c], offsets[c+1])."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    if off.ndim != 1 or off.size < 2:
+        raise ValueError("offsets must be a 1-D array of n_chains + 1 entries")
+    _check(lib().reach_batch_set_chains(b, int(off.size - 1), off.ctypes.data), None, "reach_batch_set_chains")
+
+
+def reach_batch_chain_info(b, n_chains):
+    """(iters[n_chains], last[n_chains]) of the last reach_batch_solve, per chain."""
+    iters = np.empty(n_chains, np.int64)
+    last = np.empty(n_chains, np.float64)
+    _check(lib().reach_batch_chain_info(b, iters.ctypes.data, last.ctypes.data), None, "reach_batch_chain_info")
+    return iters, last
+
+
 def reach_batch_destroy(b):
     if b:
         lib().reach_batch_destroy(b)
@@ -434,11 +453,22 @@ def reach_batch_destroy(b):
 class BatchSolver:
     """K goal sets over one chain: ``BatchSolver(n, rowptr, col, val, goals[k, n])``."""
 
-    def __init__(self, n, rowptr, col, val, goals, mode=REACH_PROB01, stream=None):
+    def __init__(self, n, rowptr, col, val, goals, mode=REACH_PROB01, stream=None, chains=None):
         self.n = int(n)
         self.k = int(goals.shape[0])
+        self.n_chains = 1
         self.b = reach_batch_create(n, rowptr, col, val, goals, stream)
+        if chains is not None:
+            self.set_chains(chains)
         reach_batch_precompute(self.b, mode)
+
+    def set_chains(self, offsets):
+        """Stop each chain of the block-diagonal union on its own (offsets: n_chains + 1)."""
+        reach_batch_set_chains(self.b, offsets)
+        self.n_chains = len(offsets) - 1
+
+    def chain_info(self):
+        return reach_batch_chain_info(self.b, self.n_chains)
 
     def classes(self, out=None):
         return reach_batch_get_classes(self.b, self.n, self.k, out)

@@ -9,6 +9,7 @@
 // correction every k sweeps, all inside one conditional-while CUDA graph.
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -28,6 +29,19 @@ struct reach_batch {
   float* D[2] = {nullptr, nullptr};  // [n][8] FP32 corrections
   unsigned* changed = nullptr;
   bool have_classes = false;
+  // Chains of the block-diagonal union (one chain [0, n) until reach_batch_set_chains).
+  // Chain lists cut each chain into chunks of BCH rows: list 0 holds every chain, list 1
+  // the chains still iterating in the current solve.
+  int32_t n_chains = 0;
+  int64_t chunks_all = 0;      // chunks of list 0
+  int64_t* coff = nullptr;     // [n_chains + 1] first state of each chain
+  int32_t* lid[2] = {nullptr, nullptr};   // chain ids of each list
+  int64_t* lpre[2] = {nullptr, nullptr};  // chunk prefix of each list, [n_chains + 1]
+  int64_t* lhdr = nullptr;     // {chains, chunks} of list 0, then of list 1
+  unsigned long long* cmax = nullptr;     // per chain: bits of max |r| of a residual step
+  double* clast = nullptr;     // per chain: last FP64 Jacobi step
+  int64_t* citer = nullptr;    // per chain: sweeps at which it stopped (-1: not yet)
+  double* work = nullptr;      // rows and entries processed: residual steps, then sweeps
   cudaGraphExec_t g_exec[3] = {nullptr, nullptr, nullptr};
   int64_t g_key[3] = {-1, -1, -1};
   int64_t passes[2] = {0, 0};
@@ -124,54 +138,134 @@ __global__ void k_batch_init_x(int64_t n, const uint8_t* __restrict__ one, doubl
 
 // Row mapping of the multi-RHS kernels: a group of lanes owns a row and each lane owns
 // some of the right-hand sides, so every lane walks the whole row and no cross-lane
-// reduction is needed (which matters most in FP64, whose pipe is narrow).
+// reduction is needed (which matters most in FP64, whose pipe is narrow).  Rows are dealt
+// by chain lists: chunk q of a list is BCH rows of one chain, warp w takes chunks w, w + W,
+// ... (W warps in the grid), so a converged chain costs nothing and a warp's per-chain
+// maximum needs one atomic per chunk at most.  At any moment the grid works on a window of
+// W * BCH consecutive rows, which keeps the gathers of that window's chains in L2.
+
+constexpr int BCH = 32;
+
+struct ChainList {
+  const int64_t* hdr;   // {chains, chunks}
+  const int32_t* id;    // chain ids (ascending)
+  const int64_t* pre;   // chunk prefix over the list, [chains + 1]
+  const int64_t* coff;  // chain offsets
+};
+
+// A warp's walk over its chunks.  q only grows, so the list position moves forward: one
+// probe of the next boundary, and a binary search over the rest when q jumped past it.
+struct ChunkWalk {
+  int32_t t = 0;
+  RDEV void rows(const ChainList& L, int32_t nl, int64_t q, int64_t& r0, int64_t& r1, int32_t& c) {
+    if (L.pre[t + 1] <= q) {
+      int32_t lo = t + 1, hi = nl;  // pre[lo] <= q < pre[hi]
+      while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (L.pre[mid] <= q) lo = mid;
+        else hi = mid;
+      }
+      t = lo;
+    }
+    c = L.id[t];
+    r0 = L.coff[c] + (q - L.pre[t]) * BCH;
+    r1 = min(r0 + (int64_t)BCH, L.coff[c + 1]);
+  }
+};
+
+RDEV unsigned long long bits_abs(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
+// Warp max of |r| bit patterns into a slot; NaN (bits above +inf) is stored as +inf.
+RDEV void warp_flush_max(unsigned long long* slot, unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(FULL, v, o);
+    v = y > v ? y : v;
+  }
+  if ((threadIdx.x & 31) == 0 && v != 0ull) atomicMax(slot, v < 0x7ff0000000000000ull ? v : 0x7ff0000000000000ull);
+}
 
 // FP64 residual of every right-hand side on the Jacobi form (values A_sj / d_s, read in
 // FP64): r_j = sum_{s'} Aj(s,s') x_j[s'] - x_j[s] on S?_j, 0 elsewhere; r_j is also the
-// first correction.  REPORT: only max|d_s r_j| (the residual of the system itself) into
-// the slot, after the loop.  Two lanes own a row, lane h the right-hand sides 4h .. 4h+3,
-// gathering two double2 of the 64-byte row of X per entry.
+// first correction.  Per chain of the list, max|r_j| goes to cmax[chain].  REPORT: only
+// max|d_s r_j| (the residual of the system itself) over the list, into st->slot[slot].
+// Two lanes own a row, lane h the right-hand sides 4h .. 4h+3, gathering two double2 of
+// the 64-byte row of X per entry.
 template <bool REPORT>
-__global__ void __launch_bounds__(BT) k_bresid(int64_t n, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(BT) k_bresid(ChainList L, const int64_t* __restrict__ rp,
                                                const int32_t* __restrict__ ci, const double* __restrict__ aj,
                                                const double* __restrict__ d, const uint8_t* __restrict__ sq,
                                                const double* __restrict__ X, float* __restrict__ R,
-                                               float* __restrict__ D1, SolveState* st, int slot) {
+                                               float* __restrict__ D1, SolveState* st, int slot,
+                                               unsigned long long* cmax) {
   if (!REPORT && st->done) return;
-  RowGroups rg = RowGroups::make<2>();
-  const int h = rg.lane;                    // right-hand sides 4h .. 4h+3
-  double mx = 0.0;
-  for (int64_t s = rg.first; s < n; s += rg.stride) {
-    const int64_t hi = rp[s + 1];
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t k = rp[s]; k < hi; ++k) {
-      const double v = __ldcs(aj + k);
-      const double2* xr = reinterpret_cast<const double2*>(X + (int64_t)__ldcs(ci + k) * 8 + 4 * h);
-      const double2 t0 = __ldg(xr), t1 = __ldg(xr + 1);
-      a[0] = fma(v, t0.x, a[0]);
-      a[1] = fma(v, t0.y, a[1]);
-      a[2] = fma(v, t1.x, a[2]);
-      a[3] = fma(v, t1.y, a[3]);
+  const int lane = threadIdx.x & 31;
+  const int h = lane & 1;      // right-hand sides 4h .. 4h+3
+  const int grp = lane >> 1;   // 16 rows of a chunk at a time
+  const int64_t nw = (int64_t)gridDim.x * (BT / 32);
+  const int32_t nl = (int32_t)L.hdr[0];
+  const int64_t nch = L.hdr[1];
+  ChunkWalk walk;
+  unsigned long long mx = 0ull;
+  int32_t cur = -1;
+  for (int64_t q = (int64_t)blockIdx.x * (BT / 32) + (threadIdx.x >> 5); q < nch; q += nw) {
+    int64_t r0, r1;
+    int32_t c;
+    walk.rows(L, nl, q, r0, r1, c);
+    if (!REPORT && c != cur) {  // warp-uniform: the warp shares the chunk
+      if (cur >= 0) warp_flush_max(cmax + cur, mx);
+      cur = c;
+      mx = 0ull;
     }
-    const unsigned m = sq[s] >> (4 * h);
+    for (int64_t s = r0 + grp; s < r1; s += 16) {
+      const int64_t hi = rp[s + 1];
+      double a[4] = {0.0, 0.0, 0.0, 0.0};
+      // two entries per trip, both entries' loads issued before the first use
+      for (int64_t k = rp[s]; k < hi; k += 2) {
+        const bool o1 = k + 1 < hi;
+        const double v = __ldcs(aj + k), w = o1 ? __ldcs(aj + k + 1) : 0.0;
+        const int32_t c0 = __ldcs(ci + k), c1 = o1 ? __ldcs(ci + k + 1) : 0;
+        const double2* xr = reinterpret_cast<const double2*>(X + (int64_t)c0 * 8 + 4 * h);
+        const double2* yr = reinterpret_cast<const double2*>(X + (int64_t)c1 * 8 + 4 * h);
+        const double2 t0 = __ldg(xr), t1 = __ldg(xr + 1);
+        double2 u0 = make_double2(0.0, 0.0), u1 = make_double2(0.0, 0.0);
+        if (o1) {
+          u0 = __ldg(yr);
+          u1 = __ldg(yr + 1);
+        }
+        a[0] = fma(v, t0.x, a[0]);
+        a[1] = fma(v, t0.y, a[1]);
+        a[2] = fma(v, t1.x, a[2]);
+        a[3] = fma(v, t1.y, a[3]);
+        if (o1) {
+          a[0] = fma(w, u0.x, a[0]);
+          a[1] = fma(w, u0.y, a[1]);
+          a[2] = fma(w, u1.x, a[2]);
+          a[3] = fma(w, u1.y, a[3]);
+        }
+      }
+      const unsigned m = sq[s] >> (4 * h);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t o = s * 8 + 4 * h + q;
-      const double r = ((m >> q) & 1u) ? a[q] - X[o] : 0.0;
-      if (REPORT) {
-        mx = fmax(mx, fabs(d[s] * r));
-      } else {
-        const float rf = __double2float_rn(r);
-        R[o] = rf;
-        D1[o] = rf;
-        mx = fmax(mx, fabs(r));
+      for (int u = 0; u < 4; ++u) {
+        const int64_t o = s * 8 + 4 * h + u;
+        const double r = ((m >> u) & 1u) ? a[u] - X[o] : 0.0;
+        if (REPORT) {
+          const unsigned long long b = bits_abs(d[s] * r);
+          mx = b > mx ? b : mx;
+        } else {
+          const float rf = __double2float_rn(r);
+          __stcs(R + o, rf);
+          __stcs(D1 + o, rf);
+          const unsigned long long b = bits_abs(r);
+          mx = b > mx ? b : mx;
+        }
       }
     }
   }
-  __shared__ double sh[32];
-  double a[1] = {mx != mx ? __longlong_as_double(0x7ff0000000000000LL) : mx};
-  block_reduce<1, true>(a, sh);
-  if (threadIdx.x == 0) atomic_max_nonneg(&st->slot[slot], a[0]);
+  if (REPORT) warp_flush_max(&st->slot[slot], mx);
+  else if (cur >= 0) warp_flush_max(cmax + cur, mx);
 }
 
 // FP32 correction sweep of every right-hand side on the Jacobi form:
@@ -179,38 +273,192 @@ __global__ void __launch_bounds__(BT) k_bresid(int64_t n, const int64_t* __restr
 // lane j the right-hand side j, so the 8 lanes gather one 32-byte row of D together.  (Two
 // lanes with a float4 each ran at the same speed but doubled the DRAM traffic: more rows
 // in flight per warp spread the gathers over more of D and L2 kept less of it.)
-__global__ void __launch_bounds__(BT) k_bsweep(int64_t n, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(BT) k_bsweep(ChainList L, const int64_t* __restrict__ rp,
                                                const int32_t* __restrict__ ci, const float* __restrict__ ah,
                                                const uint8_t* __restrict__ sq, const float* __restrict__ R,
                                                const float* __restrict__ Din, float* __restrict__ Dout,
                                                const SolveState* st) {
   if (st->done) return;
-  RowGroups rg = RowGroups::make<8>();
-  const int j = rg.lane;
-  for (int64_t s = rg.first; s < n; s += rg.stride) {
-    const int64_t hi = rp[s + 1];
-    int64_t k = rp[s];
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    for (; k + 3 < hi; k += 4) {
-      const int32_t c0 = __ldcs(ci + k), c1 = __ldcs(ci + k + 1), c2 = __ldcs(ci + k + 2), c3 = __ldcs(ci + k + 3);
-      const float v0 = __ldcs(ah + k), v1 = __ldcs(ah + k + 1), v2 = __ldcs(ah + k + 2), v3 = __ldcs(ah + k + 3);
-      a0 = fmaf(v0, __ldg(Din + (int64_t)c0 * 8 + j), a0);
-      a1 = fmaf(v1, __ldg(Din + (int64_t)c1 * 8 + j), a1);
-      a2 = fmaf(v2, __ldg(Din + (int64_t)c2 * 8 + j), a2);
-      a3 = fmaf(v3, __ldg(Din + (int64_t)c3 * 8 + j), a3);
+  const int lane = threadIdx.x & 31;
+  const int j = lane & 7;      // right-hand side of this lane
+  const int grp = lane >> 3;   // 4 rows of a chunk at a time
+  const int64_t nw = (int64_t)gridDim.x * (BT / 32);
+  const int32_t nl = (int32_t)L.hdr[0];
+  const int64_t nch = L.hdr[1];
+  ChunkWalk walk;
+  for (int64_t q = (int64_t)blockIdx.x * (BT / 32) + (threadIdx.x >> 5); q < nch; q += nw) {
+    int64_t r0, r1;
+    int32_t c;
+    walk.rows(L, nl, q, r0, r1, c);
+    for (int64_t s = r0 + grp; s < r1; s += 4) {
+      const int64_t hi = rp[s + 1];
+      int64_t k = rp[s];
+      float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+      for (; k + 3 < hi; k += 4) {
+        const int32_t c0 = __ldcs(ci + k), c1 = __ldcs(ci + k + 1), c2 = __ldcs(ci + k + 2), c3 = __ldcs(ci + k + 3);
+        const float v0 = __ldcs(ah + k), v1 = __ldcs(ah + k + 1), v2 = __ldcs(ah + k + 2), v3 = __ldcs(ah + k + 3);
+        a0 = fmaf(v0, __ldg(Din + (int64_t)c0 * 8 + j), a0);
+        a1 = fmaf(v1, __ldg(Din + (int64_t)c1 * 8 + j), a1);
+        a2 = fmaf(v2, __ldg(Din + (int64_t)c2 * 8 + j), a2);
+        a3 = fmaf(v3, __ldg(Din + (int64_t)c3 * 8 + j), a3);
+      }
+      if (k < hi) {  // the last 1 to 3 entries, loads issued together
+        const bool o1 = k + 1 < hi, o2 = k + 2 < hi;
+        const int32_t c0 = __ldcs(ci + k), c1 = o1 ? __ldcs(ci + k + 1) : 0, c2 = o2 ? __ldcs(ci + k + 2) : 0;
+        const float v0 = __ldcs(ah + k), v1 = o1 ? __ldcs(ah + k + 1) : 0.0f, v2 = o2 ? __ldcs(ah + k + 2) : 0.0f;
+        a0 = fmaf(v0, __ldg(Din + (int64_t)c0 * 8 + j), a0);
+        if (o1) a1 = fmaf(v1, __ldg(Din + (int64_t)c1 * 8 + j), a1);
+        if (o2) a2 = fmaf(v2, __ldg(Din + (int64_t)c2 * 8 + j), a2);
+      }
+      // R and the new D are streamed (evict-first): L2 keeps the gathered D of the chains
+      // in the window instead
+      const bool qj = (sq[s] >> j) & 1u;
+      __stcs(Dout + s * 8 + j, qj ? __ldcs(R + s * 8 + j) + ((a0 + a1) + (a2 + a3)) : 0.0f);
     }
-    for (; k < hi; ++k) a0 = fmaf(__ldcs(ah + k), __ldg(Din + (int64_t)__ldcs(ci + k) * 8 + j), a0);
-    const bool q = (sq[s] >> j) & 1u;
-    Dout[s * 8 + j] = q ? R[s * 8 + j] + ((a0 + a1) + (a2 + a3)) : 0.0f;
   }
 }
 
-__global__ void k_bapply(int64_t total, double* __restrict__ X, const float* __restrict__ D,
+// X += D over the rows of the list's chains.
+__global__ void k_bapply(ChainList L, double* __restrict__ X, const float* __restrict__ D,
                          const SolveState* st) {
   if (st->done) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x)
-    X[i] += (double)D[i];
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+  const int32_t nl = (int32_t)L.hdr[0];
+  const int64_t nch = L.hdr[1];
+  ChunkWalk walk;
+  for (int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); q < nch; q += nw) {
+    int64_t r0, r1;
+    int32_t c;
+    walk.rows(L, nl, q, r0, r1, c);
+    for (int64_t i = r0 * 8 + lane; i < r1 * 8; i += 32) X[i] += (double)D[i];
+  }
+}
+
+// Block-wide exclusive scan (blockDim.x a multiple of 32, at most 1024); *total gets the
+// block's sum.  sh: 32 entries of shared memory.
+template <typename T>
+RDEV T block_excl_scan(T v, T* total, T* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  T inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) sh[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    T t = lane < nwarp ? sh[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = __shfl_up_sync(FULL, t, o);
+      if (lane >= o) t += y;
+    }
+    sh[lane] = t;
+  }
+  __syncthreads();
+  *total = sh[nwarp - 1];
+  const T ex = inc - v + (wid > 0 ? sh[wid - 1] : T(0));
+  __syncthreads();
+  return ex;
+}
+
+// Stopping rule per chain, after a residual step over list 1 (one CTA of CTL_NT threads):
+// a chain whose largest step max|r_j| is below eps stops (its sweep count is recorded)
+// and leaves the list; the others are compacted in place with their chunk prefix.  The
+// solve ends when the list is empty (or max_iter is reached, as in the mixed method).
+// work[] accumulates the rows and entries of the residual steps ({0, 1}) and of the
+// k - 1 sweeps that follow ({2, 3}).
+constexpr int CTL_NT = 1024;
+__global__ void __launch_bounds__(CTL_NT) k_bchain_ctl(SolveState* st, int64_t* hdr1, int32_t* id, int64_t* pre,
+                                                     const int64_t* __restrict__ coff,
+                                                     const int64_t* __restrict__ arp,
+                                                     unsigned long long* cmax, double* clast, int64_t* citer,
+                                                     double* work, int k) {
+  if (st->done) return;
+  __shared__ int64_t sh64[32];
+  __shared__ int64_t s_keep, s_chunks;
+  __shared__ double shd[4 * 32];
+  const int32_t nl = (int32_t)hdr1[0];
+  const int64_t it = st->iter + 1;
+  const double eps = st->eps;
+  if (threadIdx.x == 0) {
+    s_keep = 0;
+    s_chunks = 0;
+  }
+  unsigned long long mxb = 0ull;
+  int64_t rows_old = 0, ent_old = 0, rows_new = 0, ent_new = 0;
+  __syncthreads();
+  for (int32_t base = 0; base < nl; base += CTL_NT) {
+    const int32_t t = base + (int32_t)threadIdx.x;
+    int32_t c = -1;
+    int64_t keep = 0, nchk = 0;
+    if (t < nl) {
+      c = id[t];
+      const unsigned long long b = cmax[c];
+      cmax[c] = 0ull;
+      mxb = b > mxb ? b : mxb;
+      const double dl = __longlong_as_double((long long)(b > 0x7ff0000000000000ull ? 0x7ff0000000000000ull : b));
+      clast[c] = dl;
+      const int64_t r = coff[c + 1] - coff[c];
+      const int64_t e = arp[coff[c + 1]] - arp[coff[c]];
+      rows_old += r;
+      ent_old += e;
+      if (dl < eps) {
+        citer[c] = it;
+      } else {
+        keep = 1;
+        nchk = (r + BCH - 1) / BCH;
+        rows_new += r;
+        ent_new += e;
+      }
+    }
+    int64_t tk, tc;
+    const int64_t pk = block_excl_scan<int64_t>(keep, &tk, sh64);
+    const int64_t pc = block_excl_scan<int64_t>(nchk, &tc, sh64);
+    // every read of this tile happened before the scans' barriers; writes land at or
+    // below the reader's own position, never in a later tile
+    if (keep) {
+      id[s_keep + pk] = c;
+      pre[s_keep + pk] = s_chunks + pc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_keep += tk;
+      s_chunks += tc;
+    }
+    __syncthreads();
+  }
+  double red[4] = {(double)rows_old, (double)ent_old, (double)rows_new, (double)ent_new};
+  block_reduce<4, false>(red, shd);
+  __shared__ unsigned long long s_mx;
+  if (threadIdx.x == 0) s_mx = 0ull;
+  __syncthreads();
+  if (mxb) atomicMax(&s_mx, mxb);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    pre[s_keep] = s_chunks;
+    hdr1[0] = s_keep;
+    hdr1[1] = s_chunks;
+    const unsigned long long b = s_mx;
+    st->last = __longlong_as_double((long long)(b > 0x7ff0000000000000ull ? 0x7ff0000000000000ull : b));
+    st->refinements += 1;
+    st->iter += 1;
+    work[0] += red[0];
+    work[1] += red[1];
+    if (s_keep == 0) {
+      st->done = 1;
+      st->status = REACH_OK;
+    } else if (st->iter + (k - 1) > st->max_iter) {
+      st->done = 1;
+      st->status = REACH_ENOTCONV;
+    } else {
+      st->iter += k - 1;
+      work[2] += red[2] * (double)(k - 1);
+      work[3] += red[3] * (double)(k - 1);
+    }
+  }
 }
 
 __global__ void k_bout(int64_t n, int k, const double* __restrict__ X, double* __restrict__ out) {
@@ -249,23 +497,124 @@ static void l_pull(reach_batch* b, uint8_t* bits, const uint8_t* block, cudaStre
                                    b->changed);
 }
 
+static ChainList chain_list(const reach_batch* b, int l) {
+  return ChainList{b->lhdr + 2 * l, b->lid[l], b->lpre[l], b->coff};
+}
+
+// Grid of the chain-list kernels: one warp per chunk of list 0 at most.
+static int chunk_grid(reach_batch* b, const void* kernel) {
+  return grid_for(b->base, kernel, BT, b->chunks_all * 32);
+}
+
 static void l_bresid(reach_batch* b, bool report, cudaStream_t s) {
   reach_ctx* c = b->base;
   if (report) {
-    const int grid = grid_rows(c, (const void*)k_bresid<true>, BT, 2, c->n);
-    k_bresid<true><<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_jv, c->d, b->sq, b->X, b->R, b->D[1],
-                                       c->st, 63);
+    k_bresid<true><<<chunk_grid(b, (const void*)k_bresid<true>), BT, 0, s>>>(
+        chain_list(b, 0), c->a_rowptr, c->a_col, c->a_jv, c->d, b->sq, b->X, b->R, b->D[1], c->st, 63, b->cmax);
   } else {
-    const int grid = grid_rows(c, (const void*)k_bresid<false>, BT, 2, c->n);
-    k_bresid<false><<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_jv, c->d, b->sq, b->X, b->R, b->D[1],
-                                        c->st, 0);
+    k_bresid<false><<<chunk_grid(b, (const void*)k_bresid<false>), BT, 0, s>>>(
+        chain_list(b, 1), c->a_rowptr, c->a_col, c->a_jv, c->d, b->sq, b->X, b->R, b->D[1], c->st, 0, b->cmax);
   }
 }
 
 static void l_bsweep(reach_batch* b, const float* din, float* dout, cudaStream_t s) {
   reach_ctx* c = b->base;
-  const int grid = grid_rows(c, (const void*)k_bsweep, BT, 8, c->n);
-  k_bsweep<<<grid, BT, 0, s>>>(c->n, c->a_rowptr, c->a_col, c->a_hi, b->sq, b->R, din, dout, c->st);
+  k_bsweep<<<chunk_grid(b, (const void*)k_bsweep), BT, 0, s>>>(chain_list(b, 1), c->a_rowptr, c->a_col, c->a_hi,
+                                                               b->sq, b->R, din, dout, c->st);
+}
+
+// Chain membership check: every positive entry of row s stays inside the chain of s.
+// bad[0] = 1 and bad[1] = the smallest offending row on failure.
+__global__ void k_chain_check(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              const double* __restrict__ val, const int64_t* __restrict__ coff, int32_t nc,
+                              unsigned long long* bad) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    int32_t lo = 0, hi = nc;  // coff[lo] <= s < coff[hi]
+    while (hi - lo > 1) {
+      const int32_t mid = (lo + hi) >> 1;
+      if (coff[mid] <= s) lo = mid;
+      else hi = mid;
+    }
+    const int64_t a = coff[lo], e = coff[lo + 1];
+    for (int64_t k = rp[s]; k < rp[s + 1]; ++k) {
+      const int64_t j = col[k];
+      if (val[k] > 0.0 && (j < a || j >= e)) {
+        bad[0] = 1ull;
+        atomicMin(&bad[1], (unsigned long long)s);
+        break;
+      }
+    }
+  }
+}
+
+static void free_chains(reach_batch* b) {
+  for (int l = 0; l < 2; ++l) {
+    if (b->lid[l]) cudaFree(b->lid[l]);
+    if (b->lpre[l]) cudaFree(b->lpre[l]);
+    b->lid[l] = nullptr;
+    b->lpre[l] = nullptr;
+  }
+  void* ps[] = {b->coff, b->lhdr, b->cmax, b->clast, b->citer, b->work};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  b->coff = nullptr;
+  b->lhdr = nullptr;
+  b->cmax = nullptr;
+  b->clast = nullptr;
+  b->citer = nullptr;
+  b->work = nullptr;
+  b->n_chains = 0;
+  b->chunks_all = 0;
+}
+
+// Installs chains with offsets h_off[0 .. nc] (host, already checked): device copies of
+// the offsets, list 0 (every chain) and the per-chain state.  A captured solve graph
+// holds the old pointers, so it is dropped.
+static cudaError_t install_chains(reach_batch* b, int32_t nc, const int64_t* h_off) {
+  cudaStream_t s = b->base->stream;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  if (b->g_exec[2]) cudaGraphExecDestroy(b->g_exec[2]);
+  b->g_exec[2] = nullptr;
+  b->g_key[2] = -1;
+  free_chains(b);
+  const size_t n1 = (size_t)nc + 1;
+  if ((e = cudaMalloc((void**)&b->coff, n1 * 8)) != cudaSuccess || (e = cudaMalloc((void**)&b->lid[0], n1 * 4)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&b->lid[1], n1 * 4)) != cudaSuccess || (e = cudaMalloc((void**)&b->lpre[0], n1 * 8)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&b->lpre[1], n1 * 8)) != cudaSuccess || (e = cudaMalloc((void**)&b->lhdr, 4 * 8)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&b->cmax, n1 * 8)) != cudaSuccess || (e = cudaMalloc((void**)&b->clast, n1 * 8)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&b->citer, n1 * 8)) != cudaSuccess || (e = cudaMalloc((void**)&b->work, 4 * 8)) != cudaSuccess) {
+    free_chains(b);
+    return e;
+  }
+  std::vector<int32_t> id(nc);
+  std::vector<int64_t> pre(n1), hdr(4);
+  int64_t chunks = 0;
+  for (int32_t c = 0; c < nc; ++c) {
+    id[c] = c;
+    pre[c] = chunks;
+    chunks += (h_off[c + 1] - h_off[c] + BCH - 1) / BCH;
+  }
+  pre[nc] = chunks;
+  hdr[0] = nc;
+  hdr[1] = chunks;
+  hdr[2] = nc;
+  hdr[3] = chunks;
+  e = cudaMemcpyAsync(b->coff, h_off, n1 * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->lid[0], id.data(), (size_t)nc * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->lpre[0], pre.data(), n1 * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->lhdr, hdr.data(), 4 * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->cmax, 0, n1 * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->clast, 0, n1 * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->citer, 0xff, n1 * 8, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    free_chains(b);
+    return e;
+  }
+  b->n_chains = nc;
+  b->chunks_all = chunks;
+  return cudaSuccess;
 }
 
 // Runs one backward fixed point to completion (conditional-while graph or host loop).
@@ -371,6 +720,7 @@ void reach_batch_destroy(reach_batch* b) {
     if (b->g_exec[i]) cudaGraphExecDestroy(b->g_exec[i]);
   bfree(b->gbits); bfree(b->rbits); bfree(b->bbits); bfree(b->sq); bfree(b->one);
   bfree(b->X); bfree(b->R); bfree(b->D[0]); bfree(b->D[1]); bfree(b->changed);
+  free_chains(b);
   reach_destroy(b->base);
   delete b;
 }
@@ -414,6 +764,10 @@ reach_status reach_batch_create(reach_batch** out, int64_t n, int64_t m, const i
     e = cudaStreamSynchronize(s);
   }
   bfree(gdev);
+  if (e == cudaSuccess) {  // one chain until the caller names them
+    const int64_t one[2] = {0, n};
+    e = install_chains(b, 1, one);
+  }
   if (e != cudaSuccess) {
     reach_status r = bcuda(b, e, "reach_batch_create");
     std::string msg = base->err;
@@ -473,6 +827,57 @@ reach_status reach_batch_precompute(reach_batch* b, int32_t mode) {
   return REACH_OK;
 }
 
+reach_status reach_batch_set_chains(reach_batch* b, int32_t n_chains, const int64_t* offsets) {
+  if (!b) return bfail(nullptr, REACH_EINVAL, "reach_batch_set_chains: NULL batch");
+  if (n_chains < 1 || !offsets) return bfail(b, REACH_EINVAL, "reach_batch_set_chains: need n_chains >= 1 and offsets");
+  reach_ctx* c = b->base;
+  const int64_t n = c->n;
+  if (offsets[0] != 0 || offsets[n_chains] != n)
+    return bfail(b, REACH_EINVAL, "reach_batch_set_chains: offsets must start at 0 and end at n");
+  for (int32_t i = 0; i < n_chains; ++i)
+    if (offsets[i + 1] < offsets[i]) return bfail(b, REACH_EINVAL, "reach_batch_set_chains: offsets must not decrease");
+  cudaStream_t s = c->stream;
+  int64_t* doff = nullptr;
+  unsigned long long* bad = nullptr;
+  unsigned long long hbad[2] = {0ull, ~0ull};
+  cudaError_t e = balloc(&doff, (int64_t)n_chains + 1);
+  if (e == cudaSuccess) e = balloc(&bad, 2);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(doff, offsets, sizeof(int64_t) * ((size_t)n_chains + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bad, hbad, sizeof(hbad), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    k_chain_check<<<grid_for(c, (const void*)k_chain_check, BT, n), BT, 0, s>>>(n, c->rowptr, c->col, c->val, doff,
+                                                                              n_chains, bad);
+    e = cudaMemcpyAsync(hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  bfree(doff);
+  bfree(bad);
+  if (e != cudaSuccess) return bcuda(b, e, "reach_batch_set_chains");
+  if (hbad[0])
+    return bfail(b, REACH_EINVAL, "reach_batch_set_chains: row " + std::to_string(hbad[1]) +
+                                      " has an entry outside its chain");
+  e = install_chains(b, n_chains, offsets);
+  if (e != cudaSuccess) {
+    // the batch keeps working as one chain
+    const int64_t one[2] = {0, n};
+    reach_status r = bcuda(b, e, "reach_batch_set_chains");
+    install_chains(b, 1, one);
+    return r;
+  }
+  return REACH_OK;
+}
+
+reach_status reach_batch_chain_info(reach_batch* b, int64_t* iters, double* last) {
+  if (!b) return bfail(nullptr, REACH_EINVAL, "reach_batch_chain_info: NULL batch");
+  cudaStream_t s = b->base->stream;
+  cudaError_t e = cudaSuccess;
+  if (iters) e = cudaMemcpyAsync(iters, b->citer, sizeof(int64_t) * (size_t)b->n_chains, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && last)
+    e = cudaMemcpyAsync(last, b->clast, sizeof(double) * (size_t)b->n_chains, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? REACH_OK : bcuda(b, e, "reach_batch_chain_info");
+}
+
 reach_status reach_batch_get_classes(reach_batch* b, uint8_t* cls, int32_t flags) {
   if (!b) return bfail(nullptr, REACH_EINVAL, "reach_batch_get_classes: NULL batch");
   if (!b->have_classes) return bfail(b, REACH_ESTATE, "reach_batch_get_classes: call reach_batch_precompute first");
@@ -517,22 +922,32 @@ reach_status reach_batch_solve(reach_batch* b, double eps, int64_t max_iter, int
   double* xdev = x_out;
   if (e == cudaSuccess && flags == REACH_HOST) e = balloc(&xdev, n * b->k);
   if (e != cudaSuccess) return bcuda(b, e, "reach_batch_solve");
-  const int g = pick_group(n, c->m_q);
   const int kref = refine_k;
+  const int32_t nc = b->n_chains;
   k_batch_init_x<<<grid_for(c, (const void*)k_batch_init_x, BT, n * 8), BT, 0, s>>>(n, b->one, b->X);
-  e = cudaEventRecord(c->ev0, s);
+  // list 1 starts as every chain; per-chain state cleared
+  e = cudaMemcpyAsync(b->lid[1], b->lid[0], (size_t)nc * 4, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->lpre[1], b->lpre[0], (size_t)(nc + 1) * 8, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->lhdr + 2, b->lhdr, 2 * 8, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->cmax, 0, (size_t)nc * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->clast, 0, (size_t)nc * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->citer, 0xff, (size_t)nc * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->work, 0, 4 * 8, s);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev0, s);
   if (e == cudaSuccess) {
-    const int64_t key = (n * 1000003LL + c->m_q) * 64 + g * 4 + kref * 1000;
+    // the graph holds the chain-list pointers: set_chains drops it when they change
+    const int64_t key = ((n * 1000003LL + c->m_q) * 64 + kref) * 1000003LL + b->chunks_all * 31 + nc;
     e = run_loop(c, b->g_exec[2], b->g_key[2], key, [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
       l_bresid(b, false, cs);
-      launch_check_mixed(cs, c->st, 0, kref);
+      k_bchain_ctl<<<1, CTL_NT, 0, cs>>>(c->st, b->lhdr + 2, b->lid[1], b->lpre[1], b->coff, c->a_rowptr, b->cmax,
+                                         b->clast, b->citer, b->work, kref);
       // kref - 1 FP32 sweeps: D[1] -> D[0] -> ...; kref even, so the last lands in D[0]
       for (int j = 1; j < kref; ++j) {
         const float* din = (j & 1) ? b->D[1] : b->D[0];
         float* dout = (j & 1) ? b->D[0] : b->D[1];
         l_bsweep(b, din, dout, cs);
       }
-      k_bapply<<<grid_for(c, (const void*)k_bapply, BT, n * 8), BT, 0, cs>>>(n * 8, b->X, b->D[0], c->st);
+      k_bapply<<<chunk_grid(b, (const void*)k_bapply), BT, 0, cs>>>(chain_list(b, 1), b->X, b->D[0], c->st);
     });
   }
   if (e == cudaSuccess) {
@@ -541,7 +956,9 @@ reach_status reach_batch_solve(reach_batch* b, double eps, int64_t max_iter, int
     k_bout<<<grid_for(c, (const void*)k_bout, BT, n * b->k), BT, 0, s>>>(n, b->k, b->X, xdev);
     e = cudaEventRecord(c->ev1, s);
   }
+  double work[4] = {0.0, 0.0, 0.0, 0.0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, c->st, sizeof(hs), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(work, b->work, sizeof(work), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && flags == REACH_HOST)
     e = cudaMemcpyAsync(x_out, xdev, sizeof(double) * (size_t)(n * b->k), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -558,8 +975,13 @@ reach_status reach_batch_solve(reach_batch* b, double eps, int64_t max_iter, int
     info->resid_inf = hs.resid;
     info->ms_precompute = c->ms_precompute;
     info->ms_solve = ms;
-    info->bytes_moved = (double)hs.refinements * ((double)c->m_q * 12.0 + (double)n * 150.0) +
-                        (double)(hs.iter - hs.refinements) * ((double)c->m_q * 8.0 + (double)n * 80.0);
+    // over the rows each step actually visited (converged chains drop out):
+    // residual steps: 8 B value + 4 B index per entry; per row 8 B rowptr, 64 B X read,
+    // 2 x 32 B R and D written, 1 B mask.  Sweeps: 4 + 4 B per entry; per row 8 B rowptr,
+    // 32 B R read, 32 B D written, 1 B mask.  X += D once per period: 160 B per row.
+    // Gathers of X and D are not counted.
+    info->bytes_moved = work[1] * 12.0 + work[0] * 137.0 + work[3] * 8.0 + work[2] * 73.0 +
+                        work[2] / (double)(kref - 1) * 160.0;
     info->status = hs.status;
     info->refinements = hs.refinements;
   }

@@ -58,6 +58,13 @@ def test_argument_checks_need_no_device(so):
     assert ctx.value is None
 
 
+def test_batch_entry_points_reject_null_batch(so):
+    off = np.array([0, 1], np.int64)
+    assert so.reach_batch_set_chains(None, 1, off.ctypes.data) == R.REACH_EINVAL
+    assert so.reach_batch_chain_info(None, None, None) == R.REACH_EINVAL
+    assert so.reach_batch_solve(None, 1e-9, 10, 0, None, 0, None) == R.REACH_EINVAL
+
+
 def test_param_entry_points_reject_bad_arguments(so):
     assert so.reach_param_probs(0, 0, None, None, None, None, 0, None, None) == R.REACH_EINVAL
     assert so.reach_param_grad_theta(1, 1, None, None, None, None, 5000, None, None) == R.REACH_EINVAL
