@@ -1,6 +1,9 @@
 // Graph precompute of §2.2-§2.3 on the device: input validation, the reversed
 // underlying digraph, backward breadth-first search for S=0 and S=1, the
 // partition, and extraction of A (off-diagonal), d = 1 - A_ii and b over S?.
+#include <algorithm>
+#include <cstdlib>
+
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -276,6 +279,10 @@ __global__ void k_bfs_level(const int64_t* __restrict__ trp, const int32_t* __re
   const int L = st->level;
   const int cur = L & 1;
   const uint32_t cnt = st->count[cur];
+  if (cnt == 0) {  // the search already ended (in the cluster kernel of this body)
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
   const int32_t* qc = cur ? qb : qa;
   int32_t* qn = cur ? qa : qb;
   RowGroups rg = RowGroups::make<G>();
@@ -315,6 +322,133 @@ static void launch_level(reach_ctx* c, int grid, int avoid_goal, uint32_t* vis,
                                       c->queue + c->n, c->bfs, c->ticket, h, use_cond);
 }
 
+// Levels with small frontiers on one thread-block cluster, many per launch: the
+// cluster's hardware barrier (a fraction of a microsecond) replaces the kernel boundary
+// and the grid-wide ticket of k_bfs_level, which dominate a deep search through narrow
+// frontiers (a model checker's layered state space: thousands of levels of a few
+// thousand states).  The launch returns, with the search state as k_bfs_level keeps it,
+// when the frontier is empty or its estimated edges exceed max_edges; k_bfs_level then
+// runs the next level on the whole GPU.  Frontier counts, the queue and the visited
+// bits are read through L2 (other SMs of the cluster wrote them).
+constexpr int BFS_CL_NT = 512;
+
+template <int G>
+__global__ void __launch_bounds__(BFS_CL_NT, 1) k_bfs_cluster(const int64_t* __restrict__ trp,
+                                                              const int32_t* __restrict__ tcol,
+                                                              const uint8_t* __restrict__ goal, int avoid_goal,
+                                                              uint32_t* vis, int32_t* qa, int32_t* qb, BfsState* st,
+                                                              double mean_deg, double max_edges, int64_t max_levels) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int64_t tid = (int64_t)cl.block_rank() * blockDim.x + threadIdx.x;
+  const int64_t groups = (int64_t)cl.num_blocks() * blockDim.x / G;
+  const int lane = threadIdx.x & (G - 1);
+  int L = *(volatile int32_t*)&st->level;
+  for (int64_t it = 0; it < max_levels; ++it) {
+    const int cur = L & 1;
+    const uint32_t cnt = *(volatile uint32_t*)&st->count[cur];
+    // the same values in every thread: written before the last barrier, not since
+    if (cnt == 0 || (double)cnt * mean_deg > max_edges) break;
+    cl.sync();  // every thread has read cnt: count[cur] may be cleared for the level after next
+    if (tid == 0) st->count[cur] = 0u;
+    const int32_t* qc = cur ? qb : qa;
+    int32_t* qn = cur ? qa : qb;
+    for (int64_t i = tid / G; i < (int64_t)cnt; i += groups) {
+      const int32_t v = __ldcg(qc + i);
+      const int64_t hi = trp[v + 1];
+      for (int64_t k = trp[v] + lane; k < hi; k += G) {
+        const int32_t u = tcol[k];
+        if (avoid_goal && goal[u]) continue;
+        const uint32_t bit = 1u << (u & 31);
+        if (__ldcg(vis + (u >> 5)) & bit) continue;
+        const uint32_t old = atomicOr(vis + (u >> 5), bit);
+        if (!(old & bit)) __stcg(qn + agg_inc(&st->count[cur ^ 1]), u);
+      }
+    }
+    cl.sync();  // the next frontier is complete
+    ++L;
+  }
+  if (tid == 0) st->level = L;
+}
+
+// Cluster size the device can host for k_bfs_cluster<G> (16, else 8, else 0 = none).
+template <int G>
+static int bfs_cluster_size(reach_ctx* c) {
+  const void* fn = (const void*)k_bfs_cluster<G>;
+  for (int cs : {16, 8}) {
+    if (cs > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(BFS_CL_NT);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) == cudaSuccess && nc > 0) return cs;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+// Estimated frontier edges up to which a level runs on the cluster.  Per level the
+// cluster needs about a microsecond plus its edges at a few thousand per microsecond;
+// the grid-wide level about 10 microseconds (launch, ticket) plus its edges at tens of
+// thousands per microsecond; they cross near 24K edges.
+constexpr double BFS_CLUSTER_EDGES = 24576.0;
+
+template <int G>
+static cudaError_t launch_cluster_levels(reach_ctx* c, int cs, int avoid_goal, uint32_t* vis, cudaStream_t s) {
+  const void* fn = (const void*)k_bfs_cluster<G>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(BFS_CL_NT);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const int64_t* trp = c->t_rowptr;
+  const int32_t* tcol = c->t_col;
+  const uint8_t* goal = c->goal;
+  int32_t* qa = c->queue;
+  int32_t* qb = c->queue + c->n;
+  BfsState* st = c->bfs;
+  double mean_deg = c->n > 0 ? std::max(1.0, (double)c->m / (double)c->n) : 1.0;
+  double max_edges = BFS_CLUSTER_EDGES;
+  int64_t max_levels = c->n + 2;
+  void* args[] = {&trp, &tcol, &goal, &avoid_goal, &vis, &qa, &qb, &st, &mean_deg, &max_edges, &max_levels};
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+static int cluster_dispatch_size(reach_ctx* c, int g) {
+  switch (g) {
+    case 2: return bfs_cluster_size<2>(c);
+    case 4: return bfs_cluster_size<4>(c);
+    case 8: return bfs_cluster_size<8>(c);
+    case 16: return bfs_cluster_size<16>(c);
+    default: return bfs_cluster_size<32>(c);
+  }
+}
+
+static cudaError_t cluster_dispatch(reach_ctx* c, int g, int cs, int avoid_goal, uint32_t* vis, cudaStream_t s) {
+  switch (g) {
+    case 2: return launch_cluster_levels<2>(c, cs, avoid_goal, vis, s);
+    case 4: return launch_cluster_levels<4>(c, cs, avoid_goal, vis, s);
+    case 8: return launch_cluster_levels<8>(c, cs, avoid_goal, vis, s);
+    case 16: return launch_cluster_levels<16>(c, cs, avoid_goal, vis, s);
+    default: return launch_cluster_levels<32>(c, cs, avoid_goal, vis, s);
+  }
+}
+
 static void level_dispatch(reach_ctx* c, int g, int grid, int avoid_goal, uint32_t* vis,
                            cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
   switch (g) {
@@ -342,6 +476,9 @@ cudaError_t bfs_backward(reach_ctx* c, int source_kind, bool avoid_goal) {
   k_bfs_init<<<ig, 256, 0, s>>>(n, source_kind, c->goal, other, vis, c->queue, c->bfs);
   const int g = pick_group(n, c->m);
   const int grid = c->sm_count * 4;
+  // small frontiers run on one cluster (0: no cluster launch available, or disabled)
+  const char* ev = std::getenv("REACH_BFS_CLUSTER");
+  const int cs = (ev && ev[0] == '0') ? 0 : cluster_dispatch_size(c, g);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (c->device_loops) {
@@ -362,8 +499,10 @@ cudaError_t bfs_backward(reach_ctx* c, int source_kind, bool avoid_goal) {
       e = cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeRelaxed);
       if (e == cudaSuccess) {
+        if (cs > 0) e = cluster_dispatch(c, g, cs, avoid_goal ? 1 : 0, vis, c->cap);
         level_dispatch(c, g, grid, avoid_goal ? 1 : 0, vis, h, 1, c->cap);
-        e = cudaStreamEndCapture(c->cap, &body);
+        const cudaError_t e2 = cudaStreamEndCapture(c->cap, &body);
+        if (e == cudaSuccess) e = e2;
       }
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -375,6 +514,7 @@ cudaError_t bfs_backward(reach_ctx* c, int source_kind, bool avoid_goal) {
   // host-driven level loop
   BfsState hs;
   for (int64_t level = 0; level <= n + 1; ++level) {
+    if (cs > 0 && (e = cluster_dispatch(c, g, cs, avoid_goal ? 1 : 0, vis, s)) != cudaSuccess) return e;
     level_dispatch(c, g, grid, avoid_goal ? 1 : 0, vis, cudaGraphConditionalHandle(), 0, s);
     e = cudaMemcpyAsync(&hs, c->bfs, sizeof(hs), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -363,3 +363,22 @@ def test_bulk_copy_staged_sweep_matches_oracle(c1, name, monkeypatch):
     with R.Solver(c.n, c.rowptr, c.col, c.val, c.goal) as s:
         ms = R.reach_time_kernel(s.ctx, "sweep32", 3)
     assert ms > 0.0
+
+
+@pytest.mark.parametrize("name", ["layered", "dense", "gambler", "random"])
+def test_partition_with_and_without_the_cluster_search(c1, name, monkeypatch):
+    """The backward searches of §2.2 run their narrow levels on one thread-block cluster and
+    wide levels on the whole GPU; with the cluster path switched off (REACH_BFS_CLUSTER=0)
+    every level runs on the GPU.  Both give the oracle's S=0 / S=1 / S? exactly, in both
+    partition modes."""
+    c = {"random": lambda: c1,
+         "layered": lambda: synth.layered_chain(layers=300, width=200, seed=12),
+         "dense": lambda: synth.dense_random_chain(n=3000, density=0.1, sink_frac=0.02, seed=7),
+         "gambler": lambda: synth.gamblers_ruin(500, 0.48)}[name]()
+    need_gpu()
+    for mode in MODES:
+        cls_o = O.partition(c.n, c.rowptr, c.col, c.val, c.goal, mode)
+        for flag in ("1", "0"):
+            monkeypatch.setenv("REACH_BFS_CLUSTER", flag)
+            with R.Solver(c.n, c.rowptr, c.col, c.val, c.goal, mode=mode) as s:
+                assert np.array_equal(s.classes(), cls_o), (name, mode, flag)
