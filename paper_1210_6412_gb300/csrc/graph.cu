@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(BFS_CL_NT, 1) k_bfs_cluster(const int64_t* __r
         const int32_t u = tcol[k];
         if (avoid_goal && goal[u]) continue;
         const uint32_t bit = 1u << (u & 31);
-        if (__ldcg(vis + (u >> 5)) & bit) continue;
+        // no read-before-atomic filter here: on a narrow level it would add a round trip
         const uint32_t old = atomicOr(vis + (u >> 5), bit);
         if (!(old & bit)) __stcg(qn + agg_inc(&st->count[cur ^ 1]), u);
       }
