@@ -294,21 +294,28 @@ __global__ void __launch_bounds__(BT) k_bsweep(ChainList L, const int64_t* __res
       const int64_t hi = rp[s + 1];
       int64_t k = rp[s];
       float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-      for (; k + 3 < hi; k += 4) {
-        const int32_t c0 = __ldcs(ci + k), c1 = __ldcs(ci + k + 1), c2 = __ldcs(ci + k + 2), c3 = __ldcs(ci + k + 3);
-        const float v0 = __ldcs(ah + k), v1 = __ldcs(ah + k + 1), v2 = __ldcs(ah + k + 2), v3 = __ldcs(ah + k + 3);
-        a0 = fmaf(v0, __ldg(Din + (int64_t)c0 * 8 + j), a0);
-        a1 = fmaf(v1, __ldg(Din + (int64_t)c1 * 8 + j), a1);
-        a2 = fmaf(v2, __ldg(Din + (int64_t)c2 * 8 + j), a2);
-        a3 = fmaf(v3, __ldg(Din + (int64_t)c3 * 8 + j), a3);
-      }
-      if (k < hi) {  // the last 1 to 3 entries, loads issued together
-        const bool o1 = k + 1 < hi, o2 = k + 2 < hi;
-        const int32_t c0 = __ldcs(ci + k), c1 = o1 ? __ldcs(ci + k + 1) : 0, c2 = o2 ? __ldcs(ci + k + 2) : 0;
-        const float v0 = __ldcs(ah + k), v1 = o1 ? __ldcs(ah + k + 1) : 0.0f, v2 = o2 ? __ldcs(ah + k + 2) : 0.0f;
-        a0 = fmaf(v0, __ldg(Din + (int64_t)c0 * 8 + j), a0);
-        if (o1) a1 = fmaf(v1, __ldg(Din + (int64_t)c1 * 8 + j), a1);
-        if (o2) a2 = fmaf(v2, __ldg(Din + (int64_t)c2 * 8 + j), a2);
+      // eight entries per trip, every index and value load before the gathers: a row of
+      // the batch (2 to 32 entries) takes one to four round trips
+      for (; k < hi; k += 8) {
+        int32_t c[8];
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const bool ok = k + u < hi;
+          c[u] = ok ? __ldcs(ci + k + u) : 0;
+          v[u] = ok ? __ldcs(ah + k + u) : 0.0f;
+        }
+        float g[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) g[u] = k + u < hi ? __ldg(Din + (int64_t)c[u] * 8 + j) : 0.0f;
+        a0 = fmaf(v[0], g[0], a0);
+        a1 = fmaf(v[1], g[1], a1);
+        a2 = fmaf(v[2], g[2], a2);
+        a3 = fmaf(v[3], g[3], a3);
+        a0 = fmaf(v[4], g[4], a0);
+        a1 = fmaf(v[5], g[5], a1);
+        a2 = fmaf(v[6], g[6], a2);
+        a3 = fmaf(v[7], g[7], a3);
       }
       // R and the new D are streamed (evict-first): L2 keeps the gathered D of the chains
       // in the window instead

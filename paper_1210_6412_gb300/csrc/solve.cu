@@ -33,10 +33,12 @@ RDEV int4 ld_idx4(const uint16_t* p) {
   return make_int4(u.x, u.y, u.z, u.w);
 }
 
+// init: the accumulator's starting value (a row's constant term, so that adding it costs
+// no separate FP64 instruction).
 template <int G, bool V, typename XF>
 RDEV double dot64(int64_t lo, int64_t hi, int lane, const int32_t* __restrict__ ci,
-                  const double* __restrict__ av, XF xf) {
-  double s = 0.0;
+                  const double* __restrict__ av, XF xf, double init = 0.0) {
+  double s = init;
   if constexpr (V) {
     int64_t a = (lo + 3) & ~int64_t(3);
     if (a > hi) a = hi;
@@ -163,8 +165,9 @@ RDEV float dot32(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
 template <int G, bool V, typename IT = int32_t>
 RDEV double dot_hilo(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
                      const float* __restrict__ ah, const float* __restrict__ al,
-                     const double* __restrict__ x, const float* __restrict__ xf, float& sl) {
-  double s = 0.0;
+                     const double* __restrict__ x, const float* __restrict__ xf, float& sl,
+                     double init = 0.0) {
+  double s = init;
   if constexpr (V) {
     int64_t a = (lo + 3) & ~int64_t(3);
     if (a > hi) a = hi;
@@ -325,14 +328,17 @@ __global__ void __launch_bounds__(NT) k_jacobi64(int64_t nq, const int64_t* __re
       bv = bj[i];
       xo = x[i];
     }
-    if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, aj, xf);
+    // short rows: the sum starts at bj_i in lane 0 (bv = 0 elsewhere), which saves the
+    // separate FP64 add on a pipe that bounds these sweeps
+    if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, aj, xf, V ? 0.0 : bv);
     s = group_sum<G>(s);
     if (i < nq && rg.lane == 0) {
       if (V) {
         bv = bj[i];
         xo = x[i];
       }
-      const double xv = bv + s;          // (b_i + sum A_ij x_j) / d_i in the Jacobi form
+      // (b_i + sum A_ij x_j) / d_i in the Jacobi form
+      const double xv = V ? bv + s : s;
       mx = umax64(mx, abs_bits(xv - xo));
       xn[i] = xv;
     }
@@ -420,7 +426,7 @@ __global__ void __launch_bounds__(NT) k_resid_hilo(int64_t nq, const int64_t* __
       bv = bj[i];
       xo = x[i];
     }
-    if (i < nq) s = dot_hilo<G, V, IT>(rp[i], rp[i + 1], rg.lane, ci, ah, al, x, xf, sl);
+    if (i < nq) s = dot_hilo<G, V, IT>(rp[i], rp[i + 1], rg.lane, ci, ah, al, x, xf, sl, V ? 0.0 : bv);
     s = group_sum<G>(s);
     sl = group_sum<G>(sl);
     if (i < nq && rg.lane == 0) {
@@ -428,8 +434,9 @@ __global__ void __launch_bounds__(NT) k_resid_hilo(int64_t nq, const int64_t* __
         bv = bj[i];
         xo = x[i];
       }
-      // residual of the Jacobi form: r_i / d_i = bj_i + (Aj x)_i - x_i
-      const double r = bv + (s + (double)sl) - xo;
+      // residual of the Jacobi form: r_i / d_i = bj_i + (Aj x)_i - x_i (short rows: bj_i is
+      // already in s)
+      const double r = ((V ? bv + s : s) + (double)sl) - xo;
       const float rf = __double2float_rn(r);
       r32[i] = rf;
       dl0[i] = rf;
