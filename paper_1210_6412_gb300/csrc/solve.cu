@@ -47,7 +47,7 @@ RDEV double dot64(int64_t lo, int64_t hi, int lane, const int32_t* __restrict__ 
     // four independent FP64 accumulators: the narrow FP64 pipe of GB300 has a long
     // latency, and one dependent chain per lane would leave it waiting
     double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    for (int64_t k = a + 4 * lane; k < e; k += 128) {
+    for (int64_t k = a + 4 * lane; k < e; k += 4 * G) {
       const int4 c4 = __ldcs(reinterpret_cast<const int4*>(ci + k));
       const double2 v0 = __ldcs(reinterpret_cast<const double2*>(av + k));
       const double2 v1 = __ldcs(reinterpret_cast<const double2*>(av + k + 2));
@@ -104,7 +104,7 @@ RDEV float dot32(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
     auto load_trip = [&](int64_t k, int4 (&ci4)[U], float4 (&vv4)[U]) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int64_t kk = k + 128 * u;
+        const int64_t kk = k + 4 * G * u;
         if (kk < e) {
           ci4[u] = ld_idx4(ci + kk);
           vv4[u] = __ldcs(reinterpret_cast<const float4*>(av + kk));
@@ -117,7 +117,7 @@ RDEV float dot32(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
     int64_t k = a + 4 * lane;
     load_trip(k, c4, v4);
     while (k < e) {
-      const int64_t kn = k + 128 * U;
+      const int64_t kn = k + 4 * G * U;
       int4 n4[U];
       float4 w4[U];
       load_trip(kn, n4, w4);
@@ -179,7 +179,7 @@ RDEV double dot_hilo(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci
       sl = fmaf(__ldcs(al + k), __ldg(xf + c), sl);
     }
     double s1 = 0.0, s2 = 0.0, s3 = 0.0;   // independent FP64 chains (see dot64)
-    for (int64_t k = a + 4 * lane; k < e; k += 128) {
+    for (int64_t k = a + 4 * lane; k < e; k += 4 * G) {
       const int4 c4 = ld_idx4(ci + k);
       const float4 h = __ldcs(reinterpret_cast<const float4*>(ah + k));
       const float4 l = __ldcs(reinterpret_cast<const float4*>(al + k));
@@ -791,11 +791,13 @@ struct Lay {
 };
 
 constexpr int LAY_SEG = 128;
+constexpr int LAY_VEC16 = 48;   // half a warp per row with 16-byte loads
 constexpr int LAY_TMA = 80;
 
 static Lay lay_of(int code) {
   if (code == LAY_SEG) return Lay{32, true, true};
   if (code == LAY_TMA) return Lay{32, true, false, true};
+  if (code == LAY_VEC16) return Lay{16, true};
   return code >= 64 ? Lay{32, true} : Lay{code, false};
 }
 
@@ -838,7 +840,8 @@ static Lay row_layout(reach_ctx* c, int method) {
 
 #define LAY_DISPATCH(L, FN, ...)                          \
   do {                                                    \
-    if ((L).vec) FN<32, true>(__VA_ARGS__);               \
+    if ((L).vec && (L).g == 16) FN<16, true>(__VA_ARGS__); \
+    else if ((L).vec) FN<32, true>(__VA_ARGS__);          \
     else switch ((L).g) {                                 \
         case 1: FN<1, false>(__VA_ARGS__); break;         \
         case 2: FN<2, false>(__VA_ARGS__); break;         \
@@ -1228,7 +1231,7 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
   // tiles (FP64 Jacobi and the FP32 sweep), which wins when a few rows are very long
   // (LAY_TMA, the FP32 sweep staged by bulk copies, is not a candidate: it measured 1.7x
   // slower than 64 on the dense system, with each row's first segments arriving cold)
-  const int codes[9] = {1, 2, 4, 8, 16, 32, 64, 66, LAY_SEG};
+  const int codes[10] = {1, 2, 4, 8, 16, 32, LAY_VEC16, 64, 66, LAY_SEG};
   const double mean = (double)c->m_q / (double)c->n_q;
   Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_jv, c->bj};   // Jacobi form (the FP64 sweep)
   cudaStream_t s = c->stream;

@@ -191,7 +191,7 @@ def test_autotune_then_solve(c1, method, tol):
     with R.Solver(c1.n, c1.rowptr, c1.col, c1.val, c1.goal) as s:
         s.solve("jacobi", eps=1e-12)                 # leaves the device state 'done'
         t = s.autotune(method)
-        assert t["lanes"] in (1, 2, 4, 8, 16, 32, 64, 66, 128) and t["sweep_ms"] > 0
+        assert t["lanes"] in (1, 2, 4, 8, 16, 32, 48, 64, 66, 128) and t["sweep_ms"] > 0
         x, info = s.solve(method, eps=_eps(method))
         assert np.max(np.abs(x - x_o)) <= tol
         for k in ("jacobi64", "sweep32", "resid_hilo", "bicgstab_spmv"):
@@ -331,6 +331,23 @@ def test_short_row_mappings_match_oracle(c1, name, lanes, method, tol, monkeypat
     assert np.max(np.abs(x - x_o)) <= tol
 
 
+@pytest.mark.parametrize("lanes", ["48", "64"])
+@pytest.mark.parametrize("name", ["dense", "skewed", "random"])
+@pytest.mark.parametrize("method,tol", [("jacobi", TOL_FP64), ("mixed", TOL_MIXED), ("bicgstab", TOL_FP64)])
+def test_vector_row_mappings_match_oracle(c1, name, lanes, method, tol, monkeypatch):
+    """REACH_LANES=48 (half a warp per row) and 64 (a warp per row), both with 16-byte
+    loads of four indices and four values after a scalar head that aligns the row."""
+    monkeypatch.setenv("REACH_LANES", lanes)
+    c = {"random": lambda: c1,
+         "skewed": lambda: synth.skewed_chain(n=20000, hub_deg=9000),
+         "dense": lambda: synth.dense_random_chain(n=2000, density=0.1, sink_frac=0.02, seed=5)}[name]()
+    cls_o, x_o = oracle_solution(c)
+    cls, x, info = gpu_solve(c, O.PROB01, method, 1e-11 if method == "mixed" else 1e-13)
+    assert np.array_equal(cls, cls_o)
+    assert info["status"] == R.REACH_OK
+    assert np.max(np.abs(x - x_o)) <= tol
+
+
 def test_autotuner_may_pick_entry_balanced_tiles():
     """On a chain with a few very long rows the entry-balanced tiles are a candidate of the
     autotuner for the FP32 sweep and the FP64 sweep; whatever it picks solves correctly."""
@@ -342,7 +359,7 @@ def test_autotuner_may_pick_entry_balanced_tiles():
         xj, ij = s.solve("jacobi", eps=1e-12, max_iter=1_000_000)
         xm, im = s.solve("mixed", eps=1e-11, max_iter=1_000_000)
         xb, ib = s.solve("bicgstab", eps=1e-12, max_iter=10_000)
-    assert all(p in (1, 2, 4, 8, 16, 32, 64, 66, 128) for p in picks.values())
+    assert all(p in (1, 2, 4, 8, 16, 32, 48, 64, 66, 128) for p in picks.values())
     assert ij["status"] == R.REACH_OK and im["status"] == R.REACH_OK and ib["status"] == R.REACH_OK
     assert np.max(np.abs(xj - xm)) <= TOL_MIXED and np.max(np.abs(xj - xb)) <= 1e-9
 
