@@ -382,6 +382,8 @@ def run_workload(args):
 
     random4096: 4096 states, 16 successors, 2% goals, 2% sinks, solved to max|dx| < 1e-10.
     layered: 2000 x 4000 layered model-checker-like chain (8M states).
+    table1: random chains with the state and transition counts of the paper's Table 1,
+            GPU time-to-solution next to the oracle's on one host core.
     batched: independent chains with 8 goal sets each (`--chains`, default 64; 256 is the
              full batch), 2% sinks, FP32 + FP64 refinement to 1e-6.
     parametric: 4M-state softmax chain, forward solve plus the adjoint gradient in theta.
@@ -415,6 +417,29 @@ def run_workload(args):
             _timed_solves(R, torch, c.n, d_in, R.REACH_PROB01, eps, list(eps), stream)
         res, total = _timed_solves(R, torch, c.n, d_in, R.REACH_PROB01, eps, list(eps), stream)
         line.update({"n": c.n, "nnz": c.m, "eps": eps, "methods": res, "step_ms": total})
+    elif args.workload == "table1":
+        # the chain sizes of the paper's Table 1 (random quicksort and biased die state
+        # spaces) as random chains: time-to-solution on the GPU (precompute + solve, device
+        # time, inside one context) next to the oracle's on one host core (partition,
+        # extraction and its solve), each to max|dx| < 1e-10.  Launch-latency bound.
+        import oracle as O
+        eps = {"jacobi": 1e-10, "mixed": 1e-10, "bicgstab": 1e-10}
+        shapes = []
+        for fam, sizes in (("quicksort", synth.TABLE1_QUICKSORT), ("biased_die", synth.TABLE1_BIASED_DIE)):
+            for (n_, m_) in sizes:
+                c = synth.table1_chain(n_, m_)
+                d_in = dev(c.rowptr, c.col, c.val, c.goal)
+                _timed_solves(R, torch, c.n, d_in, R.REACH_PROB01, eps, list(eps), stream)
+                res, total = _timed_solves(R, torch, c.n, d_in, R.REACH_PROB01, eps, list(eps), stream)
+                row = {"family": fam, "n": n_, "m": m_, "precompute_ms": res["jacobi"]["precompute_ms"]}
+                for meth, r_ in res.items():
+                    row[meth] = {"ms": r_["ms"], "iters": r_["iters"]}
+                for meth in ("jacobi", "bicgstab"):
+                    t0 = time.perf_counter()
+                    _, _, oi = O.reach_probabilities(c.n, c.rowptr, c.col, c.val, c.goal, method=meth, eps=1e-10)
+                    row["oracle_" + meth] = {"ms": (time.perf_counter() - t0) * 1e3, "iters": oi["iters"]}
+                shapes.append(row)
+        line.update({"shapes": shapes, "oracle_cores": 1})
     elif args.workload == "batched":
         bt = synth.batched_chains(n_chains=args.chains, sink_frac=0.02)
         n, rowptr, col, val, goals, offs = bt.concat()
@@ -516,7 +541,7 @@ def main():
                     help="run a short fixed-length solve for ncu and exit")
     ap.add_argument("--profile-iters", type=int, default=32)
     ap.add_argument("--workload", choices=["dense", "random4096", "layered", "layered_dag", "cascade", "skewed",
-                                           "batched", "parametric"],
+                                           "table1", "batched", "parametric"],
                     default="dense", help="dense = the benchmark; the others print their own line")
     ap.add_argument("--chains", type=int, default=64, help="--workload batched: number of chains")
     ap.add_argument("--global-stop", action="store_true",
