@@ -489,19 +489,28 @@ def run_workload(args):
         from paper_1210_6412_gb300.autograd import reach_prob
         pc = synth.parametric_chain()
         args_d = dev(pc.rowptr, pc.col, pc.cls, pc.offset, pc.goal)
-        for rep in range(max(1, args.warmup) + 1):
-            theta = torch.from_numpy(pc.theta).cuda().requires_grad_(True)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            y = reach_prob(theta, *args_d, pc.init, eps=1e-13)
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            y.backward()
-            torch.cuda.synchronize()
-            t2 = time.perf_counter()
-        line.update({"n": pc.n, "nnz": pc.m, "classes": int(pc.theta.size), "x_init": float(y),
-                     "forward_ms": (t1 - t0) * 1e3, "backward_ms": (t2 - t1) * 1e3,
-                     "grad_norm": float(theta.grad.norm())})
+        # forward and adjoint by FP64 Jacobi (the defaults), then both by BiCGStab
+        per_method = {}
+        for meth in ("jacobi", "bicgstab"):
+            for rep in range(max(1, args.warmup) + 1):
+                theta = torch.from_numpy(pc.theta).cuda().requires_grad_(True)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                y = reach_prob(theta, *args_d, pc.init, eps=1e-13, method=meth, adj_method=meth)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                y.backward()
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+            per_method[meth] = {"x_init": float(y), "forward_ms": (t1 - t0) * 1e3,
+                                "backward_ms": (t2 - t1) * 1e3, "grad": theta.grad.detach().clone()}
+        gj, gb = per_method["jacobi"].pop("grad"), per_method["bicgstab"].pop("grad")
+        line.update({"n": pc.n, "nnz": pc.m, "classes": int(pc.theta.size),
+                     "x_init": per_method["jacobi"]["x_init"],
+                     "forward_ms": per_method["jacobi"]["forward_ms"],
+                     "backward_ms": per_method["jacobi"]["backward_ms"],
+                     "grad_norm": float(gj.norm()), "bicgstab": per_method["bicgstab"],
+                     "max_grad_diff_bicgstab_vs_jacobi": float((gj - gb).abs().max())})
     print(json.dumps(line), flush=True)
     return 0
 

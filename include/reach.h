@@ -202,6 +202,12 @@ reach_status reach_time_kernel(reach_ctx* ctx, int32_t kernel, int32_t launches,
 reach_status reach_grad(reach_ctx* ctx, int64_t init, double eps, int64_t max_iter,
                         double* grad, int32_t flags, reach_info* info);
 
+/* reach_grad with the adjoint system solved by `method`: REACH_JACOBI_FP64 (what reach_grad
+ * does) or REACH_BICGSTAB_FP64 -- BiCGStab of §3.2 on (I - A)^T, with the stopping rule of
+ * the forward BiCGStab.  Any other method: REACH_EINVAL.  Arguments as in reach_grad. */
+reach_status reach_grad_method(reach_ctx* ctx, int32_t method, int64_t init, double eps, int64_t max_iter,
+                               double* grad, int32_t flags, reach_info* info);
+
 /* Parametric chains: P_e = softmax over the out-edges of each row of
  * theta[cls_e] + offset_e.  All pointers are device memory; rows must be non-empty;
  * cls_e in [0, n_classes).  p_out: float64[m].  Runs on `stream`, no sync. */

@@ -24,6 +24,7 @@ __all__ = [
     "REACH_PROB0_ONLY", "REACH_JACOBI_FP64", "REACH_JACOBI_MIXED", "REACH_BICGSTAB_FP64",
     "REACH_JACOBI_SEG", "REACH_SCC_JACOBI", "reach_scc",
     "reach_create", "reach_precompute", "reach_get_classes", "reach_solve", "reach_grad",
+    "reach_grad_method",
     "reach_param_probs", "reach_param_grad_theta", "reach_last_error", "reach_destroy",
     "reach_version", "Solver", "reach_batch_create", "reach_batch_precompute",
     "reach_batch_get_classes", "reach_batch_solve", "reach_batch_destroy", "BatchSolver",
@@ -81,6 +82,7 @@ _SIGS = {
     "reach_get_classes": (_I32, [_P, _P, _I32]),
     "reach_solve": (_I32, [_P, _I32, _D, _I64, _I32, _P, _P, _I32, C.POINTER(ReachInfo)]),
     "reach_grad": (_I32, [_P, _I64, _D, _I64, _P, _I32, C.POINTER(ReachInfo)]),
+    "reach_grad_method": (_I32, [_P, _I32, _I64, _D, _I64, _P, _I32, C.POINTER(ReachInfo)]),
     "reach_param_probs": (_I32, [_I64, _I64, _P, _P, _P, _P, _I32, _P, _P]),
     "reach_param_grad_theta": (_I32, [_I64, _I64, _P, _P, _P, _P, _I32, _P, _P]),
     "reach_last_error": (C.c_char_p, [_P]),
@@ -238,13 +240,15 @@ def reach_solve(ctx, n, method=REACH_JACOBI_FP64, eps=1e-10, max_iter=1_000_000,
     return out, info.as_dict()
 
 
-def reach_grad(ctx, m, init, eps=1e-13, max_iter=1_000_000, out=None, check=True):
-    """d x_init / d P for every stored entry (input order) and the adjoint info."""
+def reach_grad(ctx, m, init, eps=1e-13, max_iter=1_000_000, out=None, check=True, method="jacobi"):
+    """d x_init / d P for every stored entry (input order) and the adjoint info; the adjoint
+    system is solved by `method` ("jacobi" or "bicgstab")."""
     if out is None:
         out = np.empty(m, np.float64)
     op, f, keep = _arg(out, np.float64, m, "grad")
     info = ReachInfo()
-    st = lib().reach_grad(ctx, int(init), float(eps), int(max_iter), op, f, C.byref(info))
+    meth = METHODS.get(method, method) if isinstance(method, str) else int(method)
+    st = lib().reach_grad_method(ctx, meth, int(init), float(eps), int(max_iter), op, f, C.byref(info))
     if check and st != REACH_OK:
         raise ReachError(st, reach_last_error(ctx))
     return out, info.as_dict()
@@ -357,8 +361,8 @@ class Solver:
               check=True):
         return reach_solve(self.ctx, self.n, method, eps, max_iter, refine_k, x0, out, check)
 
-    def grad(self, init, eps=1e-13, max_iter=1_000_000, out=None, check=True):
-        return reach_grad(self.ctx, self.m, init, eps, max_iter, out, check)
+    def grad(self, init, eps=1e-13, max_iter=1_000_000, out=None, check=True, method="jacobi"):
+        return reach_grad(self.ctx, self.m, init, eps, max_iter, out, check, method)
 
     def autotune(self, method="jacobi"):
         return reach_autotune(self.ctx, method)

@@ -109,7 +109,7 @@ void dfree(T*& p) {
 void free_system(reach_ctx* c) {
   dfree(c->a_rowptr); dfree(c->a_col); dfree(c->a_val); dfree(c->a_hi); dfree(c->a_lo); dfree(c->a_col16);
   dfree(c->d); dfree(c->b); dfree(c->a_jv); dfree(c->bj); dfree(c->qstate);
-  dfree(c->at_rowptr); dfree(c->at_col); dfree(c->at_val); dfree(c->at_jv);
+  dfree(c->at_rowptr); dfree(c->at_col); dfree(c->at_val); dfree(c->at_jv); dfree(c->at_b);
   dfree(c->x); dfree(c->x2); dfree(c->vr); dfree(c->vq); dfree(c->vp); dfree(c->vv);
   dfree(c->vs); dfree(c->vt); dfree(c->r32); dfree(c->xf); dfree(c->dl[0]); dfree(c->dl[1]);
   seg_free(c);
@@ -117,7 +117,7 @@ void free_system(reach_ctx* c) {
 }
 
 void drop_graphs(reach_ctx* c) {
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < 10; ++i) {
     if (c->g_exec[i]) cudaGraphExecDestroy(c->g_exec[i]);
     c->g_exec[i] = nullptr;
     c->g_key[i] = -1;
@@ -535,7 +535,14 @@ reach_status reach_time_kernel(reach_ctx* c, int32_t kernel, int32_t launches, d
 
 reach_status reach_grad(reach_ctx* c, int64_t init, double eps, int64_t max_iter, double* grad,
                         int32_t flags, reach_info* info) {
+  return reach_grad_method(c, REACH_JACOBI_FP64, init, eps, max_iter, grad, flags, info);
+}
+
+reach_status reach_grad_method(reach_ctx* c, int32_t method, int64_t init, double eps, int64_t max_iter,
+                               double* grad, int32_t flags, reach_info* info) {
   if (!c) return fail(nullptr, REACH_EINVAL, "reach_grad: NULL context");
+  if (method != REACH_JACOBI_FP64 && method != REACH_BICGSTAB_FP64)
+    return fail(c, REACH_EINVAL, "reach_grad: the adjoint method must be JACOBI_FP64 or BICGSTAB_FP64");
   if (c->general) return fail(c, REACH_ESTATE, "reach_grad: defined for chains only");
   if (!c->have_x) return fail(c, REACH_ESTATE, "reach_grad: needs a successful reach_solve first");
   if (init < 0 || init >= c->n) return fail(c, REACH_EINVAL, "reach_grad: init outside [0, n)");
@@ -563,20 +570,23 @@ reach_status reach_grad(reach_ctx* c, int64_t init, double eps, int64_t max_iter
   } else if (e == cudaSuccess) {
     e = build_transposed_system(c);
     const int k = c->tune.k;
+    const bool bi = method == REACH_BICGSTAB_FP64;
     if (e == cudaSuccess) {
-      reach_status rs = start_state(c, eps, max_iter, max_iter / k + 4);
+      reach_status rs = start_state(c, eps, max_iter, bi ? max_iter + 4 : max_iter / k + 4);
       if (rs != REACH_OK) {
         if (flags == REACH_HOST) cudaFree(gdev);
         return rs;
       }
     }
+    // right-hand side e_init: vp for the Jacobi sweeps, at_b for BiCGStab (whose p is vp)
+    double* rhs = bi ? c->at_b : c->vp;
     const double one = 1.0;
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->vp, 0, sizeof(double) * c->n_q, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->vp + row, &one, sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(rhs, 0, sizeof(double) * c->n_q, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rhs + row, &one, sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev0, s);
-    if (e == cudaSuccess) e = solve_jacobi64(c, nullptr, true);
-    if (e == cudaSuccess) e = grad_entries(c, c->vr, gdev);
+    if (e == cudaSuccess) e = bi ? solve_bicgstab_transposed(c) : solve_jacobi64(c, nullptr, true);
+    if (e == cudaSuccess) e = grad_entries(c, bi ? c->x2 : c->vr, gdev);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev1, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, c->st, sizeof(hs), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -751,6 +751,7 @@ cudaError_t extract_rows(reach_ctx* c) {
   if (c->at_rowptr) { cudaFree(c->at_rowptr); c->at_rowptr = nullptr; }
   if (c->at_col) { cudaFree(c->at_col); c->at_col = nullptr; }
   if (c->at_val) { cudaFree(c->at_val); c->at_val = nullptr; }
+  if (c->at_b) { cudaFree(c->at_b); c->at_b = nullptr; }
   return cudaGetLastError();
 }
 
@@ -852,6 +853,7 @@ cudaError_t build_transposed_system(reach_ctx* c) {
   if ((e = dmalloc(&c->at_rowptr, nq + 1)) != cudaSuccess) return e;
   if ((e = dmalloc(&c->at_col, mq + 8)) != cudaSuccess) return e;
   if ((e = dmalloc(&c->at_val, mq + 8)) != cudaSuccess) return e;
+  if ((e = dmalloc(&c->at_b, nq + 1)) != cudaSuccess) return e;
   cudaMemsetAsync(c->at_col + mq, 0, 8 * sizeof(int32_t), s);
   cudaMemsetAsync(c->at_val + mq, 0, 8 * sizeof(double), s);
   uint32_t* cnt = reinterpret_cast<uint32_t*>(c->queue);

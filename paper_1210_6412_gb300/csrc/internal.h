@@ -120,6 +120,7 @@ struct reach_ctx {
   int32_t* at_col = nullptr;
   double* at_val = nullptr;
   double* at_jv = nullptr;     // its Jacobi form: A_ij / d_j in row j of the transpose
+  double* at_b = nullptr;      // right-hand side of an adjoint BiCGStab solve (e_init)
 
   // solve workspace (n_q each)
   double* x = nullptr;
@@ -149,8 +150,9 @@ struct reach_ctx {
 
   // cached solve graphs, keyed by method and shape
   // 0-3 solvers, 4 entry-balanced Jacobi, 5-6 SCC decomposition, 7 level-by-level Jacobi
-  cudaGraphExec_t g_exec[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  int64_t g_key[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  cudaGraphExec_t g_exec[10] = {nullptr, nullptr, nullptr, nullptr, nullptr,
+                                 nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t g_key[10] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
 
   void* seg = nullptr;      // tile plan of the entry-balanced Jacobi sweep (segscan.cu)
   void* scc = nullptr;      // components, levels and row order (scc.cu)
@@ -174,6 +176,7 @@ cudaError_t build_transposed_system(reach_ctx* c);
 cudaError_t solve_jacobi64(reach_ctx* c, const double* x0q, bool transposed);
 cudaError_t solve_mixed(reach_ctx* c, const double* x0q);
 cudaError_t solve_bicgstab(reach_ctx* c, const double* x0q);
+cudaError_t solve_bicgstab_transposed(reach_ctx* c);
 cudaError_t residual_inf(reach_ctx* c, const double* xq, double* out_host);
 cudaError_t scatter_full(reach_ctx* c, const double* xq, double* full);
 cudaError_t gather_q(reach_ctx* c, const double* full, double* xq);

@@ -914,27 +914,29 @@ static void l_sweep32(reach_ctx* c, const float* din, float* dout, cudaStream_t 
   l_sweep32_u<G, V, 2>(c, din, dout, s, cr);
 }
 
+// BiCGStab launchers on a system y (rows, values with diagonal c->d, right-hand side y.b):
+// the chain's system, or its transpose for the adjoint solve.
 template <int G, bool V>
-static void l_bi_init(reach_ctx* c, cudaStream_t s) {
-  const int grid = grid_rows(c, (const void*)k_bi_init<G, V>, NT, G, c->n_q);
-  k_bi_init<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_val, c->b, c->d, c->x, c->vr,
-                                      c->vq, c->vp, c->vv, c->part, c->ticket, c->bi, c->st);
+static void l_bi_init(reach_ctx* c, const Sys& y, const double* x, cudaStream_t s) {
+  const int grid = grid_rows(c, (const void*)k_bi_init<G, V>, NT, G, y.nq);
+  k_bi_init<G, V><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, c->d, x, c->vr, c->vq, c->vp, c->vv, c->part,
+                                      c->ticket, c->bi, c->st);
 }
 
 template <int G, bool V>
-static void l_bi_v(reach_ctx* c, cudaStream_t s) {
+static void l_bi_v(reach_ctx* c, const Sys& y, cudaStream_t s) {
   unsigned* cr = G == 32 ? &c->st->rowctr[0] : nullptr;
-  const int grid = grid_rows(c, (const void*)k_bi_v<G, V>, NT, G, c->n_q, cr != nullptr);
-  k_bi_v<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_val, c->d, c->vp, c->vq, c->vv,
-                                   c->part, c->ticket, c->bi, c->st, cr);
+  const int grid = grid_rows(c, (const void*)k_bi_v<G, V>, NT, G, y.nq, cr != nullptr);
+  k_bi_v<G, V><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, c->d, c->vp, c->vq, c->vv, c->part, c->ticket, c->bi,
+                                   c->st, cr);
 }
 
 template <int G, bool V>
-static void l_bi_t(reach_ctx* c, cudaStream_t s) {
+static void l_bi_t(reach_ctx* c, const Sys& y, cudaStream_t s) {
   unsigned* cr = G == 32 ? &c->st->rowctr[1] : nullptr;
-  const int grid = grid_rows(c, (const void*)k_bi_t<G, V>, NT, G, c->n_q, cr != nullptr);
-  k_bi_t<G, V><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_val, c->d, c->vs,
-                                   c->vt, c->part, c->ticket, c->bi, c->st, cr);
+  const int grid = grid_rows(c, (const void*)k_bi_t<G, V>, NT, G, y.nq, cr != nullptr);
+  k_bi_t<G, V><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, c->d, c->vs, c->vt, c->part, c->ticket, c->bi, c->st,
+                                   cr);
 }
 
 static int ew_grid(reach_ctx* c, const void* k, int64_t n) { return grid_for(c, k, NT, n); }
@@ -1071,26 +1073,25 @@ cudaError_t residual_report(reach_ctx* c, const double* xq) {
   return cudaGetLastError();
 }
 
-cudaError_t solve_bicgstab(reach_ctx* c, const double* x0q) {
+// BiCGStab iterations on the system y from x (x holds the start), the loop graph cached
+// in slot gs.  Entry-balanced products (LS.seg) serve the chain's own system only.
+static cudaError_t bicgstab_loop(reach_ctx* c, const Sys& y, double* x, const Lay& LS, const Lay& L, int gs) {
   cudaStream_t s = c->stream;
-  const int64_t nq = c->n_q;
-  if (x0q) cudaMemcpyAsync(c->x, x0q, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
-  else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
-  const Lay LS = layout(c, nq, c->m_q, REACH_BICGSTAB_FP64);
-  const Lay L = row_layout(c, REACH_BICGSTAB_FP64);
+  const int64_t nq = y.nq;
   cudaError_t e = cudaSuccess;
   if (LS.seg && (e = seg_plan(c)) != cudaSuccess) return e;
-  LAY_DISPATCH(L, l_bi_init, c, s);
+  LAY_DISPATCH(L, l_bi_init, c, y, x, s);
   // entry-balanced products write y = A u into x2 (free during BiCGStab); the M u epilogue
   // with its fused dots is then elementwise
-  e = run_loop(c, c->g_exec[2], c->g_key[2], shape_key(c, LS, 1), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
+  e = run_loop(c, c->g_exec[gs], c->g_key[gs], shape_key(c, LS, 1) * 2 + (gs == 2 ? 0 : 1),
+               [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
     k_bi_p<<<ew_grid(c, (const void*)k_bi_p, nq), NT, 0, cs>>>(nq, c->vr, c->vp, c->vv, c->vq, c->bi, c->st);
     if (LS.seg) {
       seg_spmv64(c, c->vp, c->x2, cs);
       k_bi_v_ew<<<ew_grid(c, (const void*)k_bi_v_ew, nq), NT, 0, cs>>>(nq, c->d, c->vp, c->x2, c->vq, c->vv,
                                                                        c->part, c->ticket, c->bi, c->st);
     } else {
-      LAY_DISPATCH(L, l_bi_v, c, cs);
+      LAY_DISPATCH(L, l_bi_v, c, y, cs);
     }
     k_bi_s<<<ew_grid(c, (const void*)k_bi_s, nq), NT, 0, cs>>>(nq, c->vr, c->vv, c->vs, c->bi, c->st);
     if (LS.seg) {
@@ -1098,16 +1099,37 @@ cudaError_t solve_bicgstab(reach_ctx* c, const double* x0q) {
       k_bi_t_ew<<<ew_grid(c, (const void*)k_bi_t_ew, nq), NT, 0, cs>>>(nq, c->d, c->vs, c->x2, c->vt, c->part,
                                                                        c->ticket, c->bi, c->st);
     } else {
-      LAY_DISPATCH(L, l_bi_t, c, cs);
+      LAY_DISPATCH(L, l_bi_t, c, y, cs);
     }
-    k_bi_x<<<ew_grid(c, (const void*)k_bi_x, nq), NT, 0, cs>>>(nq, c->x, c->vp, c->vs, c->vt, c->vr, c->vq,
+    k_bi_x<<<ew_grid(c, (const void*)k_bi_x, nq), NT, 0, cs>>>(nq, x, c->vp, c->vs, c->vt, c->vr, c->vq,
                                                                c->part, c->ticket, c->bi, c->st);
   });
   if (e != cudaSuccess) return e;
-  Sys y{nq, c->a_rowptr, c->a_col, c->a_val, c->b};
-  LAY_DISPATCH(L, l_resid, c, y, c->x, s);
+  LAY_DISPATCH(L, l_resid, c, y, x, s);
   k_finalize_resid<<<1, 1, 0, s>>>(c->st);
   return cudaGetLastError();
+}
+
+cudaError_t solve_bicgstab(reach_ctx* c, const double* x0q) {
+  cudaStream_t s = c->stream;
+  const int64_t nq = c->n_q;
+  if (x0q) cudaMemcpyAsync(c->x, x0q, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
+  else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
+  const Lay LS = layout(c, nq, c->m_q, REACH_BICGSTAB_FP64);
+  const Lay L = row_layout(c, REACH_BICGSTAB_FP64);
+  Sys y{nq, c->a_rowptr, c->a_col, c->a_val, c->b};
+  return bicgstab_loop(c, y, c->x, LS, L, 2);
+}
+
+// The adjoint system (I - A)^T y = e with BiCGStab (§3.2 on the transpose): row j of the
+// transpose holds A_ij, the diagonal is the same d, the right-hand side e is in c->at_b;
+// the solution goes to c->x2, from y = 0.
+cudaError_t solve_bicgstab_transposed(reach_ctx* c) {
+  const int64_t nq = c->n_q;
+  cudaMemsetAsync(c->x2, 0, sizeof(double) * nq, c->stream);
+  const Lay L = row_layout(c, -1);
+  Sys y{nq, c->at_rowptr, c->at_col, c->at_val, c->at_b};
+  return bicgstab_loop(c, y, c->x2, L, L, 8);
 }
 
 void launch_check_mixed(cudaStream_t s, SolveState* st, int slot, int k) {
@@ -1324,6 +1346,7 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
   const Lay L = layout(c, c->n_q, c->m_q, method);
   if (L.seg && (e = seg_plan(c)) != cudaSuccess) return e;
   Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_jv, c->bj};   // Jacobi form (the FP64 sweep)
+  Sys ya{c->n_q, c->a_rowptr, c->a_col, c->a_val, c->b};  // the system itself (BiCGStab)
   SolveState hs;
   std::memset(&hs, 0, sizeof(hs));
   hs.eps = 1e-300;
@@ -1352,7 +1375,7 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
     else if (kernel == 0) LAY_DISPATCH(L, l_jacobi, c, y, c->x, c->x2, &c->st->slot[0], s, ctr);
     else if (kernel == 1) LAY_DISPATCH(L, l_sweep32, c, c->dl[0], c->dl[1], s, ctr);
     else if (kernel == 2) LAY_DISPATCH(L, l_resid_hilo, c, 0, s, ctr);
-    else LAY_DISPATCH(L, l_bi_v, c, s);
+    else LAY_DISPATCH(L, l_bi_v, c, ya, s);
   };
   one(0);  // warm-up
   e = cudaEventRecord(c->ev0, s);

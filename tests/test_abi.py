@@ -53,6 +53,7 @@ def test_argument_checks_need_no_device(so):
     assert so.reach_precompute(None, 0) == R.REACH_EINVAL
     assert so.reach_solve(None, 0, 1e-9, 10, 0, None, None, 0, None) == R.REACH_EINVAL
     assert so.reach_grad(None, 0, 1e-9, 10, None, 0, None) == R.REACH_EINVAL
+    assert so.reach_grad_method(None, R.REACH_BICGSTAB_FP64, 0, 1e-9, 10, None, 0, None) == R.REACH_EINVAL
     assert so.reach_get_classes(None, None, 0) == R.REACH_EINVAL
     so.reach_destroy(None)
     assert ctx.value is None
