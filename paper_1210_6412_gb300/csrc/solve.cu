@@ -308,9 +308,11 @@ RDEV bool last_cta_reduce(double (&mine)[NS + NM], double* part, unsigned* ticke
 
 // ------------------------------------------------------------------ Jacobi FP64 (§3.1)
 // x'_i = (b_i + sum_{j != i} A_ij x_j) / d_i with d_i = 1 - A_ii: the paper's row
-// update for M = I - A, double buffered; max|x' - x| is reduced into slot.
+// update for M = I - A, double buffered; max|x' - x| is reduced into slot.  DELTA: only the
+// sweep whose max|x' - x| the stopping test reads computes it (the last of each group of
+// sweeps between checks); the others skip the FP64 difference and the reduction.
 
-template <int G, bool V>
+template <int G, bool V, bool DELTA = true>
 __global__ void __launch_bounds__(NT) k_jacobi64(int64_t nq, const int64_t* __restrict__ rp,
                                                  const int32_t* __restrict__ ci,
                                                  const double* __restrict__ aj,
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(NT) k_jacobi64(int64_t nq, const int64_t* __re
     // would only hold the registers)
     if (!V && i < nq && rg.lane == 0) {
       bv = bj[i];
-      xo = x[i];
+      if (DELTA) xo = x[i];
     }
     // short rows: the sum starts at bj_i in lane 0 (bv = 0 elsewhere), which saves the
     // separate FP64 add on a pipe that bounds these sweeps
@@ -335,15 +337,15 @@ __global__ void __launch_bounds__(NT) k_jacobi64(int64_t nq, const int64_t* __re
     if (i < nq && rg.lane == 0) {
       if (V) {
         bv = bj[i];
-        xo = x[i];
+        if (DELTA) xo = x[i];
       }
       // (b_i + sum A_ij x_j) / d_i in the Jacobi form
       const double xv = V ? bv + s : s;
-      mx = umax64(mx, abs_bits(xv - xo));
+      if (DELTA) mx = umax64(mx, abs_bits(xv - xo));
       xn[i] = xv;
     }
   }
-  cta_to_slot<1, true>(bits_to_delta(mx), slot);
+  if (DELTA) cta_to_slot<1, true>(bits_to_delta(mx), slot);
 }
 
 // FP64 residual r = b - (I - A) x, max|r| into slot (reported as resid_inf).
@@ -867,6 +869,14 @@ static void l_jacobi(reach_ctx* c, const Sys& y, const double* x, double* xn, un
   k_jacobi64<G, V><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, x, xn, slot, G == 32 ? ctr : nullptr);
 }
 
+// A sweep whose max|x' - x| nobody reads.
+template <int G, bool V>
+static void l_jacobi_nd(reach_ctx* c, const Sys& y, const double* x, double* xn, unsigned long long* slot,
+                        cudaStream_t s, unsigned* ctr = nullptr) {
+  const int grid = grid_rows(c, (const void*)k_jacobi64<G, V, false>, NT, G, y.nq, G == 32 && ctr);
+  k_jacobi64<G, V, false><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, x, xn, slot, G == 32 ? ctr : nullptr);
+}
+
 template <int G, bool V>
 static void l_resid(reach_ctx* c, const Sys& y, const double* x, cudaStream_t s) {
   const int grid = grid_rows(c, (const void*)k_resid64<G, V>, NT, G, y.nq);
@@ -1021,7 +1031,11 @@ cudaError_t solve_jacobi64(reach_ctx* c, const double* x0q, bool transposed) {
                              for (int j = 0; j < k; ++j) {
                                const double* xi = (j & 1) ? xb : xa;
                                double* xo = (j & 1) ? xa : xb;
-                               LAY_DISPATCH(L, l_jacobi, c, y, xi, xo, &c->st->slot[j], cs, &c->st->rowctr[j]);
+                               // the check reads the last sweep's max|x' - x| only
+                               if (j == k - 1)
+                                 LAY_DISPATCH(L, l_jacobi, c, y, xi, xo, &c->st->slot[j], cs, &c->st->rowctr[j]);
+                               else
+                                 LAY_DISPATCH(L, l_jacobi_nd, c, y, xi, xo, &c->st->slot[j], cs, &c->st->rowctr[j]);
                              }
                              k_check<<<1, 1, 0, cs>>>(c->st, k - 1, k, k);
                            });
