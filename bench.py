@@ -235,6 +235,8 @@ def run_ours(args):
     h_outs = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in EPS}
     stream = torch.cuda.current_stream(dev)
 
+    lanes = {}
+
     def step(inputs, outputs):
         infos = {}
         ctx = R.reach_create(n, *inputs, stream=stream.cuda_stream)
@@ -242,7 +244,7 @@ def run_ours(args):
             R.reach_precompute(ctx, R.REACH_PROB0_ONLY)
             for meth in ("jacobi", "mixed", "bicgstab"):
                 # row mapping from the autotuner (measured once per system shape, then cached)
-                R.reach_autotune(ctx, meth)
+                lanes[meth] = R.reach_autotune(ctx, meth)["lanes"]
                 _, infos[meth] = R.reach_solve(ctx, n, meth, eps=EPS[meth], max_iter=200_000,
                                                refine_k=K_REFINE, out=outputs[meth])
         finally:
@@ -300,7 +302,7 @@ def run_ours(args):
     for k, inf in infos.items():
         methods[k] = {"ms": inf["ms_solve"], "iters": inf["iters"], "max_err": errs[k],
                       "resid_inf": inf["resid_inf"], "alg_GBps": inf["bytes_moved"] / (inf["ms_solve"] * 1e6),
-                      "refinements": inf["refinements"]}
+                      "refinements": inf["refinements"], "lanes": lanes.get(k)}
     fp64_tf = 2.0 * mq / (sweep_ms * 1e-3) / 1e12
     hbm_gbs = alg_bytes / (sweep_ms * 1e-3) / 1e9
     line = {

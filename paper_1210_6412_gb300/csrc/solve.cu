@@ -886,7 +886,7 @@ static void l_resid(reach_ctx* c, const Sys& y, const double* x, cudaStream_t s)
 template <int G, bool V>
 static void l_resid_hilo(reach_ctx* c, int slot, cudaStream_t s, unsigned* ctr = nullptr) {
   unsigned* cr = G == 32 ? ctr : nullptr;
-  if (V && c->a_col16) {
+  if (c->a_col16) {   // 16-bit column indices whenever every column fits
     const int grid = grid_rows(c, (const void*)k_resid_hilo<G, V, uint16_t>, NT, G, c->n_q, cr != nullptr);
     k_resid_hilo<G, V, uint16_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col16, c->a_hi, c->a_lo, c->bj,
                                                      c->x, c->xf, c->r32, c->dl[1], c->st, slot, cr);
@@ -899,7 +899,7 @@ static void l_resid_hilo(reach_ctx* c, int slot, cudaStream_t s, unsigned* ctr =
 
 template <int G, bool V, int U>
 static void l_sweep32_u(reach_ctx* c, const float* din, float* dout, cudaStream_t s, unsigned* cr) {
-  if (V && c->a_col16) {
+  if (c->a_col16) {   // 16-bit column indices whenever every column fits
     const int grid = grid_rows(c, (const void*)k_sweep32<G, V, uint16_t, U>, NT, G, c->n_q, cr != nullptr);
     k_sweep32<G, V, uint16_t, U><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col16, c->a_hi, c->r32,
                                                      din, dout, c->st, cr);
