@@ -242,7 +242,7 @@ reach_status reach_batch_precompute(reach_batch* b, int32_t mode);
 reach_status reach_batch_get_classes(reach_batch* b, uint8_t* cls, int32_t flags);
 
 /* Jacobi on every right-hand side at once, as FP32 sweeps with an FP64 residual and
- * correction every refine_k sweeps (even, in [2, 62]; 0 = 16):
+ * correction every refine_k sweeps (even, in [2, 62]; 0 = 32):
  * x_j[s] <- sum_{s' != s} P(s,s') x_j[s'] / (1 - P(s,s)) on S?_j, with x_j = 1 on
  * S=1_j and 0 on S=0_j.  Stops when the largest FP64 Jacobi step over all S?_j is
  * below eps -- per chain once reach_batch_set_chains has named the chains; info->iters
