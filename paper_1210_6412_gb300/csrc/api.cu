@@ -151,7 +151,7 @@ void reach_destroy(reach_ctx* c) {
   dfree(c->t_rowptr); dfree(c->t_col);
   dfree(c->cls); dfree(c->qidx); dfree(c->vis); dfree(c->queue); dfree(c->bfs);
   dfree(c->xfull); dfree(c->st); dfree(c->bi); dfree(c->part); dfree(c->ticket);
-  dfree(c->verr); dfree(c->vrow);
+  dfree(c->verr); dfree(c->vrow); dfree(c->maxrow);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->cap) cudaStreamDestroy(c->cap);
@@ -207,7 +207,8 @@ static reach_status create_common(reach_ctx** out, int64_t n, int64_t m, const i
       (e = dalloc(&c->bfs, 1)) != cudaSuccess || (e = dalloc(&c->xfull, n)) != cudaSuccess ||
       (e = dalloc(&c->st, 1)) != cudaSuccess || (e = dalloc(&c->bi, 1)) != cudaSuccess ||
       (e = dalloc(&c->part, part_n)) != cudaSuccess || (e = dalloc(&c->ticket, 1)) != cudaSuccess ||
-      (e = dalloc(&c->verr, 1)) != cudaSuccess || (e = dalloc(&c->vrow, 1)) != cudaSuccess) {
+      (e = dalloc(&c->verr, 1)) != cudaSuccess || (e = dalloc(&c->vrow, 1)) != cudaSuccess ||
+      (e = dalloc(&c->maxrow, 1)) != cudaSuccess) {
     reach_status s = cuda_fail(nullptr, e, (w + ": allocation").c_str());
     reach_destroy(c);
     return s;

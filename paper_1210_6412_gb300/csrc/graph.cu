@@ -146,11 +146,41 @@ __global__ void k_validate(int64_t n, int64_t m, const int64_t* __restrict__ rp,
   }
 }
 
+// Longest row of P (rows of a bad rowptr count as 0; validation reports those).
+__global__ void k_max_row(int64_t n, const int64_t* __restrict__ rp, unsigned long long* out) {
+  unsigned long long mx = 0ull;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t len = rp[s + 1] - rp[s];
+    if (len > 0 && (unsigned long long)len > mx) mx = (unsigned long long)len;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(FULL, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
+// Rows this long, or longer, make the row-wise graph kernels take a warp per row: with
+// fewer lanes a few very long rows (hubs) would serialise on a handful of them.
+constexpr int64_t LONG_ROW = 4096;
+
+int graph_group(reach_ctx* c, int64_t rows, int64_t nnz) {
+  return c->max_row >= LONG_ROW ? 32 : pick_group(rows, nnz);
+}
+
 cudaError_t launch_validate(reach_ctx* c) {
   const int64_t mean = c->n ? c->m / c->n : 0;
   cudaMemsetAsync(c->verr, 0, sizeof(unsigned), c->stream);
   cudaMemsetAsync(c->vrow, 0x7f, sizeof(int64_t), c->stream);
-  if (mean >= 16) {
+  cudaMemsetAsync(c->maxrow, 0, sizeof(unsigned long long), c->stream);
+  k_max_row<<<grid_for(c, (const void*)k_max_row, 256, c->n), 256, 0, c->stream>>>(c->n, c->rowptr, c->maxrow);
+  unsigned long long mr = 0ull;
+  cudaError_t e = cudaMemcpyAsync(&mr, c->maxrow, sizeof(mr), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return e;
+  c->max_row = (int64_t)mr;
+  if (mean >= 16 || c->max_row >= LONG_ROW) {
     int grid = grid_for(c, (const void*)k_validate<32>, 256, c->n * 32);
     k_validate<32><<<grid, 256, 0, c->stream>>>(c->n, c->m, c->rowptr, c->col, c->val, 1e-9,
                                                 c->verr, c->vrow, c->general ? 1 : 0);
@@ -215,7 +245,7 @@ cudaError_t build_reverse_pattern(reach_ctx* c) {
   const int64_t n = c->n;
   uint32_t* cnt = reinterpret_cast<uint32_t*>(c->queue);   // n entries of scratch
   cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n, s);
-  const int g = pick_group(n, c->m);
+  const int g = graph_group(c, n, c->m);
   int64_t* bsum = reinterpret_cast<int64_t*>(c->part);
 #define REV_LAUNCH(G)                                                                         \
   {                                                                                           \
@@ -725,7 +755,7 @@ cudaError_t extract_rows(reach_ctx* c) {
   if ((e = dmalloc(&c->qstate, nq)) != cudaSuccess) return e;
   int64_t* acnt = nullptr;
   if ((e = dmalloc(&acnt, nq)) != cudaSuccess) return e;
-  const int g = pick_group(n, c->m);
+  const int g = graph_group(c, n, c->m);
   if (nq > 0) extract_dispatch(c, g, acnt, 0);
   int64_t* mq_dev = reinterpret_cast<int64_t*>(c->st) + 1;
   exclusive_scan<int64_t>(acnt, c->a_rowptr, nq, mq_dev, bsum, s);
@@ -796,7 +826,7 @@ cudaError_t build_jacobi_form(reach_ctx* c) {
   if ((e = dmalloc(&c->a_jv, mq + 8)) != cudaSuccess) return e;
   if ((e = dmalloc(&c->bj, nq)) != cudaSuccess) return e;
   cudaMemsetAsync(c->a_jv + mq, 0, 8 * sizeof(double), c->stream);
-  if (nq > 0) jform_dispatch(c, pick_group(nq, mq), nq, c->a_rowptr, c->a_val, c->b, c->a_jv, c->bj);
+  if (nq > 0) jform_dispatch(c, graph_group(c, nq, mq), nq, c->a_rowptr, c->a_val, c->b, c->a_jv, c->bj);
   return cudaGetLastError();
 }
 

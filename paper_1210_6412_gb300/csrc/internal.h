@@ -143,6 +143,8 @@ struct reach_ctx {
   unsigned* ticket = nullptr;
   unsigned* verr = nullptr;
   int64_t* vrow = nullptr;
+  unsigned long long* maxrow = nullptr;  // longest row of P (device, written by validation)
+  int64_t max_row = 0;                   // its host copy
 
   reach::Tuning tune;
   bool device_loops = true;   // conditional-while graphs (false: host-driven loops)
