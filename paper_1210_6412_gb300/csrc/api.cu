@@ -180,11 +180,12 @@ static reach_status create_common(reach_ctx** out, int64_t n, int64_t m, const i
   c->device_loops = !(hl && hl[0] == '1');
   // REACH_LANES fixes the row mapping of every solver kernel that has none autotuned:
   // 1, 2, 4, 8, 16 or 32 lanes per row, 48 = half a warp with vector loads, 64 = a warp with
-  // vector loads, 80 = the FP32 sweep with rows staged by bulk copies (other kernels as 64),
-  // 128 = entry-balanced tiles
+  // vector loads, 72 = the FP32 sweep with its vector in shared memory and 80 = the FP32 sweep
+  // with rows staged by bulk copies (other kernels as 64), 128 = entry-balanced tiles
   if (const char* ln = std::getenv("REACH_LANES")) {
     const int v = std::atoi(ln);
-    if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32 || v == 48 || v == 64 || v == 80 || v == 128)
+    if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32 || v == 48 || v == 64 || v == 72 || v == 80 ||
+        v == 128)
       c->tune.g = v;
   }
   cudaError_t e = cudaGetDevice(&c->device);

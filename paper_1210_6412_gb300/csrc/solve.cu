@@ -83,16 +83,18 @@ RDEV double dot64(int64_t lo, int64_t hi, int lane, const int32_t* __restrict__ 
   return s;
 }
 
-// FP32 values, FP32 accumulation (inner sweeps of the mixed method).
-template <int G, bool V, typename IT = int32_t, int U = 2>
+// FP32 values, FP32 accumulation (inner sweeps of the mixed method).  XS: x lives in
+// shared memory (plain loads) instead of global memory (read-only path).
+template <int G, bool V, typename IT = int32_t, int U = 2, bool XS = false>
 RDEV float dot32(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
                  const float* __restrict__ av, const float* __restrict__ x) {
+  auto gx = [x](int j) { return XS ? x[j] : __ldg(x + j); };
   float s = 0.0f;
   if constexpr (V) {
     int64_t a = (lo + 3) & ~int64_t(3);
     if (a > hi) a = hi;
     const int64_t e = a + ((hi - a) & ~int64_t(3));
-    if (lo + lane < a) s = fmaf(__ldcs(av + lo + lane), __ldg(x + ld_idx(ci + lo + lane)), s);
+    if (lo + lane < a) s = fmaf(__ldcs(av + lo + lane), gx(ld_idx(ci + lo + lane)), s);
     // U quads per lane per trip, software-pipelined: the next trip's index and value
     // loads are issued before this trip's gathers, so HBM loads stay in flight while
     // the gathers of x (L1 / L2) complete.  Quads past the row end load as zeros.
@@ -123,10 +125,10 @@ RDEV float dot32(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
       load_trip(kn, n4, w4);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        acc[u] = fmaf(v4[u].x, __ldg(x + c4[u].x), acc[u]);
-        acc[u] = fmaf(v4[u].y, __ldg(x + c4[u].y), acc[u]);
-        acc[u] = fmaf(v4[u].z, __ldg(x + c4[u].z), acc[u]);
-        acc[u] = fmaf(v4[u].w, __ldg(x + c4[u].w), acc[u]);
+        acc[u] = fmaf(v4[u].x, gx(c4[u].x), acc[u]);
+        acc[u] = fmaf(v4[u].y, gx(c4[u].y), acc[u]);
+        acc[u] = fmaf(v4[u].z, gx(c4[u].z), acc[u]);
+        acc[u] = fmaf(v4[u].w, gx(c4[u].w), acc[u]);
         c4[u] = n4[u];
         v4[u] = w4[u];
       }
@@ -134,7 +136,7 @@ RDEV float dot32(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) s += acc[u];
-    if (e + lane < hi) s = fmaf(__ldcs(av + e + lane), __ldg(x + ld_idx(ci + e + lane)), s);
+    if (e + lane < hi) s = fmaf(__ldcs(av + e + lane), gx(ld_idx(ci + e + lane)), s);
   } else {
     // four entries per lane per trip, loads first (see dot64)
     float s1 = 0.0f;
@@ -484,6 +486,50 @@ __global__ void __launch_bounds__(NT) k_sweep32(int64_t nq, const int64_t* __res
   }
 }
 
+// The FP32 sweep with the correction vector staged in shared memory (layout 72): every
+// CTA copies din (n? floats, at most SMX_MAX_ROWS) into shared memory once per launch, and
+// a row's gathers then read shared memory instead of L1, whose tag lookups for 32 scattered
+// addresses per warp instruction compete with the streamed matrix.  One CTA of 1024 threads
+// per SM; a warp per row from the row counter, 16-byte loads of four 16-bit indices and four
+// values, two quads per lane in flight.
+constexpr int SMX_NT = 1024;
+constexpr int64_t SMX_MAX_ROWS = 53248;   // 208 KB of FP32
+
+__global__ void __launch_bounds__(SMX_NT, 1) k_sweep32_smem(int64_t nq, const int64_t* __restrict__ rp,
+                                                            const uint16_t* __restrict__ ci,
+                                                            const float* __restrict__ ah,
+                                                            const float* __restrict__ r32,
+                                                            const float* __restrict__ din, float* __restrict__ dout,
+                                                            const SolveState* st, unsigned* ctr) {
+  extern __shared__ float xs[];
+  if (st->done) return;
+  const int64_t n4 = nq >> 2;
+  for (int64_t j = threadIdx.x; j < n4; j += blockDim.x)
+    reinterpret_cast<float4*>(xs)[j] = __ldg(reinterpret_cast<const float4*>(din) + j);
+  for (int64_t j = 4 * n4 + threadIdx.x; j < nq; j += blockDim.x) xs[j] = __ldg(din + j);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = warp_fetch_row(ctr); i < nq; i = warp_fetch_row(ctr)) {
+    float s = dot32<32, true, uint16_t, 2, true>(rp[i], rp[i + 1], lane, ci, ah, xs);
+    s = warp_sum(s);
+    if (lane == 0) dout[i] = r32[i] + s;
+  }
+}
+
+cudaError_t sweep32_smem(reach_ctx* c, const float* din, float* dout, cudaStream_t s, unsigned* ctr) {
+  const size_t bytes = sizeof(float) * (size_t)c->n_q;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_sweep32_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float) * SMX_MAX_ROWS));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_sweep32_smem<<<c->sm_count, SMX_NT, bytes, s>>>(c->n_q, c->a_rowptr, c->a_col16, c->a_hi, c->r32, din, dout,
+                                                   c->st, ctr);
+  return cudaGetLastError();
+}
+
 // out_i = v_i / d_i (the right-hand side of a Jacobi form).
 __global__ void k_div_d(int64_t nq, const double* __restrict__ v, const double* __restrict__ d,
                         double* __restrict__ out) {
@@ -790,15 +836,18 @@ struct Lay {
   bool vec;
   bool seg = false;     // entry-balanced tiles (segscan.cu) instead of a row mapping
   bool tma = false;     // FP32 sweep with rows staged by bulk copies (tma.cu); others as 64
+  bool smx = false;     // FP32 sweep with the correction vector in shared memory; others as 64
 };
 
 constexpr int LAY_SEG = 128;
 constexpr int LAY_VEC16 = 48;   // half a warp per row with 16-byte loads
 constexpr int LAY_TMA = 80;
+constexpr int LAY_SMX = 72;
 
 static Lay lay_of(int code) {
   if (code == LAY_SEG) return Lay{32, true, true};
   if (code == LAY_TMA) return Lay{32, true, false, true};
+  if (code == LAY_SMX) return Lay{32, true, false, false, true};
   if (code == LAY_VEC16) return Lay{16, true};
   return code >= 64 ? Lay{32, true} : Lay{code, false};
 }
@@ -821,7 +870,12 @@ static int solver_group(int64_t rows, int64_t nnz) {
 
 static Lay layout(reach_ctx* c, int64_t rows, int64_t nnz, int method = 0) {
   if (method >= 0 && method < 3 && c->tune.gm[method] > 0) return lay_of(c->tune.gm[method]);
-  if (c->tune.g > 0) return lay_of(c->tune.g);
+  if (c->tune.g > 0) {
+    Lay L = lay_of(c->tune.g);
+    // the shared-memory sweep needs 16-bit indices and a vector that fits: else as 64
+    if (L.smx && (!c->a_col16 || c->n_q > SMX_MAX_ROWS)) L.smx = false;
+    return L;
+  }
   const int g = solver_group(rows, nnz);
   const bool vec = g == 32 && rows > 0 && nnz / rows >= 96;
   return {g, vec};
@@ -1004,6 +1058,7 @@ cudaError_t run_loop(reach_ctx* c, cudaGraphExec_t& exec, int64_t& exec_key, int
 
 static int64_t shape_key(reach_ctx* c, const Lay& L, int k) {
   return (c->n_q * 1000003LL + c->m_q) * 131 + L.g * 7 + (L.vec ? 1 : 0) + (L.seg ? 3 : 0) + (L.tma ? 5 : 0) +
+         (L.smx ? 11 : 0) +
          1000LL * k +
          100000LL * c->tune.sweep_u;
 }
@@ -1066,6 +1121,7 @@ cudaError_t solve_mixed(reach_ctx* c, const double* x0q) {
       float* dout = (j & 1) ? c->dl[0] : c->dl[1];
       if (L.seg) seg_sweep32(c, din, dout, cs);
       else if (L.tma) sweep32_tma(c, din, dout, cs, &c->st->rowctr[j]);
+      else if (L.smx) sweep32_smem(c, din, dout, cs, &c->st->rowctr[j]);
       else LAY_DISPATCH(L, l_sweep32, c, din, dout, cs, &c->st->rowctr[j]);
     }
     k_apply<<<ew_grid(c, (const void*)k_apply, nq), NT, 0, cs>>>(nq, c->x, c->xf, c->dl[0], c->st, k);
@@ -1267,6 +1323,8 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
   // tiles (FP64 Jacobi and the FP32 sweep), which wins when a few rows are very long
   // (LAY_TMA, the FP32 sweep staged by bulk copies, is not a candidate: it measured 1.7x
   // slower than 64 on the dense system, with each row's first segments arriving cold)
+  // (LAY_SMX, the FP32 sweep with its vector in shared memory, is opt-in too: on the dense
+  // system it measured within 1 % of 64, so the L1 gathers are not what limits that sweep)
   const int codes[10] = {1, 2, 4, 8, 16, 32, LAY_VEC16, 64, 66, LAY_SEG};
   const double mean = (double)c->m_q / (double)c->n_q;
   Sys y{c->n_q, c->a_rowptr, c->a_col, c->a_jv, c->bj};   // Jacobi form (the FP64 sweep)
@@ -1276,6 +1334,7 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
   for (int code : codes) {
     const Lay L = lay_of(code);
     if (code == 66 && method != REACH_JACOBI_MIXED) continue;
+    if (L.smx && (method != REACH_JACOBI_MIXED || !c->a_col16 || c->n_q > SMX_MAX_ROWS)) continue;
     if (L.seg && (e = seg_plan(c)) != cudaSuccess) return e;
     if (L.vec && !L.seg && mean < 16) continue;  // nothing to vectorise
     if (!L.vec && L.g > 4 * mean + 4) continue;  // mostly idle lanes
@@ -1297,6 +1356,9 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
           LAY_DISPATCH(L, l_resid_hilo, c, 62, s, ctr);
         } else if (L.tma) {
           sweep32_tma(c, c->dl[0], c->dl[1], s, ctr);
+        } else if (L.smx) {
+          e = sweep32_smem(c, c->dl[0], c->dl[1], s, ctr);
+          if (e != cudaSuccess) return e;
         } else if (L.seg && method == REACH_JACOBI_MIXED) {
           seg_sweep32(c, c->dl[0], c->dl[1], s);
         } else if (L.seg && method == REACH_BICGSTAB_FP64) {
@@ -1380,6 +1442,7 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
     if (L.seg && kernel == 0) seg_sweep(c, c->x, c->x2, &c->st->slot[0], s);
     else if (L.seg && kernel == 1) seg_sweep32(c, c->dl[0], c->dl[1], s);
     else if (L.tma && kernel == 1) sweep32_tma(c, c->dl[0], c->dl[1], s, ctr);
+    else if (L.smx && kernel == 1) sweep32_smem(c, c->dl[0], c->dl[1], s, ctr);
     else if (L.seg && kernel == 2) seg_resid_hilo(c, &c->st->slot[0], s);
     else if (L.seg && kernel == 3) {
       seg_spmv64(c, c->vp, c->x2, s);
