@@ -518,13 +518,10 @@ __global__ void __launch_bounds__(SMX_NT, 1) k_sweep32_smem(int64_t nq, const in
 
 cudaError_t sweep32_smem(reach_ctx* c, const float* din, float* dout, cudaStream_t s, unsigned* ctr) {
   const size_t bytes = sizeof(float) * (size_t)c->n_q;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_sweep32_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(float) * SMX_MAX_ROWS));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // per device and cheap: set on every launch rather than cached in a static
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_sweep32_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float) * SMX_MAX_ROWS));
+  if (e != cudaSuccess) return e;
   k_sweep32_smem<<<c->sm_count, SMX_NT, bytes, s>>>(c->n_q, c->a_rowptr, c->a_col16, c->a_hi, c->r32, din, dout,
                                                    c->st, ctr);
   return cudaGetLastError();
