@@ -171,12 +171,14 @@ reach_status reach_scc(reach_ctx* ctx, int32_t* label, int32_t* level, int32_t f
 /* Autotuner for the row mapping of `method` on the current system (after
  * reach_precompute).  Times every candidate mapping of the method's dominant kernel --
  * lanes per row 1 (the paper's one thread per row, §5.1; tried only when rows average at
- * most 8 entries), 2, 4, 8, 16, 32, a warp with 16-byte vector loads (reported as 64; 66
- * for the FP32 sweep with four quads per trip), or entry-balanced tiles of 4096 stored
- * entries (reported as 128: the segmented sweep of REACH_JACOBI_SEG, and for BiCGStab a
- * segmented product followed by the elementwise M u with its dot products; it wins when
- * a few rows are very long) -- for a few launches and
- * keeps the fastest for later solves of this context.  For
+ * most 8 entries), 2, 4, 8, 16, 32, half a warp or a warp with 16-byte vector loads
+ * (reported as 48 and 64; 66 for the FP32 sweep with four quads per trip), or
+ * entry-balanced tiles of 4096 stored entries (reported as 128: the segmented sweep of
+ * REACH_JACOBI_SEG, and for BiCGStab a segmented product followed by the elementwise M u
+ * with its dot products; it wins when a few rows are very long) -- for a few launches and
+ * keeps the fastest for later solves of this context.  Two FP32-sweep variants are not
+ * candidates and are chosen only through the REACH_LANES environment variable: 72 (the
+ * correction vector staged in shared memory) and 80 (rows staged by bulk copies).  For
  * JACOBI_FP64 it also picks the sweeps between convergence checks, used when
  * reach_solve gets refine_k = 0.  Setting REACH_AUTOTUNE=1 in the environment makes the
  * first reach_solve of each method run it.  Outputs (host, may be NULL): the chosen
