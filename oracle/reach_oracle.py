@@ -17,7 +17,10 @@ paper's order and notation:
   §1, §2.3   the direct O(n^3) route (LU with partial pivoting)   -> dense_solve
   (none)     adjoint solve and parameter gradients                -> adjoint, grad_p,
                                                                      softmax_probs, grad_theta
-  (none)     a-posteriori error bound                             -> error_bound
+  (none)     a-posteriori error bounds: exact ||M^-1|| from tau = M^-1 1, Varah's
+             row-dominance bound, and the bound from an approximate tau -> error_bound,
+                                                                     varah_margin, varah_bound,
+                                                                     supersolution_norm_bound
   §8         strongly connected components of the digraph of A, solved in reverse
              topological order (the future-work idea of §8)      -> scc_labels, scc_levels,
                                                                      block_jacobi
@@ -342,6 +345,47 @@ def error_bound(m, b, x):
     tau = dense_solve(m, np.ones(m.shape[0]))
     r = b - m @ x
     return float(np.max(tau) * np.max(np.abs(r))) if r.size else 0.0
+
+
+def varah_margin(m):
+    """min_i (|M_ii| - sum_{j != i} |M_ij|): the row-dominance margin of M.
+
+    For a chain's M = I - A this is the smallest one-step probability of leaving S?
+    (into S=0 or S=1).  When it is positive, ||M^-1||_inf <= 1 / margin (Varah 1975).
+    """
+    m = sp.csr_matrix(m)
+    if m.shape[0] == 0:
+        return np.inf
+    diag = np.abs(m.diagonal())
+    off = abs(m - sp.diags(m.diagonal())) @ np.ones(m.shape[0])
+    return float(np.min(diag - off))
+
+
+def varah_bound(m, b, x):
+    """Certified max-norm error of x for M x = b from Varah's bound: ||b - M x|| / margin.
+
+    Valid for any strictly row-diagonally-dominant M; +inf when the margin is not positive.
+    """
+    r = b - sp.csr_matrix(m) @ x
+    if r.size == 0:
+        return 0.0
+    c = varah_margin(m)
+    return float(np.max(np.abs(r)) / c) if c > 0 else np.inf
+
+
+def supersolution_norm_bound(m, tau_tilde):
+    """Upper bound of ||M^-1||_inf from any vector with M tau_tilde >= c 1, c > 0.
+
+    For an M-matrix M = I - A (A >= 0, spectral radius of A below 1) the inverse is
+    entrywise non-negative, so M (tau_tilde - c tau) >= 0 gives tau <= tau_tilde / c for the
+    exact tau = M^-1 1, and ||M^-1||_inf = max_i tau_i <= max_i tau_tilde_i / c.  An
+    approximate tau (from any solver) thus certifies the norm; +inf when c <= 0.
+    """
+    t = np.asarray(tau_tilde, np.float64)
+    if t.size == 0:
+        return 0.0
+    c = float(np.min(sp.csr_matrix(m) @ t))
+    return float(np.max(t) / c) if c > 0 else np.inf
 
 
 # ---------------------------------------------------------------- §8: SCCs in reverse topological order

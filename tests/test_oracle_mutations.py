@@ -169,3 +169,82 @@ def test_block_jacobi_highest_level_first_is_caught(monkeypatch):
     with pytest.raises(AssertionError):
         for seed in range(10):
             pins.test_block_jacobi_matches_lu(seed)
+
+
+def _softmax_variant(index_by_row=False, offset_sign=1.0, shift_from_first_row=False):
+    def bad(rowptr, cls_e, offset, theta):
+        rowptr = np.asarray(rowptr)
+        deg = np.diff(rowptr)
+        row = np.repeat(np.arange(deg.size), deg)
+        idx = np.minimum(row, len(theta) - 1) if index_by_row else np.asarray(cls_e)
+        logit = np.asarray(theta, float)[idx] + offset_sign * np.asarray(offset, float)
+        mx = np.maximum.reduceat(logit, rowptr[:-1])
+        shift = np.full(logit.size, mx[0]) if shift_from_first_row else np.repeat(mx, deg)
+        e = np.exp(logit - shift)
+        return e / np.repeat(np.add.reduceat(e, rowptr[:-1]), deg)
+    return bad
+
+
+def test_softmax_theta_indexed_by_row_is_caught(monkeypatch):
+    _patch(monkeypatch, "softmax_probs", _softmax_variant(index_by_row=True))
+    with pytest.raises(AssertionError):
+        pins.test_softmax_class_parameters_set_edge_ratios()
+
+
+def test_softmax_offset_sign_is_caught(monkeypatch):
+    _patch(monkeypatch, "softmax_probs", _softmax_variant(offset_sign=-1.0))
+    with pytest.raises(AssertionError):
+        pins.test_softmax_offsets_of_one_class_give_exact_shares()
+
+
+def test_softmax_shift_from_another_row_is_caught(monkeypatch):
+    _patch(monkeypatch, "softmax_probs", _softmax_variant(shift_from_first_row=True))
+    with pytest.raises(AssertionError), np.errstate(all="ignore"):
+        pins.test_softmax_large_logits_per_row()
+
+
+def test_error_bound_with_the_smallest_tau_is_caught(monkeypatch):
+    def bad(m, b, x):
+        tau = R.dense_solve(m, np.ones(m.shape[0]))
+        return float(np.min(tau) * np.max(np.abs(b - m @ x)))
+    _patch(monkeypatch, "error_bound", bad)
+    with pytest.raises(AssertionError):
+        pins.test_error_bound_exact_on_fair_gamblers_ruin(10)
+
+
+def test_error_bound_with_the_mean_tau_is_caught(monkeypatch):
+    def bad(m, b, x):
+        tau = R.dense_solve(m, np.ones(m.shape[0]))
+        return float(np.mean(tau) * np.max(np.abs(b - m @ x)))
+    _patch(monkeypatch, "error_bound", bad)
+    with pytest.raises(AssertionError):
+        pins.test_error_bound_exact_on_fair_gamblers_ruin(10)
+
+
+def test_varah_margin_without_absolute_values_is_caught(monkeypatch):
+    def bad(m):
+        m = sp.csr_matrix(m)
+        off = (m - sp.diags(m.diagonal())) @ np.ones(m.shape[0])
+        return float(np.min(m.diagonal() - off))
+    _patch(monkeypatch, "varah_margin", bad)
+    with pytest.raises(AssertionError):
+        pins.test_varah_margin_of_chains_is_the_smallest_exit_probability()
+
+
+def test_varah_margin_with_the_diagonal_in_the_sum_is_caught(monkeypatch):
+    def bad(m):
+        m = sp.csr_matrix(m)
+        return float(np.min(np.abs(m.diagonal()) - abs(m) @ np.ones(m.shape[0])))
+    _patch(monkeypatch, "varah_margin", bad)
+    with pytest.raises(AssertionError):
+        pins.test_varah_bound_attained_on_constant_exit_rows()
+
+
+def test_supersolution_bound_with_max_over_min_swapped_is_caught(monkeypatch):
+    def bad(m, t):
+        t = np.asarray(t, float)
+        c = float(np.max(sp.csr_matrix(m) @ t))
+        return float(np.max(t) / c) if c > 0 else np.inf
+    _patch(monkeypatch, "supersolution_norm_bound", bad)
+    with pytest.raises(AssertionError):
+        pins.test_supersolution_bound_from_an_approximate_tau()

@@ -389,3 +389,151 @@ def test_scc_labels_leaves_its_input_alone():
     before = (a.indptr.copy(), a.indices.copy(), a.data.copy())
     O.scc_labels(a)
     assert all(np.array_equal(x, y) for x, y in zip(before, (a.indptr, a.indices, a.data)))
+
+
+# ---------------------------------------------------------------- softmax parametrisation (exact values)
+# P_e = exp(theta[class_e] + offset_e) / sum over the row's out-edges: pinned by values the
+# definition fixes, independently of how the oracle evaluates it.
+
+def _one_row(cls_e, offset, theta):
+    rowptr = np.array([0, len(cls_e)], np.int64)
+    return O.softmax_probs(rowptr, np.asarray(cls_e, np.int32), np.asarray(offset, float),
+                           np.asarray(theta, float))
+
+
+def test_softmax_offsets_of_one_class_give_exact_shares():
+    """Three edges of one class with offsets (0, ln 2, ln 3): weights 1 : 2 : 3."""
+    p = _one_row([0, 0, 0], [0.0, np.log(2.0), np.log(3.0)], [0.7])
+    np.testing.assert_allclose(p, [1 / 6, 1 / 3, 1 / 2], rtol=1e-15, atol=0)
+
+
+def test_softmax_class_parameters_set_edge_ratios():
+    """Equal offsets, classes 1 and 0 with theta differing by ln 4: the edge ratio is 4."""
+    theta = np.array([0.3, 0.3 + np.log(4.0)])
+    p = _one_row([1, 0], [0.5, 0.5], theta)
+    np.testing.assert_allclose(p, [0.8, 0.2], rtol=1e-15, atol=0)
+    # class and offset both enter: logits ln 3 + 0 and 0 + ln 2 -> 3 : 2
+    p = _one_row([0, 1], [np.log(3.0), 0.0], [0.0, np.log(2.0)])
+    np.testing.assert_allclose(p, [0.6, 0.4], rtol=1e-15, atol=0)
+
+
+def test_softmax_single_edge_and_shift_invariance():
+    pc = synth.parametric_chain(n=400, n_classes=8, seed=21)
+    p = O.softmax_probs(pc.rowptr, pc.cls, pc.offset, pc.theta)
+    np.testing.assert_allclose(np.add.reduceat(p, pc.rowptr[:-1]), 1.0, rtol=0, atol=1e-15)
+    single = np.flatnonzero(np.diff(pc.rowptr) == 1)
+    assert single.size and np.all(p[pc.rowptr[single]] == 1.0)
+    # a constant added to every theta cancels in every row
+    p2 = O.softmax_probs(pc.rowptr, pc.cls, pc.offset, pc.theta + 5.25)
+    np.testing.assert_allclose(p2, p, rtol=1e-13, atol=0)
+
+
+def test_softmax_theta_of_a_class_moves_only_its_rows():
+    pc = synth.parametric_chain(n=400, n_classes=8, seed=22)
+    p = O.softmax_probs(pc.rowptr, pc.cls, pc.offset, pc.theta)
+    row = np.repeat(np.arange(pc.n), np.diff(pc.rowptr))
+    for c in (0, 5):
+        th = pc.theta.copy()
+        th[c] += 0.5
+        q = O.softmax_probs(pc.rowptr, pc.cls, pc.offset, th)
+        rows_c = np.zeros(pc.n, bool)
+        rows_c[row[pc.cls == c]] = True
+        moved = np.abs(q - p) > 0
+        assert np.all(~moved[~rows_c[row]])                       # other rows untouched
+        # rows that mix class c with other classes change; class-c edges gain weight
+        mixed = rows_c & np.bincount(row, weights=(pc.cls != c), minlength=pc.n).astype(bool)
+        assert np.all(moved[mixed[row]])
+        assert np.all(q[(pc.cls == c) & mixed[row]] > p[(pc.cls == c) & mixed[row]])
+
+
+def test_softmax_large_logits_per_row():
+    """Rows with logits near +-700: each row is computed from its own logits (exp would
+    overflow or underflow if the row's shift came from another row)."""
+    rowptr = np.array([0, 2, 4], np.int64)
+    cls_e = np.array([0, 1, 2, 3], np.int32)
+    theta = np.array([700.0, 700.0 + np.log(3.0), -700.0, -700.0 + np.log(7.0)])
+    p = O.softmax_probs(rowptr, cls_e, np.zeros(4), theta)
+    np.testing.assert_allclose(p, [0.25, 0.75, 0.125, 0.875], rtol=1e-13, atol=0)
+
+
+# ---------------------------------------------------------------- error bounds (exact values)
+
+def _fair_gambler_system(N):
+    c = synth.gamblers_ruin(N, 0.5)
+    cls = O.partition(*chain_arrays(c))
+    q, a, b = O.extract_system(c.n, c.rowptr, c.col, c.val, cls)
+    return q, O.system_matrix(a), b
+
+
+@pytest.mark.parametrize("N", [2, 9, 10, 31])
+def test_error_bound_exact_on_fair_gamblers_ruin(N):
+    """Fair walk on 0..N: tau_i = i (N - i), the expected duration, so ||M^-1||_inf is
+    max_i i (N - i) = floor(N/2) ceil(N/2).  At x = x* + c tau the residual is -c 1, the
+    error is c max tau and the bound is attained: error_bound = c floor(N/2) ceil(N/2)."""
+    q, m, b = _fair_gambler_system(N)
+    tau = q * (N - q)                                  # rows of S? are the states 1..N-1
+    xs = q / N
+    c = 1e-3
+    bound = O.error_bound(m, b, xs + c * tau)
+    want = c * (N // 2) * ((N + 1) // 2)
+    assert abs(bound - want) <= 1e-11 * want
+    # one entry perturbed by c: residual max is c (the entry's own row), bound c max tau
+    k = len(q) // 2
+    x = xs.copy()
+    x[k] += c
+    assert abs(O.error_bound(m, b, x) - c * (N // 2) * ((N + 1) // 2)) <= 1e-11 * c * N * N
+    # the supersolution bound from the exact tau is the same norm
+    assert abs(O.supersolution_norm_bound(m, tau) - (N // 2) * ((N + 1) // 2)) <= 1e-12 * N * N
+
+
+def test_supersolution_bound_from_an_approximate_tau():
+    """Any tau' with M tau' >= c 1 bounds the norm from above; it tightens as tau' -> tau."""
+    N = 24
+    q, m, _ = _fair_gambler_system(N)
+    exact = (N // 2) * ((N + 1) // 2)
+    tau = (q * (N - q)).astype(float)
+    for scale in (1.5, 1.01, 1.0 + 1e-9):
+        assert exact <= O.supersolution_norm_bound(m, scale * tau) <= scale * exact * (1 + 1e-12)
+    assert O.supersolution_norm_bound(m, 0.5 * tau) >= exact * (1 - 1e-12)
+    # a vector with M t <= 0 somewhere certifies nothing
+    t = tau.copy()
+    t[3] += 5.0
+    assert O.supersolution_norm_bound(m, t) == np.inf
+
+
+def test_varah_bound_attained_on_constant_exit_rows():
+    """Rows that all leave S? with the same probability e: M 1 = e 1, so ||M^-1|| = 1/e,
+    the margin is e, and at x = x* + c 1 both bounds equal the true error c."""
+    rng = np.random.default_rng(4)
+    n, e = 40, 0.125
+    w = rng.uniform(0.1, 1.0, (n, n)) * (rng.random((n, n)) < 0.3)
+    np.fill_diagonal(w, 0.0)
+    w[np.arange(n), (np.arange(n) + 1) % n] += 0.1                  # no empty row
+    a = sp.csr_matrix((1.0 - e) * w / w.sum(axis=1, keepdims=True))
+    m = sp.identity(n, format="csr") - a
+    b = np.full(n, e * 0.25)
+    xs = O.dense_solve(m, b)
+    c = 1e-3
+    assert abs(O.varah_margin(m) - e) <= 1e-15
+    assert abs(O.varah_bound(m, b, xs + c) - c) <= 1e-11 * c
+    assert abs(O.error_bound(m, b, xs + c) - c) <= 1e-11 * c
+    # a bound that ignores the exit margin (residual alone) is e times too small
+    assert O.varah_bound(m, b, xs + c) >= 0.99 * c > 1.01 * e * c
+
+
+def test_varah_margin_of_chains_is_the_smallest_exit_probability():
+    """On the worked chain's system A = [[0, .5], [.4, 0]]: exits 0.5 and 0.6, margin 0.5;
+    on the fair gambler's ruin interior rows never leave S? in one step: margin 0, no bound."""
+    c = synth.worked_chain()
+    cls = O.partition(*chain_arrays(c))
+    q, a, b = O.extract_system(c.n, c.rowptr, c.col, c.val, cls)
+    m = O.system_matrix(a)
+    assert O.varah_margin(m) == 0.5
+    assert O.varah_bound(m, b, np.array([0.625, 0.25]) + 1e-3) == pytest.approx(
+        max(abs(b - m @ (np.array([0.625, 0.25]) + 1e-3))) / 0.5, rel=1e-15)
+    _, mg, bg = _fair_gambler_system(10)
+    assert O.varah_margin(mg) == 0.0
+    assert O.varah_bound(mg, bg, np.zeros(9)) == np.inf
+    # for a general diagonally dominant system the margin is |M_ii| - sum |M_ij|
+    md = sp.csr_matrix(np.array([[4.0, -1.0, 2.0], [1.0, -5.0, 1.0], [0.0, 3.0, 3.5]]))
+    assert O.varah_margin(md) == pytest.approx(0.5, abs=1e-15)
