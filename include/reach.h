@@ -98,6 +98,17 @@ typedef struct {
   double bytes_moved;     /* algorithmic HBM bytes of this solve */
   int32_t status;         /* reach_status of the solve */
   int32_t refinements;    /* JACOBI_MIXED: FP64 residual steps taken */
+  /* Certified bound on max_i |x*_i - x_i| over S?, where x* solves the stored FP64 system
+   * (I - A) x* = b exactly (x = 1 on S=1 and 0 on S=0 are exact): ||(I - A)^-1||_inf times
+   * an upper bound of the exact ||b - (I - A) x||_inf of the returned x, with the residual's
+   * rounding error bounded and every step rounded upward.  The norm bound is the smaller of
+   * Varah's, 1 / min_i (|d_i| - sum_j |A_ij|) (Varah 1975; d_i - sum_j A_ij is a chain
+   * state's one-step probability of leaving S?), taken at reach_precompute, and the one
+   * from reach_norm_bound.  +inf when neither is available (some S? state cannot leave S?
+   * in one step and reach_norm_bound was not called).  reach_grad: the bound on the adjoint
+   * solution y from Varah's margin over the columns of A.  reach_norm_bound: its norm bound
+   * from the approximate tau alone. */
+  double err_bound;
 } reach_info;
 
 /* Strongly connected components of the digraph of A over S? (an edge i -> j for each
@@ -154,6 +165,23 @@ reach_status reach_get_classes(reach_ctx* ctx, uint8_t* cls, int32_t flags);
 reach_status reach_solve(reach_ctx* ctx, int32_t method, double eps, int64_t max_iter,
                          int32_t refine_k, const double* x0, double* x_out, int32_t flags,
                          reach_info* info);
+
+/* Certified upper bound of ||(I - A)^-1||_inf for the current chain system (§2.3), for the
+ * error bound of every later reach_solve.  Solves (I - A) tau = 1 -- tau_s is the expected
+ * number of steps a walk from s spends in S? -- with `method` (JACOBI_FP64, JACOBI_MIXED or
+ * BICGSTAB_FP64; eps and max_iter as in reach_solve; refinement period 16), then checks the
+ * approximate tau' it returns: with c = min_i ((I - A) tau')_i, bounded from below with
+ * directed rounding, c > 0 gives ||(I - A)^-1||_inf <= max_i tau'_i / c, because
+ * (I - A)^-1 >= 0 entrywise for a chain.  This needs no exit margin, so it bounds chains
+ * whose states do not all leave S? in one step, and it is close to the true norm when tau'
+ * is accurate.  *kinv (host, may be NULL) receives the norm bound now in use (the smaller
+ * of this one and Varah's; +inf if c <= 0).  info (may be NULL) describes the tau solve.
+ * The system's b is restored afterwards; the context's last solution for reach_grad is
+ * kept.  REACH_ESTATE for a general system (reach_system_create), where (I - A)^-1 >= 0
+ * does not hold.  A tau solve that hits max_iter still yields a valid (looser) bound and
+ * returns REACH_OK.  Synchronises the stream. */
+reach_status reach_norm_bound(reach_ctx* ctx, int32_t method, double eps, int64_t max_iter, double* kinv,
+                              reach_info* info);
 
 /* Strongly connected components of the digraph of A over S? and their levels (§8:
  * the paper's future work takes the components in reverse topological order).  After
@@ -282,15 +310,19 @@ void reach_batch_destroy(reach_batch* b);
  * rowptr int64[n_q+1] and col int32 in [0, n_q), val float64; b and d = 1 - A_ii as
  * float64[n_q]) and x float64[n_q] (start vector in, solution out).  It runs Jacobi
  * sweeps x <- (b + A x) / d and checks max|x' - x| < eps every check_every (even, >= 2)
- * sweeps, at most max_iter sweeps; *iters_out and *delta_out (host, may be NULL)
- * receive the sweep count and the last max|x' - x|.
+ * sweeps and after the last sweep, running at most max_iter sweeps (the last window is
+ * shortened to fit); *iters_out and *delta_out (host, may be NULL) receive the sweep
+ * count and the last max|x' - x|.
  * Scratch (the second Jacobi vector) lives in a fixed device array inside the library,
  * sized for n_q <= 524288 (4 MiB + 4 KiB, held on every device that loads the library
- * until the process exits); larger n_q returns REACH_EINVAL.  The first call on a
- * device looks up that array's device address; make that first call before any stream
- * capture.  Every call on a device shares the array, so calls that overlap on the GPU
- * (other streams or threads) race: serialise them.  Returns REACH_ENOTCONV when
- * max_iter runs out.  Synchronises `stream` after every check. */
+ * until the process exits); larger n_q returns REACH_EINVAL.  Every call looks up that
+ * array's address on the current device (a lookup that allocates nothing); the first call
+ * on a device also loads the library's device code there, so make that first call before
+ * any stream capture.  `stream` must belong to the current device (REACH_EINVAL
+ * otherwise).  Every call on a device shares the array, so calls that overlap on the GPU
+ * (other streams or threads) race: serialise them.  Returns REACH_ENOTCONV when max_iter
+ * runs out, REACH_ECUDA when a launch or copy fails.  Synchronises `stream` after every
+ * check. */
 reach_status reach_jacobi_solve_noalloc(int64_t n_q, const int64_t* rowptr, const int32_t* col,
                                         const double* val, const double* b, const double* d,
                                         double eps, int64_t max_iter, int32_t check_every,

@@ -28,7 +28,7 @@ __all__ = [
     "reach_param_probs", "reach_param_grad_theta", "reach_last_error", "reach_destroy",
     "reach_version", "Solver", "reach_batch_create", "reach_batch_precompute",
     "reach_batch_get_classes", "reach_batch_solve", "reach_batch_destroy", "BatchSolver",
-    "reach_batch_set_chains", "reach_batch_chain_info",
+    "reach_batch_set_chains", "reach_batch_chain_info", "reach_norm_bound",
 ]
 
 REACH_OK, REACH_EINVAL, REACH_ENOMEM, REACH_ECUDA, REACH_ESTATE = 0, 1, 2, 3, 4
@@ -57,7 +57,8 @@ class ReachInfo(C.Structure):
     _fields_ = [("iters", C.c_int64), ("n_q", C.c_int64), ("m_q", C.c_int64),
                 ("last_delta", C.c_double), ("resid_inf", C.c_double),
                 ("ms_precompute", C.c_double), ("ms_solve", C.c_double),
-                ("bytes_moved", C.c_double), ("status", C.c_int32), ("refinements", C.c_int32)]
+                ("bytes_moved", C.c_double), ("status", C.c_int32), ("refinements", C.c_int32),
+                ("err_bound", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -99,6 +100,7 @@ _SIGS = {
     "reach_system_create": (_I32, [C.POINTER(_P), _I64, _I64, _P, _P, _P, _P, _I32, _P]),
     "reach_time_kernel": (_I32, [_P, _I32, _I32, C.POINTER(_D)]),
     "reach_scc": (_I32, [_P, _P, _P, _I32, _I32, C.POINTER(ReachSccInfo)]),
+    "reach_norm_bound": (_I32, [_P, _I32, _D, _I64, C.POINTER(_D), C.POINTER(ReachInfo)]),
     "reach_jacobi_solve_noalloc": (_I32, [_I64, _P, _P, _P, _P, _P, _D, _I64, _I32, _P,
                                           C.POINTER(_I64), C.POINTER(_D), _P]),
 }
@@ -254,6 +256,16 @@ def reach_grad(ctx, m, init, eps=1e-13, max_iter=1_000_000, out=None, check=True
     return out, info.as_dict()
 
 
+def reach_norm_bound(ctx, method=REACH_BICGSTAB_FP64, eps=1e-8, max_iter=1_000_000):
+    """Certified bound of ||(I - A)^-1||_inf from a solve of (I - A) tau = 1; later solves
+    of the context use it for their err_bound.  Returns (bound in use, info of the tau solve)."""
+    method = METHODS.get(method, method) if isinstance(method, str) else int(method)
+    k = C.c_double(0.0)
+    info = ReachInfo()
+    _check(lib().reach_norm_bound(ctx, method, float(eps), int(max_iter), C.byref(k), C.byref(info)), ctx)
+    return k.value, info.as_dict()
+
+
 def reach_param_probs(rowptr, cls, offset, theta, out, stream=None):
     """P_e = row softmax of theta[cls_e] + offset_e (CUDA tensors)."""
     n = rowptr.numel() - 1
@@ -366,6 +378,9 @@ class Solver:
 
     def autotune(self, method="jacobi"):
         return reach_autotune(self.ctx, method)
+
+    def norm_bound(self, method="bicgstab", eps=1e-8, max_iter=1_000_000):
+        return reach_norm_bound(self.ctx, method, eps, max_iter)
 
     def scc(self, labels=True, max_rounds=0):
         return reach_scc(self.ctx, labels, max_rounds)

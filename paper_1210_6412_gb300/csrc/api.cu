@@ -112,6 +112,10 @@ void free_system(reach_ctx* c) {
   dfree(c->at_rowptr); dfree(c->at_col); dfree(c->at_val); dfree(c->at_jv); dfree(c->at_b);
   dfree(c->x); dfree(c->x2); dfree(c->vr); dfree(c->vq); dfree(c->vp); dfree(c->vv);
   dfree(c->vs); dfree(c->vt); dfree(c->r32); dfree(c->xf); dfree(c->dl[0]); dfree(c->dl[1]);
+  dfree(c->tau_save);
+  c->kinv_varah = INFINITY;
+  c->kinv_tau = INFINITY;
+  c->kinv_varah_t = -1.0;
   seg_free(c);
   scc_free(c);
 }
@@ -129,6 +133,14 @@ cudaMemcpyKind kind_to_dev(int32_t flags) {
 }
 cudaMemcpyKind kind_from_dev(int32_t flags) {
   return flags == REACH_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+// Certified max-norm error: ||M^-1|| (kinv, an upper bound) times the upper bound of the
+// exact residual norm, the product rounded up; 0 for an empty system, +inf without a bound.
+double error_bound(int64_t n_q, double kinv, double resid_ub) {
+  if (n_q == 0) return 0.0;
+  if (!(kinv < INFINITY) || !(resid_ub < INFINITY)) return INFINITY;
+  return std::nextafter(kinv * resid_ub, INFINITY);
 }
 
 }  // namespace
@@ -151,7 +163,7 @@ void reach_destroy(reach_ctx* c) {
   dfree(c->t_rowptr); dfree(c->t_col);
   dfree(c->cls); dfree(c->qidx); dfree(c->vis); dfree(c->queue); dfree(c->bfs);
   dfree(c->xfull); dfree(c->st); dfree(c->bi); dfree(c->part); dfree(c->ticket);
-  dfree(c->verr); dfree(c->vrow); dfree(c->maxrow);
+  dfree(c->verr); dfree(c->vrow); dfree(c->maxrow); dfree(c->keys);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->cap) cudaStreamDestroy(c->cap);
@@ -209,7 +221,7 @@ static reach_status create_common(reach_ctx** out, int64_t n, int64_t m, const i
       (e = dalloc(&c->st, 1)) != cudaSuccess || (e = dalloc(&c->bi, 1)) != cudaSuccess ||
       (e = dalloc(&c->part, part_n)) != cudaSuccess || (e = dalloc(&c->ticket, 1)) != cudaSuccess ||
       (e = dalloc(&c->verr, 1)) != cudaSuccess || (e = dalloc(&c->vrow, 1)) != cudaSuccess ||
-      (e = dalloc(&c->maxrow, 1)) != cudaSuccess) {
+      (e = dalloc(&c->maxrow, 1)) != cudaSuccess || (e = dalloc(&c->keys, 2)) != cudaSuccess) {
     reach_status s = cuda_fail(nullptr, e, (w + ": allocation").c_str());
     reach_destroy(c);
     return s;
@@ -306,6 +318,7 @@ reach_status reach_system_create(reach_ctx** out, int64_t n, int64_t m, const in
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess && !verr) e = build_jacobi_form(c);
   if (e == cudaSuccess && !verr) e = alloc_workspace(c);
+  if (e == cudaSuccess && !verr) e = varah_norm_bound(c, false, &c->kinv_varah);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev1, s);
   if (e == cudaSuccess) e = cudaEventSynchronize(c->ev1);
   float ms = 0.f;
@@ -344,7 +357,9 @@ reach_status reach_precompute(reach_ctx* c, int32_t mode) {
   if (e == cudaSuccess) e = build_jacobi_form(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "reach_precompute");
   if ((e = alloc_workspace(c)) != cudaSuccess) return cuda_fail(c, e, "reach_precompute: workspace");
-  e = cudaEventRecord(c->ev1, s);
+  // the norm bound behind every solve's certified error (Varah's, from the exit margins)
+  e = varah_norm_bound(c, false, &c->kinv_varah);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev1, s);
   if (e == cudaSuccess) e = cudaEventSynchronize(c->ev1);
   float ms = 0.f;
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev0, c->ev1);
@@ -475,6 +490,7 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
     info->bytes_moved = bytes;
     info->status = hs.status;
     info->refinements = hs.refinements;
+    info->err_bound = error_bound(c->n_q, std::min(c->kinv_varah, c->kinv_tau), hs.resid_ub);
   }
   c->have_x = hs.status == REACH_OK;
   if (hs.status != REACH_OK) {
@@ -485,6 +501,72 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
     set_err(c, why);
   }
   return (reach_status)hs.status;
+}
+
+reach_status reach_norm_bound(reach_ctx* c, int32_t method, double eps, int64_t max_iter, double* kinv,
+                              reach_info* info) {
+  if (!c) return fail(nullptr, REACH_EINVAL, "reach_norm_bound: NULL context");
+  if (!c->have_classes) return fail(c, REACH_ESTATE, "reach_norm_bound: call reach_precompute first");
+  if (c->general)
+    return fail(c, REACH_ESTATE, "reach_norm_bound: needs a chain (the bound uses (I - A)^-1 >= 0)");
+  if (method != REACH_JACOBI_FP64 && method != REACH_JACOBI_MIXED && method != REACH_BICGSTAB_FP64)
+    return fail(c, REACH_EINVAL, "reach_norm_bound: method must be JACOBI_FP64, JACOBI_MIXED or BICGSTAB_FP64");
+  if (!(eps > 0.0) || !std::isfinite(eps) || max_iter < 1)
+    return fail(c, REACH_EINVAL, "reach_norm_bound: need eps > 0 and max_iter >= 1");
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (c->n_q == 0) {
+    if (kinv) *kinv = 0.0;
+    return REACH_OK;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!c->tau_save && (e = dalloc(&c->tau_save, 2 * c->n_q)) != cudaSuccess)
+    return cuda_fail(c, e, "reach_norm_bound: allocation");
+  c->tune.k = 16;
+  const int64_t max_bodies = method == REACH_BICGSTAB_FP64 ? max_iter + 4 : max_iter / 16 + 4;
+  reach_status rs = start_state(c, eps, max_iter, max_bodies);
+  if (rs != REACH_OK) return rs;
+  cudaStream_t s = c->stream;
+  e = cudaEventRecord(c->ev0, s);
+  if (e == cudaSuccess) e = tau_rhs_begin(c);
+  if (e == cudaSuccess) {
+    if (method == REACH_JACOBI_FP64) e = solve_jacobi64(c, nullptr, false);
+    else if (method == REACH_JACOBI_MIXED) e = solve_mixed(c, nullptr);
+    else e = solve_bicgstab(c, nullptr);
+  }
+  // the system's own right-hand side goes back whatever happened to the solve
+  const cudaError_t e2 = tau_rhs_end(c);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev1, s);
+  SolveState hs;
+  std::memset(&hs, 0, sizeof(hs));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, c->st, sizeof(hs), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  // tau' itself is in c->x whether or not the stopping rule held: any tau' certifies
+  double kt = INFINITY;
+  if (e == cudaSuccess) e = tau_norm_bound(c, c->x, &kt);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reach_norm_bound");
+  if (kt < c->kinv_tau) c->kinv_tau = kt;
+  if (kinv) *kinv = std::min(c->kinv_varah, c->kinv_tau);
+  if (info) {
+    info->iters = hs.iter;
+    info->n_q = c->n_q;
+    info->m_q = c->m_q;
+    info->last_delta = hs.last;
+    info->resid_inf = hs.resid;
+    info->ms_precompute = c->ms_precompute;
+    info->ms_solve = ms;
+    info->status = hs.status;
+    info->refinements = hs.refinements;
+    info->err_bound = kt;
+  }
+  // a tau solve that stopped early still gives a valid (looser, possibly infinite) bound
+  if (hs.status != REACH_OK && hs.status != REACH_ENOTCONV) {
+    set_err(c, "reach_norm_bound: the solve for tau failed");
+    return (reach_status)hs.status;
+  }
+  return REACH_OK;
 }
 
 reach_status reach_scc(reach_ctx* c, int32_t* label, int32_t* level, int32_t flags, int32_t max_rounds,
@@ -571,6 +653,7 @@ reach_status reach_grad_method(reach_ctx* c, int32_t method, int64_t init, doubl
     hs.status = REACH_OK;
   } else if (e == cudaSuccess) {
     e = build_transposed_system(c);
+    if (e == cudaSuccess && c->kinv_varah_t < 0.0) e = varah_norm_bound(c, true, &c->kinv_varah_t);
     const int k = c->tune.k;
     const bool bi = method == REACH_BICGSTAB_FP64;
     if (e == cudaSuccess) {
@@ -610,6 +693,8 @@ reach_status reach_grad_method(reach_ctx* c, int32_t method, int64_t init, doubl
     info->ms_precompute = c->ms_precompute;
     info->ms_solve = ms;
     info->status = status;
+    // the adjoint's own error: ||(I - A)^-T|| from Varah's margin over the columns of A
+    info->err_bound = kind == CLS_SQ ? error_bound(c->n_q, c->kinv_varah_t, hs.resid_ub) : 0.0;
   }
   if (status != REACH_OK) set_err(c, "reach_grad: adjoint solve did not converge");
   return status;

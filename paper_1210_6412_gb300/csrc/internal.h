@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <functional>
 #include <string>
 
@@ -26,6 +27,7 @@ struct SolveState {
   int64_t iter;
   double last;          // stopping quantity of the last check
   double resid;         // FP64 max|b - (I - A) x| after the loop
+  double resid_ub;      // certified upper bound of the exact max|b - (I - A) x| (rounding included)
   int32_t status;       // reach_status
   int32_t done;         // set once the stopping rule held or max_iter ran out
   int32_t refinements;
@@ -146,6 +148,15 @@ struct reach_ctx {
   unsigned long long* maxrow = nullptr;  // longest row of P (device, written by validation)
   int64_t max_row = 0;                   // its host copy
 
+  // norm bounds of (I - A)^-1 for the certified error bound of every solve: Varah's
+  // (from the row-dominance margin, at precompute), the one from an approximate
+  // tau = (I - A)^-1 1 (reach_norm_bound), and Varah's over the transpose (adjoint)
+  double kinv_varah = INFINITY;
+  double kinv_tau = INFINITY;
+  double kinv_varah_t = -1.0;           // < 0: not computed yet
+  unsigned long long* keys = nullptr;   // two ordered-key reduction words
+  double* tau_save = nullptr;           // b and bj while the tau system is solved (2 n?)
+
   reach::Tuning tune;
   bool device_loops = true;   // conditional-while graphs (false: host-driven loops)
   double ms_precompute = 0.0;
@@ -200,7 +211,7 @@ void seg_spmv64(reach_ctx* c, const double* u, double* y, cudaStream_t s);
 void seg_resid_hilo(reach_ctx* c, unsigned long long* slot, cudaStream_t s);
 void seg_free(reach_ctx* c);
 // ---- tma.cu
-void sweep32_tma(reach_ctx* c, const float* din, float* dout, cudaStream_t s, unsigned* ctr);
+cudaError_t sweep32_tma(reach_ctx* c, const float* din, float* dout, cudaStream_t s, unsigned* ctr);
 // ---- scc.cu
 cudaError_t scc_decompose(reach_ctx* c, int32_t max_rounds, bool* loop_ok);
 cudaError_t scc_outputs(reach_ctx* c, int32_t* label, int32_t* level, cudaMemcpyKind kind, reach_scc_info* info);
@@ -211,6 +222,10 @@ void scc_free(reach_ctx* c);
 cudaError_t exclusive_scan_u8(reach_ctx* c, const uint8_t* in, int64_t* out, int64_t n, int64_t* total_dev);
 cudaError_t exclusive_scan_u32(reach_ctx* c, const uint32_t* in, int64_t* out, int64_t n);
 cudaError_t residual_report(reach_ctx* c, const double* xq);
+cudaError_t varah_norm_bound(reach_ctx* c, bool transposed, double* kinv);
+cudaError_t tau_rhs_begin(reach_ctx* c);
+cudaError_t tau_rhs_end(reach_ctx* c);
+cudaError_t tau_norm_bound(reach_ctx* c, const double* tau, double* kinv);
 
 // ---- shared host helpers (api.cu)
 int pick_group(int64_t rows, int64_t nnz);

@@ -9,7 +9,6 @@
 // -- in a fixed device array compiled into the library.
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -29,10 +28,6 @@ constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + sizeof(double) * (size_t)NOALL
 // library holds it until the process exits.  Host code must not use the symbol as an
 // address: the device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
-
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mu;
-void* g_scratch[MAX_DEVICES] = {};
 
 __global__ void k_na_clear(unsigned long long* dmax) { *dmax = 0ull; }
 
@@ -72,21 +67,20 @@ void na_sweep(int grid, cudaStream_t s, int64_t nq, const int64_t* rp, const int
   k_na_sweep<G><<<grid, 256, 0, s>>>(nq, rp, ci, av, b, d, x, xn, dmax);
 }
 
-// Device address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array on the current device.  Looked up on every call:
+// the lookup is cheap and allocates nothing, and a cached pointer would go stale after a
+// cudaDeviceReset (new context) or point into another device's copy.
 cudaError_t scratch_on_current_device(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch[dev] = p;
-  }
-  *out = static_cast<unsigned char*>(g_scratch[dev]);
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
+}
+
+reach_status na_cuda_fail(cudaError_t e, const char* what) {
+  set_err(nullptr, std::string("reach_jacobi_solve_noalloc: ") + what + ": " + cudaGetErrorString(e));
+  return REACH_ECUDA;
 }
 
 }  // namespace
@@ -108,25 +102,29 @@ extern "C" reach_status reach_jacobi_solve_noalloc(int64_t n_q, const int64_t* r
     set_err(nullptr, "reach_jacobi_solve_noalloc: need eps > 0, max_iter >= 1, check_every even >= 2");
     return REACH_EINVAL;
   }
-  unsigned char* base = nullptr;
-  cudaError_t e = scratch_on_current_device(&base);
-  if (e != cudaSuccess) {
-    set_err(nullptr, std::string("reach_jacobi_solve_noalloc: scratch lookup: ") + cudaGetErrorString(e));
-    return REACH_ECUDA;
-  }
-  unsigned long long* dmax = reinterpret_cast<unsigned long long*>(base);
-  double* xn = reinterpret_cast<double*>(base + NOALLOC_HEADER);
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return na_cuda_fail(e, "current device");
+  // the scratch used is the current device's copy: the stream must belong to that device
+  int sdev = dev;
+  e = cudaStreamGetDevice(s, &sdev);
+  if (e != cudaSuccess) return na_cuda_fail(e, "stream device");
+  if (sdev != dev) {
+    set_err(nullptr, "reach_jacobi_solve_noalloc: the stream belongs to another device than the current one");
+    return REACH_EINVAL;
+  }
+  unsigned char* base = nullptr;
+  e = scratch_on_current_device(&base);
+  if (e != cudaSuccess) return na_cuda_fail(e, "scratch lookup");
+  unsigned long long* dmax = reinterpret_cast<unsigned long long*>(base);
+  double* xn = reinterpret_cast<double*>(base + NOALLOC_HEADER);
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return na_cuda_fail(e, "device attribute");
   int64_t nnz = 0;
   e = cudaMemcpyAsync(&nnz, rowptr + n_q, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) {
-    set_err(nullptr, std::string("reach_jacobi_solve_noalloc: ") + cudaGetErrorString(e));
-    return REACH_ECUDA;
-  }
+  if (e != cudaSuccess) return na_cuda_fail(e, "reading rowptr[n_q]");
   const int g = pick_group(n_q, nnz);
   const int64_t blocks = (n_q * g + 255) / 256;
   const int grid = (int)std::min<int64_t>(blocks, (int64_t)sms * 8);
@@ -134,10 +132,13 @@ extern "C" reach_status reach_jacobi_solve_noalloc(int64_t n_q, const int64_t* r
   double delta = 0.0;
   reach_status status = REACH_ENOTCONV;
   while (it < max_iter) {
-    for (int j = 0; j < check_every; ++j) {
+    // a window of check_every sweeps, the last one shortened so that exactly max_iter
+    // sweeps run at most; the window's last sweep computes max|x' - x|
+    const int w = (int)std::min<int64_t>(check_every, max_iter - it);
+    for (int j = 0; j < w; ++j) {
       const double* xi = (j & 1) ? xn : x;
       double* xo = (j & 1) ? x : xn;
-      if (j == check_every - 1) k_na_clear<<<1, 1, 0, s>>>(dmax);
+      if (j == w - 1) k_na_clear<<<1, 1, 0, s>>>(dmax);
       switch (g) {
         case 2: na_sweep<2>(grid, s, n_q, rowptr, col, val, b, d, xi, xo, dmax); break;
         case 4: na_sweep<4>(grid, s, n_q, rowptr, col, val, b, d, xi, xo, dmax); break;
@@ -146,14 +147,17 @@ extern "C" reach_status reach_jacobi_solve_noalloc(int64_t n_q, const int64_t* r
         default: na_sweep<32>(grid, s, n_q, rowptr, col, val, b, d, xi, xo, dmax); break;
       }
     }
-    it += check_every;
+    // an odd window leaves the newest iterate in the scratch vector: copy it back
+    if (w & 1) e = cudaMemcpyAsync(x, xn, sizeof(double) * (size_t)n_q, cudaMemcpyDeviceToDevice, s);
+    // a launch that failed without a sticky error would otherwise leave x untouched and
+    // the reduction word at the previous call's value
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return na_cuda_fail(e, "sweep launch");
+    it += w;
     unsigned long long bits = 0;
     e = cudaMemcpyAsync(&bits, dmax, sizeof(bits), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      set_err(nullptr, std::string("reach_jacobi_solve_noalloc: ") + cudaGetErrorString(e));
-      return REACH_ECUDA;
-    }
+    if (e != cudaSuccess) return na_cuda_fail(e, "reading max|x' - x|");
     std::memcpy(&delta, &bits, sizeof(delta));
     if (delta < eps) {
       status = REACH_OK;

@@ -350,25 +350,124 @@ __global__ void __launch_bounds__(NT) k_jacobi64(int64_t nq, const int64_t* __re
   if (DELTA) cta_to_slot<1, true>(bits_to_delta(mx), slot);
 }
 
-// FP64 residual r = b - (I - A) x, max|r| into slot (reported as resid_inf).
-template <int G, bool V>
-__global__ void __launch_bounds__(NT) k_resid64(int64_t nq, const int64_t* __restrict__ rp,
-                                                const int32_t* __restrict__ ci,
-                                                const double* __restrict__ av,
-                                                const double* __restrict__ b,
-                                                const double* __restrict__ d,
-                                                const double* __restrict__ x,
-                                                unsigned long long* slot) {
+// ------------------------------------------------------------------ certified error bound
+// For M = I - A (§2.3) and any x, ||x* - x||_inf <= ||M^-1||_inf ||b - M x||_inf.  The
+// residual kernel below returns, per row, an upper bound of the EXACT |b - M x|_i of the
+// stored FP64 system: the computed |r_i| plus the rounding allowance gamma_D S_i, where
+// S_i = |b_i| + |d_i x_i| + sum_j |A_ij x_j| (summed with upward rounding) and D the number
+// of roundings any term passes through in this kernel's fixed order (ceil(len / G)
+// sequential FMAs per lane, log2 G shuffle additions, then + b_i and - d_i x_i), with
+// gamma_D = D u / (1 - D u), u = 2^-53, evaluated with upward rounding.
+
+template <int G>
+RDEV double group_sum_ru(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = __dadd_ru(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+
+template <int G>
+constexpr int log2_of() { return G <= 1 ? 0 : 1 + log2_of<G / 2>(); }
+
+template <int G>
+__global__ void __launch_bounds__(NT) k_resid_cert(int64_t nq, const int64_t* __restrict__ rp,
+                                                   const int32_t* __restrict__ ci,
+                                                   const double* __restrict__ av,
+                                                   const double* __restrict__ b,
+                                                   const double* __restrict__ d,
+                                                   const double* __restrict__ x,
+                                                   unsigned long long* slot_r, unsigned long long* slot_ub) {
   RowGroups rg = RowGroups::make<G>();
-  double mx = 0.0;
-  auto xf = [x](int32_t j) { return __ldg(x + j); };
+  unsigned long long mr = 0ull, mu = 0ull;
   for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
-    double s = 0.0;
-    if (i < nq) s = dot64<G, V>(rp[i], rp[i + 1], rg.lane, ci, av, xf);
+    double s = 0.0, a = 0.0;
+    int64_t lo = 0, hi = 0;
+    if (i < nq) {
+      lo = rp[i];
+      hi = rp[i + 1];
+      for (int64_t k = lo + rg.lane; k < hi; k += G) {
+        const double v = __ldcs(av + k), xv = __ldg(x + __ldcs(ci + k));
+        s = fma(v, xv, s);
+        a = __fma_ru(fabs(v), fabs(xv), a);
+      }
+    }
     s = group_sum<G>(s);
-    if (i < nq && rg.lane == 0) mx = fmax(mx, nan_to_inf(fabs(b[i] + s - d[i] * x[i])));
+    a = group_sum_ru<G>(a);
+    if (i < nq && rg.lane == 0) {
+      const double bi = b[i], di = d[i], xi = x[i];
+      const double r = fma(-di, xi, bi + s);
+      const double sum_abs = __dadd_ru(__dadd_ru(a, fabs(bi)), __dmul_ru(fabs(di), fabs(xi)));
+      const double depth = (double)((hi - lo + G - 1) / G + log2_of<G>() + 2);
+      const double du = depth * 0x1p-53;   // exact: an integer times a power of two
+      const double gam = __ddiv_ru(du, __dadd_rd(1.0, -du));
+      const double ub = __dadd_ru(fabs(r), __dmul_ru(gam, sum_abs));
+      mr = umax64(mr, abs_bits(r));
+      mu = umax64(mu, abs_bits(ub));
+    }
   }
-  cta_to_slot<1, true>(mx, slot);
+  __shared__ double sh[64];
+  double v[2] = {bits_to_delta(mr), bits_to_delta(mu)};
+  block_reduce<2, true>(v, sh);
+  if (threadIdx.x == 0) {
+    atomic_max_nonneg(slot_r, nan_to_inf(v[0]));
+    atomic_max_nonneg(slot_ub, nan_to_inf(v[1]));
+  }
+}
+
+// Order-preserving map of doubles onto unsigned integers (for atomicMin / atomicMax of
+// values of either sign), and back.
+RDEV unsigned long long ordered_key(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// Lower bound, per row, of (|M| w)_i in the sense needed by the norm bounds:
+//   ABS:  |d_i| - sum_j |A_ij|          (w = 1: Varah's row-dominance margin)
+//   else: d_i w_i - sum_j A_ij w_j      (M w for a chain's M-matrix, A >= 0)
+// The subtracted sum is accumulated with upward rounding (an upper bound of the exact
+// sum whatever the signs), the first term with downward rounding, the difference rounded
+// down: a guaranteed lower bound of the exact value.  min over rows -> *kmin, and for
+// !ABS max_i w_i -> *kmax, both as ordered keys.
+template <int G, bool ABS>
+__global__ void __launch_bounds__(NT) k_row_lower(int64_t nq, const int64_t* __restrict__ rp,
+                                                  const int32_t* __restrict__ ci,
+                                                  const double* __restrict__ av,
+                                                  const double* __restrict__ d,
+                                                  const double* __restrict__ w,
+                                                  unsigned long long* kmin, unsigned long long* kmax) {
+  RowGroups rg = RowGroups::make<G>();
+  double lo_min = __longlong_as_double(0x7ff0000000000000LL), w_max = -lo_min;
+  for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
+    double a = 0.0;
+    if (i < nq)
+      for (int64_t k = rp[i] + rg.lane; k < rp[i + 1]; k += G) {
+        const double v = av[k];
+        a = ABS ? __dadd_ru(a, fabs(v)) : __fma_ru(v, w[ci[k]], a);
+      }
+    a = group_sum_ru<G>(a);
+    if (i < nq && rg.lane == 0) {
+      const double first = ABS ? fabs(d[i]) : __dmul_rd(d[i], w[i]);
+      const double lo = __dadd_rd(first, -a);
+      lo_min = fmin(lo_min, lo != lo ? -__longlong_as_double(0x7ff0000000000000LL) : lo);
+      if (!ABS) w_max = fmax(w_max, w[i]);
+    }
+  }
+  // warp reductions and one atomic per warp: the values have either sign, which the
+  // zero-padded block reduction does not handle
+  lo_min = -warp_max(-lo_min);
+  if (!ABS) w_max = warp_max(w_max);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(kmin, ordered_key(lo_min));
+    if (!ABS) atomicMax(kmax, ordered_key(w_max));
+  }
+}
+
+__global__ void k_fill_tau_rhs(int64_t nq, const double* __restrict__ d, double* __restrict__ b,
+                               double* __restrict__ bj) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+    b[i] = 1.0;
+    bj[i] = 1.0 / d[i];
+  }
 }
 
 __global__ void k_check(SolveState* st, int slot_idx, int sweeps, int reset_n) {
@@ -400,7 +499,9 @@ __global__ void k_loop_ctl(SolveState* st, cudaGraphConditionalHandle h, int use
 
 __global__ void k_finalize_resid(SolveState* st) {
   st->resid = slot_value(&st->slot[63]);
+  st->resid_ub = slot_value(&st->slot[61]);
   st->slot[63] = 0ull;
+  st->slot[61] = 0ull;
 }
 
 // ------------------------------------------------------------------ mixed precision
@@ -928,10 +1029,12 @@ static void l_jacobi_nd(reach_ctx* c, const Sys& y, const double* x, double* xn,
   k_jacobi64<G, V, false><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, x, xn, slot, G == 32 ? ctr : nullptr);
 }
 
+// The reported residual: max|b - M x| and its certified upper bound (k_resid_cert, one
+// accumulator per lane so that the rounding depth is known; V layouts use a warp per row).
 template <int G, bool V>
 static void l_resid(reach_ctx* c, const Sys& y, const double* x, cudaStream_t s) {
-  const int grid = grid_rows(c, (const void*)k_resid64<G, V>, NT, G, y.nq);
-  k_resid64<G, V><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, c->d, x, &c->st->slot[63]);
+  const int grid = grid_rows(c, (const void*)k_resid_cert<G>, NT, G, y.nq);
+  k_resid_cert<G><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, c->d, x, &c->st->slot[63], &c->st->slot[61]);
 }
 
 template <int G, bool V>
@@ -1138,6 +1241,106 @@ cudaError_t residual_report(reach_ctx* c, const double* xq) {
   LAY_DISPATCH(L, l_resid, c, y, xq, c->stream);
   k_finalize_resid<<<1, 1, 0, c->stream>>>(c->st);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ norm bounds (host side)
+
+static double key_to_double(unsigned long long k) {
+  const unsigned long long u = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  double v;
+  std::memcpy(&v, &u, sizeof(v));
+  return v;
+}
+
+// Launches k_row_lower over the system (or its transpose) and reads back the minimum
+// lower bound and (for w) the largest w_i.  Synchronises the context stream.
+static cudaError_t row_lower(reach_ctx* c, bool transposed, const double* w, double* lo_min, double* w_max) {
+  const int64_t nq = c->n_q;
+  const int64_t* rp = transposed ? c->at_rowptr : c->a_rowptr;
+  const int32_t* ci = transposed ? c->at_col : c->a_col;
+  const double* av = transposed ? c->at_val : c->a_val;
+  cudaStream_t s = c->stream;
+  unsigned long long keys[2] = {~0ull, 0ull};
+  cudaError_t e = cudaMemcpyAsync(c->keys, keys, sizeof(keys), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  const int g = solver_group(nq, c->m_q);   // the transpose has the same entries
+#define KL(G)                                                                                            \
+  do {                                                                                                   \
+    if (w) {                                                                                             \
+      const int grid = grid_rows(c, (const void*)k_row_lower<G, false>, NT, G, nq);                     \
+      k_row_lower<G, false><<<grid, NT, 0, s>>>(nq, rp, ci, av, c->d, w, c->keys, c->keys + 1);          \
+    } else {                                                                                             \
+      const int grid = grid_rows(c, (const void*)k_row_lower<G, true>, NT, G, nq);                       \
+      k_row_lower<G, true><<<grid, NT, 0, s>>>(nq, rp, ci, av, c->d, nullptr, c->keys, c->keys + 1);     \
+    }                                                                                                    \
+  } while (0)
+  switch (g) {
+    case 1: KL(1); break;
+    case 2: KL(2); break;
+    case 4: KL(4); break;
+    case 8: KL(8); break;
+    case 16: KL(16); break;
+    default: KL(32); break;
+  }
+#undef KL
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(keys, c->keys, sizeof(keys), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  const double lo = key_to_double(keys[0]);
+  *lo_min = lo == lo ? lo : -INFINITY;
+  if (w_max) {
+    const double wm = key_to_double(keys[1]);
+    *w_max = wm == wm ? wm : INFINITY;
+  }
+  return cudaSuccess;
+}
+
+// ||M^-1||_inf <= 1 / min_i (|d_i| - sum_j |A_ij|) when that margin is positive (Varah);
+// +inf otherwise.  Over the rows of the transpose, the same bound for ||M^-T||_inf.
+cudaError_t varah_norm_bound(reach_ctx* c, bool transposed, double* kinv) {
+  if (c->n_q == 0) {
+    *kinv = 0.0;
+    return cudaSuccess;
+  }
+  double margin = 0.0;
+  const cudaError_t e = row_lower(c, transposed, nullptr, &margin, nullptr);
+  if (e != cudaSuccess) return e;
+  *kinv = margin > 0.0 ? std::nextafter(1.0 / margin, INFINITY) : INFINITY;
+  return cudaSuccess;
+}
+
+// The right-hand side of (I - A) tau = 1 in place of b (and 1 / d in place of bj), the
+// system's own saved in c->tau_save; tau_rhs_end puts them back.
+cudaError_t tau_rhs_begin(reach_ctx* c) {
+  const int64_t nq = c->n_q;
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaMemcpyAsync(c->tau_save, c->b, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->tau_save + nq, c->bj, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  k_fill_tau_rhs<<<ew_grid(c, (const void*)k_fill_tau_rhs, nq), NT, 0, s>>>(nq, c->d, c->b, c->bj);
+  return cudaGetLastError();
+}
+
+cudaError_t tau_rhs_end(reach_ctx* c) {
+  const int64_t nq = c->n_q;
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaMemcpyAsync(c->b, c->tau_save, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->bj, c->tau_save + nq, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
+  return e;
+}
+
+// From an approximate tau' (any vector): c = min_i (M tau')_i, bounded from below with
+// directed rounding; if c > 0 then ||M^-1||_inf <= max_i tau'_i / c for the chain's
+// M-matrix (M^-1 >= 0 entrywise, so tau = M^-1 1 <= tau' / c).  +inf otherwise.
+cudaError_t tau_norm_bound(reach_ctx* c, const double* tau, double* kinv) {
+  double cmin = 0.0, tmax = 0.0;
+  const cudaError_t e = row_lower(c, false, tau, &cmin, &tmax);
+  if (e != cudaSuccess) return e;
+  *kinv = (cmin > 0.0 && tmax > 0.0 && std::isfinite(tmax)) ? std::nextafter(tmax / cmin, INFINITY) : INFINITY;
+  return cudaSuccess;
 }
 
 // BiCGStab iterations on the system y from x (x holds the start), the loop graph cached
@@ -1352,7 +1555,8 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
         } else if (part == 1) {
           LAY_DISPATCH(L, l_resid_hilo, c, 62, s, ctr);
         } else if (L.tma) {
-          sweep32_tma(c, c->dl[0], c->dl[1], s, ctr);
+          e = sweep32_tma(c, c->dl[0], c->dl[1], s, ctr);
+          if (e != cudaSuccess) return e;
         } else if (L.smx) {
           e = sweep32_smem(c, c->dl[0], c->dl[1], s, ctr);
           if (e != cudaSuccess) return e;
@@ -1438,9 +1642,13 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
     cudaMemsetAsync(&c->st->done, 0, sizeof(int32_t), s);
     if (L.seg && kernel == 0) seg_sweep(c, c->x, c->x2, &c->st->slot[0], s);
     else if (L.seg && kernel == 1) seg_sweep32(c, c->dl[0], c->dl[1], s);
-    else if (L.tma && kernel == 1) sweep32_tma(c, c->dl[0], c->dl[1], s, ctr);
-    else if (L.smx && kernel == 1) sweep32_smem(c, c->dl[0], c->dl[1], s, ctr);
-    else if (L.seg && kernel == 2) seg_resid_hilo(c, &c->st->slot[0], s);
+    else if (L.tma && kernel == 1) {
+      const cudaError_t le = sweep32_tma(c, c->dl[0], c->dl[1], s, ctr);
+      if (le != cudaSuccess) e = le;
+    } else if (L.smx && kernel == 1) {
+      const cudaError_t le = sweep32_smem(c, c->dl[0], c->dl[1], s, ctr);
+      if (le != cudaSuccess) e = le;
+    } else if (L.seg && kernel == 2) seg_resid_hilo(c, &c->st->slot[0], s);
     else if (L.seg && kernel == 3) {
       seg_spmv64(c, c->vp, c->x2, s);
       k_bi_v_ew<<<ew_grid(c, (const void*)k_bi_v_ew, c->n_q), NT, 0, s>>>(c->n_q, c->d, c->vp, c->x2, c->vq, c->vv,
@@ -1452,6 +1660,7 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
     else LAY_DISPATCH(L, l_bi_v, c, ya, s);
   };
   one(0);  // warm-up
+  if (e != cudaSuccess) return e;
   e = cudaEventRecord(c->ev0, s);
   for (int j = 1; j <= launches && e == cudaSuccess; ++j) one(j);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev1, s);

@@ -105,7 +105,10 @@ __global__ void __launch_bounds__(TMA_WARPS * 32, 2) k_sweep32_tma(int64_t nq, c
     float acc = 0.0f;
     for (int g = 0; g < nseg; ++g) {
       const int s = g % TMA_ST;
-      if (!mbar_wait(&bars[s], (parity >> s) & 1u)) {
+      // every lane waits (each needs the completed phase before reading the stage), and
+      // the outcome is made warp-uniform: a lane that gave up takes the whole warp out,
+      // so no lane reaches the warp-wide shuffles below without the others
+      if (!__all_sync(0xffffffffu, mbar_wait(&bars[s], (parity >> s) & 1u))) {
         failed = true;
         break;
       }
@@ -153,26 +156,28 @@ static size_t tma_smem() {
 }
 
 template <typename IT>
-static void launch_tma(reach_ctx* c, const IT* ci, const float* din, float* dout, cudaStream_t s, unsigned* ctr) {
+static cudaError_t launch_tma(reach_ctx* c, const IT* ci, const float* din, float* dout, cudaStream_t s,
+                              unsigned* ctr) {
   const void* fn = (const void*)k_sweep32_tma<IT>;
   const size_t sm = tma_smem<IT>();
-  static bool attr_set = false;   // per instantiation; the attribute is per function
-  if (!attr_set) {
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr_set = true;
-  }
+  // the attribute belongs to the function on the current device: set it on every launch
+  // (cheap) rather than once per process
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TMA_WARPS * 32, sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TMA_WARPS * 32, sm);
+  if (e != cudaSuccess) return e;
   const int64_t warps_needed = c->n_q;
   int grid = c->sm_count * (per_sm > 0 ? per_sm : 1);
   if ((int64_t)grid * TMA_WARPS > warps_needed) grid = (int)((warps_needed + TMA_WARPS - 1) / TMA_WARPS);
   if (grid < 1) grid = 1;
   k_sweep32_tma<IT><<<grid, TMA_WARPS * 32, sm, s>>>(c->n_q, c->a_rowptr, ci, c->a_hi, c->r32, din, dout, c->st, ctr);
+  return cudaGetLastError();
 }
 
-void sweep32_tma(reach_ctx* c, const float* din, float* dout, cudaStream_t s, unsigned* ctr) {
-  if (c->a_col16) launch_tma<uint16_t>(c, c->a_col16, din, dout, s, ctr);
-  else launch_tma<int32_t>(c, c->a_col, din, dout, s, ctr);
+cudaError_t sweep32_tma(reach_ctx* c, const float* din, float* dout, cudaStream_t s, unsigned* ctr) {
+  if (c->a_col16) return launch_tma<uint16_t>(c, c->a_col16, din, dout, s, ctr);
+  return launch_tma<int32_t>(c, c->a_col, din, dout, s, ctr);
 }
 
 }  // namespace reach
