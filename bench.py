@@ -9,9 +9,10 @@ the system of §2.3 as the paper writes it, with S=1 = GS (PROB0_ONLY): 32440 un
 about 105M entries, exact solution x* = 1 (certified by the S=0/S=1 partition).
 
 One step = ingest + validate P (a copy from HBM-resident inputs), the partition and
-extraction (§2.2-2.3), then FP64 Jacobi, mixed-precision Jacobi (FP32 sweeps, FP64
+extraction (§2.2-2.3), a certified bound of ||(I - A)^-1|| (a BiCGStab solve of
+(I - A) tau = 1), then FP64 Jacobi, mixed-precision Jacobi (FP32 sweeps, FP64
 refinement every 16 sweeps) and FP64 BiCGStab, each run until its max error against
-x* is at most 1e-9.  The matrix is 1.3 GB, far larger than the 129 MB L2, so no
+x* is at most 1e-9; each reports its certified error bound.  The matrix is 1.3 GB, far larger than the 129 MB L2, so no
 flush is needed between steps.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle instead.
@@ -41,9 +42,8 @@ TARGET_ERR = 1e-9
 # stopping thresholds that give max error <= 1e-9 on this system (contraction ~0.99)
 EPS = {"jacobi": 5e-12, "mixed": 5e-12, "bicgstab": 5e-12}
 K_REFINE = 16
-# DRAM bytes (read + write) per launch from ncu captures of the current kernels on this
-# workload: profiles/jacobi64_dense32768.md and profiles/mixed_dense32768.md.  Set back
-# to None whenever the kernel changes, until it is captured again.
+# DRAM bytes (read + write) per launch of the current kernels on this workload, from one
+# ncu capture each; set back to None whenever the kernel changes, until it is captured again.
 NCU_TRAFFIC_BYTES = 1.271472e9 + 2.955776e6
 NCU_TRAFFIC_SWEEP32_BYTES = 0.633107e9 + 2.984192e6
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA per clock (ncu's
@@ -132,61 +132,139 @@ def dist_init():
     return ws, rank, local
 
 
-def cpu_oracle_sample(chain, sweeps=6):
-    """The oracle as it stands on a bounded sample of the step, scaled to one full step.
+def cpu_info():
+    """Host cores and CPU model (for the CPU baseline's record)."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.strip().startswith("Model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine()}
 
-    Runs the oracle's partition (PROB0_ONLY) and extraction on the full matrix, BiCGStab
-    to the same stopping rule, and `sweeps` Jacobi sweeps; the Jacobi time-to-solution is
-    extrapolated from the measured per-sweep time and the contraction of max|dx|.
+
+class CpuOracleStep:
+    """One time-to-solution of the oracle on the host cores, split into `pieces` parts.
+
+    The oracle's partition (PROB0_ONLY) and extraction of the full matrix (numpy, as it
+    stands), then its FP64 Jacobi and BiCGStab loops in their C build on `threads` cores,
+    each to the benchmark's stopping rule.  The oracle has no mixed-precision form, so its
+    step is precompute + Jacobi + BiCGStab.  Piece 0 also runs the precompute; pieces
+    0..pieces-2 run `chunk` Jacobi sweeps each (resuming from the previous iterate); the
+    last piece finishes Jacobi and runs BiCGStab.  Every part is measured, nothing is
+    extrapolated: the pieces' times add up to one full time-to-solution.
     """
-    import oracle as O
+
+    def __init__(self, chain, threads=0, pieces=1, expect_sweeps=2150):
+        from oracle import c_oracle
+        self.co = c_oracle
+        self.chain = chain
+        self.threads = c_oracle.set_threads(threads)
+        self.pieces = max(1, int(pieces))
+        self.chunk = -(-int(expect_sweeps) // self.pieces)
+        self.t = {"precompute": 0.0, "jacobi": 0.0, "bicgstab": 0.0}
+        self.sweeps = 0
+        self.done = False
+        self.x = None
+
+    def piece(self, i):
+        import oracle as O
+        c = self.chain
+        if i == 0:
+            t0 = time.perf_counter()
+            cls = O.partition(c.n, c.rowptr, c.col, c.val, c.goal, O.PROB0_ONLY)
+            q, a, b = O.extract_system(c.n, c.rowptr, c.col, c.val, cls)
+            self.m, self.b = O.system_matrix(a), b
+            self.t["precompute"] += time.perf_counter() - t0
+        last = i == self.pieces - 1
+        if not self.done:
+            t0 = time.perf_counter()
+            budget = 10_000_000 if last else self.chunk
+            self.x, it, d, ok = self.co.jacobi(self.m, self.b, EPS["jacobi"], budget, x0=self.x)
+            self.t["jacobi"] += time.perf_counter() - t0
+            self.sweeps += it
+            self.done = ok
+        if last:
+            t0 = time.perf_counter()
+            self.xb, self.bi_iters, _, st = self.co.bicgstab(self.m, self.b, EPS["bicgstab"], 200)
+            self.t["bicgstab"] += time.perf_counter() - t0
+
+    def run(self):
+        for i in range(self.pieces):
+            self.piece(i)
+        return self
+
+    def total_ms(self):
+        return 1e3 * sum(self.t.values())
+
+    def record(self):
+        return {"value": self.total_ms(), "unit": "ms", "cores": self.threads, "kind": "oracle",
+                **cpu_info(),
+                "parts_ms": {k: 1e3 * v for k, v in self.t.items()},
+                "jacobi_sweeps": self.sweeps,
+                "bicgstab_iters": self.bi_iters,
+                "max_err": {"jacobi": float(np.max(np.abs(self.x - 1.0))),
+                            "bicgstab": float(np.max(np.abs(self.xb - 1.0)))},
+                "sample": ("the whole workload, measured: the oracle's partition + extraction (numpy), "
+                           f"then its FP64 Jacobi ({self.sweeps} sweeps) and BiCGStab ({self.bi_iters} "
+                           f"iterations) loops in C on {self.threads} host threads, each to eps = "
+                           f"{EPS['jacobi']:g}; the oracle has no mixed-precision form")}
+
+
+def cpu_single_core_estimate(chain_m, b, sweeps_total, sweeps=5):
+    """The paper's sequential-C analogue: a few Jacobi sweeps of the C loops on one thread,
+    scaled by the full sweep count (an extrapolation, labelled as such)."""
+    from oracle import c_oracle
+    c_oracle.set_threads(1)
     t0 = time.perf_counter()
-    cls = O.partition(chain.n, chain.rowptr, chain.col, chain.val, chain.goal, O.PROB0_ONLY)
-    q, a, b = O.extract_system(chain.n, chain.rowptr, chain.col, chain.val, cls)
-    m = O.system_matrix(a)
-    t_pre = time.perf_counter() - t0
-    hist = []
-    t0 = time.perf_counter()
-    O.jacobi(m, b, 0.0, sweeps, history=hist)
-    t_sweep = (time.perf_counter() - t0) / sweeps
-    d = [float(np.max(np.abs(hist[i + 1] - hist[i]))) for i in range(len(hist) - 1)]
-    rho = (d[-1] / d[1]) ** (1.0 / (len(d) - 2)) if len(d) > 2 and d[1] > 0 else 0.99
-    jac_iters = int(np.ceil(1 + np.log(EPS["jacobi"] / d[0]) / np.log(rho))) if d[0] > 0 else 1
-    t0 = time.perf_counter()
-    xb, bi_iters, _, ok = O.bicgstab(m, b, EPS["bicgstab"], 200)
-    t_bicg = time.perf_counter() - t0
-    total_s = t_pre + 2 * jac_iters * t_sweep + t_bicg   # the oracle has one FP64 Jacobi; counted twice
-    return {
-        "value_ms": total_s * 1e3,
-        "sample": (f"oracle partition+extraction of the full matrix ({t_pre:.1f} s), BiCGStab to "
-                   f"eps={EPS['bicgstab']:g} ({bi_iters} iters, {t_bicg:.1f} s), {sweeps} Jacobi sweeps "
-                   f"({t_sweep:.2f} s each) extrapolated to {jac_iters} sweeps at contraction {rho:.4f}; "
-                   "the Jacobi leg is counted for both Jacobi forms"),
-        "cpu_seconds_spent": t_pre + sweeps * t_sweep + t_bicg,
-        "bicgstab_max_err": float(np.max(np.abs(xb - 1.0))) if xb.size else 0.0,
-    }
+    c_oracle.jacobi(chain_m, b, 0.0, sweeps)
+    per = (time.perf_counter() - t0) / sweeps
+    c_oracle.set_threads(0)
+    return {"value": per * sweeps_total * 1e3, "unit": "ms", "cores": 1, "kind": "extrapolated",
+            "sample": f"{sweeps} Jacobi sweeps of the C loops on one thread ({per * 1e3:.1f} ms each) "
+                      f"x {sweeps_total} sweeps; Jacobi leg only"}
 
 
 def run_reference(args):
+    """The reference arm: the oracle on the host cores.  The K timed steps together run one
+    full time-to-solution (CpuOracleStep split into K pieces); `value` is their total and
+    ms_per_step their mean.  The W warm-up steps page in the inputs and the code (the
+    partition of the matrix and a few sweeps), untimed."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     chain = make_chain()
-    vals = []
-    samples = []
-    for i in range(args.warmup + args.steps):
-        r = cpu_oracle_sample(chain, sweeps=4)
-        if i >= args.warmup:
-            vals.append(r["value_ms"])
-            samples.append(r["sample"])
-    v = statistics.median(vals)
+    for _ in range(max(1, min(args.warmup, 1))):
+        w = CpuOracleStep(chain, pieces=2, expect_sweeps=6)
+        w.piece(0)
+    step = CpuOracleStep(chain, pieces=args.steps)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step.piece(i)
+    wall_ms = (time.perf_counter() - t0) * 1e3
+    rec = step.record()
+    v = rec["value"]
+    rec["sample"] = (f"the {args.steps} timed steps together run one full time-to-solution "
+                     f"(wall {wall_ms:.0f} ms): " + rec["sample"])
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD},
-        "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": samples[-1]},
+        "cpu_baseline": rec,
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -208,15 +286,21 @@ def kernel_times(R, n, d_in, stream, launches=20):
     return out
 
 
-def launches_per_step(infos, k):
+def launches_per_step(infos, k, tau_iters=0):
     """Kernels of this library launched in one step (counted from the loop structure)."""
     j, mx, b = infos["jacobi"], infos["mixed"], infos["bicgstab"]
     create = 1
-    precompute = 5 + 2 + j.get("bfs_levels", 4) + 1 + 3 + 1 + 3 + 1 + 1
+    precompute = 5 + 2 + j.get("bfs_levels", 4) + 1 + 3 + 1 + 3 + 1 + 1 + 1
     jac = j["iters"] + 2 * (j["iters"] // k) + 3
     mix = mx["refinements"] * (2 + (k - 1) + 2) + 3 + 1
     bic = 1 + 5 * b["iters"] + 3
-    return create + precompute + jac + mix + bic
+    tau = 1 + (1 + 5 * tau_iters + 3) + 1       # right-hand side, BiCGStab, (I - A) tau' check
+    return create + precompute + jac + mix + bic + tau
+
+
+def finite_or_none(v):
+    """JSON has no infinity: an unavailable bound is written as null."""
+    return float(v) if v is not None and np.isfinite(v) else None
 
 
 def run_ours(args):
@@ -236,12 +320,15 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     lanes = {}
+    bound = {}
 
     def step(inputs, outputs):
         infos = {}
         ctx = R.reach_create(n, *inputs, stream=stream.cuda_stream)
         try:
             R.reach_precompute(ctx, R.REACH_PROB0_ONLY)
+            # certified ||(I - A)^-1|| from tau = (I - A)^-1 1, for every solve's error bound
+            bound["kinv"], bound["info"] = R.reach_norm_bound(ctx, "bicgstab", eps=1e-8)
             for meth in ("jacobi", "mixed", "bicgstab"):
                 # row mapping from the autotuner (measured once per system shape, then cached)
                 lanes[meth] = R.reach_autotune(ctx, meth)["lanes"]
@@ -301,6 +388,7 @@ def run_ours(args):
     methods = {}
     for k, inf in infos.items():
         methods[k] = {"ms": inf["ms_solve"], "iters": inf["iters"], "max_err": errs[k],
+                      "err_bound": finite_or_none(inf["err_bound"]),
                       "resid_inf": inf["resid_inf"], "alg_GBps": inf["bytes_moved"] / (inf["ms_solve"] * 1e6),
                       "refinements": inf["refinements"], "lanes": lanes.get(k)}
     fp64_tf = 2.0 * mq / (sweep_ms * 1e-3) / 1e12
@@ -315,6 +403,9 @@ def run_ours(args):
         "methods": methods,
         "precompute_ms": jac["ms_precompute"],
         "max_err_all": max(errs.values()),
+        "err_bound_all": finite_or_none(max(inf["err_bound"] for inf in infos.values())),
+        "norm_bound": {"kinv": finite_or_none(bound["kinv"]), "ms": bound["info"]["ms_solve"],
+                       "iters": bound["info"]["iters"], "method": "bicgstab on (I - A) tau = 1"},
         # the dominant kernel (FP64 Jacobi sweep) is bound by the FP64 pipe, not HBM
         "roofline": {"bound": "alu", "kernel": "k_jacobi64 (FP64 Jacobi sweep)",
                      "achieved": fp64_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -330,13 +421,13 @@ def run_ours(args):
         "kernels": kernels,
         "e2e": {"value": statistics.median(e_ms), "unit": "ms", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_step(infos, K_REFINE) * args.steps,
+        "gpu_launches": launches_per_step(infos, K_REFINE, bound["info"]["iters"]) * args.steps,
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cb = cpu_oracle_sample(chain)
-        line["cpu_baseline"] = {"value": cb["value_ms"], "unit": "ms", "cores": 1, "kind": "oracle",
-                                "sample": cb["sample"]}
+        st = CpuOracleStep(chain).run()          # one full, measured run on every host core
+        line["cpu_baseline"] = st.record()
+        line["cpu_baseline"]["single_core"] = cpu_single_core_estimate(st.m, st.b, st.sweeps)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -54,3 +54,21 @@ def test_peaks_reads_the_measured_table_or_falls_back(bench, tmp_path, monkeypat
     assert bench.peaks() == (6800.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6767.4}')
     assert bench.peaks() == (6767.4, "measured")
+
+
+def test_cpu_oracle_step_pieces_add_up_to_one_solve(bench):
+    """The reference arm splits one oracle time-to-solution over the timed steps: any
+    split runs the same Jacobi sweeps to the same iterate as one uninterrupted run."""
+    from paper_1210_6412_gb300 import synth
+    c = synth.dense_random_chain(n=1500, density=0.1, goal_frac=0.02, seed=3)
+    one = bench.CpuOracleStep(c, pieces=1).run()
+    many = bench.CpuOracleStep(c, pieces=7, expect_sweeps=one.sweeps // 2).run()
+    assert one.done and many.done
+    assert one.sweeps == many.sweeps
+    assert (one.x == many.x).all()
+    rec = many.record()
+    assert rec["kind"] == "oracle" and rec["cores"] >= 1 and rec["nproc"] >= 1
+    assert rec["max_err"]["jacobi"] < 1e-8 and rec["max_err"]["bicgstab"] < 1e-8
+    assert abs(rec["value"] - sum(rec["parts_ms"].values())) < 1e-6
+    single = bench.cpu_single_core_estimate(many.m, many.b, many.sweeps, sweeps=2)
+    assert single["kind"] == "extrapolated" and single["cores"] == 1

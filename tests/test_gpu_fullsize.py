@@ -1,16 +1,15 @@
 """Parity at the full workload sizes.
 
 The dense random chain (n = 32768, 10% density, about 107M entries) is the benchmark
-workload; it always runs.  The layered 8M-state chain, the 4M-state parametric chain and
-the 256-chain batch take minutes to generate on the host and run only with REACH_FULL=1.
+workload.  The layered 8M-state chain, the 4M-state parametric chain and the 256-chain
+batch (67M states, 1.1G entries) are the other full configurations; together they take a
+few minutes, most of it generating the batch on the host.
 
 Where the oracle cannot solve the full system in seconds the check uses facts that hold
 at any size: the exact solution x* = 1 certified by the S=0/S=1 partition, or the
 a-posteriori bound ||x* - x|| <= ||b - M x|| / min_i (M_ii - sum_j |M_ij|) for the strictly
 diagonally dominant M = I - A (Varah's bound), with the residual computed by the oracle.
 """
-import os
-
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -21,7 +20,6 @@ from paper_1210_6412_gb300 import synth
 from tests.gpu_util import need_gpu
 
 pytestmark = pytest.mark.gpu
-full = pytest.mark.skipif(os.environ.get("REACH_FULL") != "1", reason="set REACH_FULL=1 (minutes)")
 
 EPS = {"jacobi": 5e-12, "mixed": 5e-12, "bicgstab": 5e-12}    # the benchmark's thresholds
 
@@ -57,12 +55,16 @@ def test_bench_workload_full(dense):
         assert np.array_equal(s.classes(), cls01_o)
     with R.Solver(c.n, *d_in, mode=R.REACH_PROB0_ONLY) as s:
         assert np.array_equal(s.classes(), cls0_o)
+        kinv, _ = s.norm_bound("bicgstab", eps=1e-8)
+        assert np.isfinite(kinv)
         for meth in ("jacobi", "mixed", "bicgstab"):
             s.autotune(meth)
             x, info = s.solve(meth, eps=EPS[meth], max_iter=200_000, refine_k=16,
                               out=torch.empty(c.n, dtype=torch.float64, device="cuda"))
             err = float(torch.max(torch.abs(x - 1.0)))
             assert info["status"] == R.REACH_OK and err <= 1e-9, (meth, err)
+            # the certified bound covers the true error and certifies the target accuracy
+            assert err <= info["err_bound"] <= 1e-9, (meth, err, info["err_bound"])
 
 
 def test_dense_with_sinks_full():
@@ -78,7 +80,6 @@ def test_dense_with_sinks_full():
             assert np.all((x >= 0) & (x <= 1))
 
 
-@full
 def test_layered_full():
     torch = need_gpu()
     c = synth.layered_chain()
@@ -88,12 +89,15 @@ def test_layered_full():
     x_o = O.full_vector(c.n, cls_o, q, xq)
     with R.Solver(c.n, *_dev(torch, c.rowptr, c.col, c.val, c.goal)) as s:
         assert np.array_equal(s.classes(), cls_o)
+        kinv, _ = s.norm_bound("bicgstab", eps=1e-8)
         for meth, tol in (("jacobi", 1e-9), ("mixed", 1e-6), ("bicgstab", 1e-9)):
             x, info = s.solve(meth, eps=1e-13 if meth != "mixed" else 1e-11)
-            assert np.max(np.abs(x - x_o)) <= tol, meth
+            err = np.max(np.abs(x - x_o))
+            assert err <= tol, meth
+            # certified against the exact solution, which the oracle's x approximates to 1e-12
+            assert err <= info["err_bound"] + 1e-12 and info["err_bound"] <= tol, (meth, info["err_bound"])
 
 
-@full
 def test_parametric_full():
     torch = need_gpu()
     from paper_1210_6412_gb300.autograd import reach_prob
@@ -114,13 +118,12 @@ def test_parametric_full():
         assert abs(fd - g[j]) <= 1e-5 * max(abs(fd), 1e-6) + 1e-9, (j, fd, g[j])
 
 
-@full
 def test_batched_full():
     torch = need_gpu()
     bt = synth.batched_chains(sink_frac=0.02)
     n, rowptr, col, val, goals, offs = bt.concat()
     d_in = _dev(torch, rowptr, col, val, goals)
-    with R.BatchSolver(n, *d_in) as bs:
+    with R.BatchSolver(n, *d_in, chains=offs) as bs:     # per-chain stopping, as the benchmark
         cls = bs.classes()
         x, info = bs.solve(eps=1e-8)
     assert info["status"] == R.REACH_OK
