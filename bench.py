@@ -543,6 +543,7 @@ def run_workload(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             with R.BatchSolver(n, *d_in, chains=chains) as bs:
+                tune = bs.autotune() if args.batch_autotune else {}
                 x, info = bs.solve(eps=1e-8, out=torch.empty((goals.shape[0], n), dtype=torch.float64,
                                                               device="cuda"))
                 citers, _ = bs.chain_info()
@@ -556,7 +557,8 @@ def run_workload(args):
                                       "max": int(citers.max()),
                                       "row_weighted_mean": float(np.sum(citers * np.diff(offs)) / n)}
                      if chains is not None else None,
-                     "resid_inf": info["resid_inf"],
+                     "resid_inf": info["resid_inf"], "err_bound": finite_or_none(info["err_bound"]),
+                     "autotune": tune,
                      "alg_GBps": info["bytes_moved"] / info["ms_solve"] / 1e6, "wall_ms": wall})
         # the same answers from plain FP64 Jacobi, one (chain, goal set) at a time, same eps
         if args.plain:
@@ -648,6 +650,8 @@ def main():
     ap.add_argument("--chains", type=int, default=64, help="--workload batched: number of chains")
     ap.add_argument("--global-stop", action="store_true",
                     help="--workload batched: one stopping rule over the whole union instead of one per chain")
+    ap.add_argument("--batch-autotune", type=int, default=1,
+                    help="--workload batched: pick the sweep variant and refinement period by timing")
     ap.add_argument("--plain", type=int, default=1,
                     help="--workload batched: also solve every (chain, goal set) with plain FP64 Jacobi")
     args = ap.parse_args()

@@ -166,7 +166,17 @@ reach_status reach_solve(reach_ctx* ctx, int32_t method, double eps, int64_t max
                          int32_t refine_k, const double* x0, double* x_out, int32_t flags,
                          reach_info* info);
 
-/* Certified upper bound of ||(I - A)^-1||_inf for the current chain system (§2.3), for the
+/* The system over S? that reach_precompute extracted (§2.3), for callers that split it
+ * (e.g. over several GPUs with the row blocks below): n_q and m_q (host, may be NULL), A
+ * off-diagonal in CSR (rowptr int64[n_q+1], col int32[m_q] in [0, n_q), val float64[m_q];
+ * rows and columns in ascending state order), d = 1 - A_ii float64[n_q], b float64[n_q] and
+ * state int64[n_q] (the state of each row).  Any array pointer may be NULL (not written);
+ * call with NULL arrays first to read the sizes.  Arrays per flags.  Synchronises the
+ * stream. */
+reach_status reach_get_system(reach_ctx* ctx, int64_t* n_q, int64_t* m_q, int64_t* rowptr, int32_t* col,
+                              double* val, double* d, double* b, int64_t* state, int32_t flags);
+
+/* Certified upper bound of ||(I - A)^-1||_inf for the current chain system (§2.3), for the/* Certified upper bound of ||(I - A)^-1||_inf for the current chain system (§2.3), for the
  * error bound of every later reach_solve.  Solves (I - A) tau = 1 -- tau_s is the expected
  * number of steps a walk from s spends in S? -- with `method` (JACOBI_FP64, JACOBI_MIXED or
  * BICGSTAB_FP64; eps and max_iter as in reach_solve; refinement period 16), then checks the
@@ -277,11 +287,27 @@ reach_status reach_batch_get_classes(reach_batch* b, uint8_t* cls, int32_t flags
  * S=1_j and 0 on S=0_j.  Stops when the largest FP64 Jacobi step over all S?_j is
  * below eps -- per chain once reach_batch_set_chains has named the chains; info->iters
  * is then the sweep count of the slowest chain and info->last_delta the largest last
- * step.  x_out: float64[k * n], goal-set major.  Synchronises the stream. */
+ * step; info->err_bound is +inf (no norm bound per goal set is computed for a batch).
+ * x_out: float64[k * n], goal-set major.  Synchronises the stream. */
 reach_status reach_batch_solve(reach_batch* b, double eps, int64_t max_iter, int32_t refine_k,
                                double* x_out, int32_t flags, reach_info* info);
 
-/* The chains of a batch whose matrix is the block-diagonal union of independent chains:
+/* Autotuner of the batched solve (after reach_batch_precompute): times every variant of
+ * the FP32 multi-RHS sweep on this batch -- 0: two lanes per row, each gathering four
+ * right-hand sides as one 16-byte load (the default); 1: eight lanes per row, one
+ * right-hand side each; 2: as 0 with the gathers of the corrections marked evict-last
+ * in L2 (the matrix and the streamed vectors are evict-first); 3: as 0 with the index
+ * and value loads of a row's next four entries issued before the current gathers
+ * complete; 4: 2 and 3 together -- for a few launches each and keeps the fastest.  Then
+ * it times one FP64 residual step c and picks the refinement period
+ * k = sqrt(2 N c / t) for N = 500 sweeps and sweep time t (even, in [8, 62]), used by
+ * reach_batch_solve when it gets refine_k = 0.  Setting REACH_AUTOTUNE=1 in the
+ * environment makes the first reach_batch_solve run it.  Outputs (host, may be NULL): the
+ * variant, its time per sweep in ms, the period.  The rows a chain solve visits and its
+ * results do not depend on the variant; only the summation order of the sweeps does. */
+reach_status reach_batch_autotune(reach_batch* b, int32_t* variant, double* sweep_ms, int32_t* refine_k);
+
+/* The chains of a batch whose matrix is the block-diagonal union of independent chains:/* The chains of a batch whose matrix is the block-diagonal union of independent chains:
  * chain c owns states [offsets[c], offsets[c+1]) and no positive entry of P leaves it.
  * With chains set, reach_batch_solve applies its stopping rule to each chain on its own
  * (the largest FP64 Jacobi step over the chain's S?_j, all goal sets): a chain that
@@ -300,6 +326,59 @@ reach_status reach_batch_chain_info(reach_batch* b, int64_t* iters, double* last
 
 /* Release the batch.  NULL is a no-op. */
 void reach_batch_destroy(reach_batch* b);
+
+/* ---- Row blocks for a solve spread over several GPUs -------------------------------
+ * The related work of §8 runs Jacobi on two GPUs and its future work is a multi-GPU
+ * BiCGStab; both split the rows of (I - A) x = b (§2.3).  A row block is one process's
+ * share on its own GPU: rows [r0, r1) of A (off-diagonal entries) with d = 1 - A_ii and b,
+ * its columns renumbered so that the block's own rows are columns [0, n_rows) and every
+ * other column it references (its halo) is a column in [n_rows, n_rows + n_halo).  A vector
+ * that a product reads is EXTENDED: n_rows own entries followed by n_halo halo entries.
+ * The caller exchanges own entries between the processes (e.g. an NCCL all-gather into a
+ * "gathered" vector) and reach_block_halo fills the halo entries from it:
+ * halo entry j = gathered[halo_src[j]].  The caller also reduces the scalars each call
+ * returns (sums of dot products, maxima) over the processes.  Every call below runs
+ * asynchronously on the block's stream; vectors and scalar outputs are device memory. */
+typedef struct reach_block reach_block;
+
+/* rowptr int64[n_rows+1] (rowptr[0] = 0), col int32[m] in [0, n_rows + n_halo), val
+ * float64[m] = A_ij (i != j), d float64[n_rows] (non-zero), b float64[n_rows],
+ * halo_src int64[n_halo] in [0, gathered_len).  Pointers per flags; copied. */
+reach_status reach_block_create(reach_block** out, int64_t n_rows, int64_t n_halo, const int64_t* rowptr,
+                                const int32_t* col, const double* val, const double* d, const double* b,
+                                const int64_t* halo_src, int64_t gathered_len, int32_t flags, void* stream);
+
+/* x_ext[n_rows + j] = gathered[halo_src[j]] for every halo entry j. */
+reach_status reach_block_halo(reach_block* blk, const double* gathered, double* x_ext);
+
+/* One Jacobi sweep (§3.1) of the block: x_new_i = (b_i + sum_j A_ij x_ext_j) / d_i for its
+ * rows (on the Jacobi form A_ij / d_i, b_i / d_i), and *delta = max_i |x_new_i - x_ext_i|
+ * over them (one double, device). */
+reach_status reach_block_jacobi(reach_block* blk, const double* x_ext, double* x_new, double* delta);
+
+/* y = (I - A) u on the block's rows: y_i = d_i u_ext_i - sum_j A_ij u_ext_j.  With w (not
+ * NULL): *dot = sum_i w_i y_i over the block's rows (the local part of a dot product). */
+reach_status reach_block_matvec(reach_block* blk, const double* u_ext, double* y, const double* w, double* dot);
+
+/* out[0] = u . v over the block's rows, and out[1] = u . w when w is not NULL. */
+reach_status reach_block_dot(reach_block* blk, const double* u, const double* v, const double* w, double* out);
+
+/* The vector updates of one BiCGStab iteration (§3.2) on the block's rows:
+ *   REACH_BLOCK_P:  p = r + beta (p - omega v)
+ *   REACH_BLOCK_S:  s = r - alpha v, *out = max_i |s_i|
+ *   REACH_BLOCK_XR: x += alpha p + omega s, r = s - omega t, *out = max_i |r_i|
+ *   REACH_BLOCK_XP: x += alpha p (the last step when max|s| met the stopping rule)
+ * Arguments a stage does not use may be NULL. */
+enum { REACH_BLOCK_P = 0, REACH_BLOCK_S = 1, REACH_BLOCK_XR = 2, REACH_BLOCK_XP = 3 };
+reach_status reach_block_bicgstab_update(reach_block* blk, int32_t stage, double alpha, double beta, double omega,
+                                         double* x, double* r, double* p, const double* v, double* s,
+                                         const double* t, double* out);
+
+/* Last error of the block's calls.  NULL: "". */
+const char* reach_block_last_error(const reach_block* blk);
+
+/* Release the block.  NULL is a no-op. */
+void reach_block_destroy(reach_block* blk);
 
 /* ---- Allocation-free Jacobi solve ----------------------------------------------------
  * The paper has no counterpart: this entry point exists for callers that cannot call

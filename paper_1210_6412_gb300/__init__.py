@@ -28,7 +28,7 @@ __all__ = [
     "reach_param_probs", "reach_param_grad_theta", "reach_last_error", "reach_destroy",
     "reach_version", "Solver", "reach_batch_create", "reach_batch_precompute",
     "reach_batch_get_classes", "reach_batch_solve", "reach_batch_destroy", "BatchSolver",
-    "reach_batch_set_chains", "reach_batch_chain_info", "reach_norm_bound",
+    "reach_batch_set_chains", "reach_batch_chain_info", "reach_norm_bound", "reach_batch_autotune",
 ]
 
 REACH_OK, REACH_EINVAL, REACH_ENOMEM, REACH_ECUDA, REACH_ESTATE = 0, 1, 2, 3, 4
@@ -37,6 +37,7 @@ REACH_HOST, REACH_DEVICE = 0, 1
 REACH_PROB01, REACH_PROB0_ONLY = 0, 1
 REACH_JACOBI_FP64, REACH_JACOBI_MIXED, REACH_BICGSTAB_FP64, REACH_JACOBI_SEG = 0, 1, 2, 3
 REACH_SCC_JACOBI = 4
+REACH_BLOCK_P, REACH_BLOCK_S, REACH_BLOCK_XR, REACH_BLOCK_XP = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENOTCONV",
                 6: "EBREAKDOWN", 7: "ETIMEOUT"}
@@ -96,11 +97,21 @@ _SIGS = {
     "reach_batch_destroy": (None, [_P]),
     "reach_batch_set_chains": (_I32, [_P, _I32, _P]),
     "reach_batch_chain_info": (_I32, [_P, _P, _P]),
+    "reach_batch_autotune": (_I32, [_P, C.POINTER(_I32), C.POINTER(_D), C.POINTER(_I32)]),
     "reach_autotune": (_I32, [_P, _I32, C.POINTER(_I32), C.POINTER(_D), C.POINTER(_I32)]),
     "reach_system_create": (_I32, [C.POINTER(_P), _I64, _I64, _P, _P, _P, _P, _I32, _P]),
     "reach_time_kernel": (_I32, [_P, _I32, _I32, C.POINTER(_D)]),
     "reach_scc": (_I32, [_P, _P, _P, _I32, _I32, C.POINTER(ReachSccInfo)]),
     "reach_norm_bound": (_I32, [_P, _I32, _D, _I64, C.POINTER(_D), C.POINTER(ReachInfo)]),
+    "reach_get_system": (_I32, [_P, C.POINTER(_I64), C.POINTER(_I64), _P, _P, _P, _P, _P, _P, _I32]),
+    "reach_block_create": (_I32, [C.POINTER(_P), _I64, _I64, _P, _P, _P, _P, _P, _P, _I64, _I32, _P]),
+    "reach_block_halo": (_I32, [_P, _P, _P]),
+    "reach_block_jacobi": (_I32, [_P, _P, _P, _P]),
+    "reach_block_matvec": (_I32, [_P, _P, _P, _P, _P]),
+    "reach_block_dot": (_I32, [_P, _P, _P, _P, _P]),
+    "reach_block_bicgstab_update": (_I32, [_P, _I32, _D, _D, _D, _P, _P, _P, _P, _P, _P, _P]),
+    "reach_block_last_error": (C.c_char_p, [_P]),
+    "reach_block_destroy": (None, [_P]),
     "reach_jacobi_solve_noalloc": (_I32, [_I64, _P, _P, _P, _P, _P, _D, _I64, _I32, _P,
                                           C.POINTER(_I64), C.POINTER(_D), _P]),
 }
@@ -464,6 +475,13 @@ def reach_batch_chain_info(b, n_chains):
     return iters, last
 
 
+def reach_batch_autotune(b):
+    """Pick the batched sweep variant and refinement period by timing them on this batch."""
+    v, ms, k = C.c_int32(0), C.c_double(0.0), C.c_int32(0)
+    _check(lib().reach_batch_autotune(b, C.byref(v), C.byref(ms), C.byref(k)), None, "reach_batch_autotune")
+    return {"variant": v.value, "sweep_ms": ms.value, "refine_k": k.value}
+
+
 def reach_batch_destroy(b):
     if b:
         lib().reach_batch_destroy(b)
@@ -488,6 +506,9 @@ class BatchSolver:
 
     def chain_info(self):
         return reach_batch_chain_info(self.b, self.n_chains)
+
+    def autotune(self):
+        return reach_batch_autotune(self.b)
 
     def classes(self, out=None):
         return reach_batch_get_classes(self.b, self.n, self.k, out)

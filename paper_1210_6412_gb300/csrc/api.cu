@@ -503,6 +503,27 @@ reach_status reach_solve(reach_ctx* c, int32_t method, double eps, int64_t max_i
   return (reach_status)hs.status;
 }
 
+reach_status reach_get_system(reach_ctx* c, int64_t* n_q, int64_t* m_q, int64_t* rowptr, int32_t* col, double* val,
+                              double* d, double* b, int64_t* state, int32_t flags) {
+  if (!c) return fail(nullptr, REACH_EINVAL, "reach_get_system: NULL context");
+  if (!c->have_classes) return fail(c, REACH_ESTATE, "reach_get_system: call reach_precompute first");
+  if (flags != REACH_HOST && flags != REACH_DEVICE) return fail(c, REACH_EINVAL, "reach_get_system: bad flags");
+  if (n_q) *n_q = c->n_q;
+  if (m_q) *m_q = c->m_q;
+  cudaStream_t s = c->stream;
+  const cudaMemcpyKind k = kind_from_dev(flags);
+  cudaError_t e = cudaSuccess;
+  const int64_t nq = c->n_q, mq = c->m_q;
+  if (rowptr) e = cudaMemcpyAsync(rowptr, c->a_rowptr, sizeof(int64_t) * (nq + 1), k, s);
+  if (e == cudaSuccess && col && mq > 0) e = cudaMemcpyAsync(col, c->a_col, sizeof(int32_t) * mq, k, s);
+  if (e == cudaSuccess && val && mq > 0) e = cudaMemcpyAsync(val, c->a_val, sizeof(double) * mq, k, s);
+  if (e == cudaSuccess && d && nq > 0) e = cudaMemcpyAsync(d, c->d, sizeof(double) * nq, k, s);
+  if (e == cudaSuccess && b && nq > 0) e = cudaMemcpyAsync(b, c->b, sizeof(double) * nq, k, s);
+  if (e == cudaSuccess && state && nq > 0) e = cudaMemcpyAsync(state, c->qstate, sizeof(int64_t) * nq, k, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? REACH_OK : cuda_fail(c, e, "reach_get_system");
+}
+
 reach_status reach_norm_bound(reach_ctx* c, int32_t method, double eps, int64_t max_iter, double* kinv,
                               reach_info* info) {
   if (!c) return fail(nullptr, REACH_EINVAL, "reach_norm_bound: NULL context");

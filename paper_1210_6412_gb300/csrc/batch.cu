@@ -7,8 +7,11 @@
 // with x_j fixed to 1 on S=1_j and 0 on S=0_j, which is the system of §2.3 for each j
 // (b enters through the fixed ones).  It runs as FP32 sweeps with an FP64 residual and
 // correction every k sweeps, all inside one conditional-while CUDA graph.
+#include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -43,7 +46,8 @@ struct reach_batch {
   double* clast = nullptr;     // per chain: last FP64 Jacobi step
   int64_t* citer = nullptr;    // per chain: sweeps at which it stopped (-1: not yet)
   double* work = nullptr;      // rows and entries processed: residual steps, then sweeps
-  bool quad_lanes = true;      // FP32 sweep with two lanes per row (k_bsweep_q; else k_bsweep)
+  int sweep_variant = 0;       // FP32 sweep: BSW_Q (default), BSW_LANES8, BSW_Q_HINT, BSW_Q_PIPE, BSW_Q_HINT_PIPE
+  int tuned_k = 0;             // refinement period from reach_batch_autotune (0 = none)
   cudaGraphExec_t g_exec[3] = {nullptr, nullptr, nullptr};
   int64_t g_key[3] = {-1, -1, -1};
   int64_t passes[2] = {0, 0};
@@ -52,6 +56,8 @@ struct reach_batch {
 namespace reach {
 
 constexpr int BT = 256;
+// FP32 sweep variants of the batch (autotuner candidates)
+enum { BSW_Q = 0, BSW_LANES8 = 1, BSW_Q_HINT = 2, BSW_Q_PIPE = 3, BSW_Q_HINT_PIPE = 4, BSW_COUNT = 5 };
 
 __global__ void k_goal_bits(int64_t n, int k, const uint8_t* __restrict__ goals, uint8_t* __restrict__ g) {
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
@@ -327,8 +333,33 @@ __global__ void __launch_bounds__(BT) k_bsweep(ChainList L, const int64_t* __res
   }
 }
 
+// L2 policy for the gathers of D: evict-last, so that the gathered D of the chains in the
+// window outlives the matrix, R and D' streams (those are loaded and stored evict-first).
+RDEV uint64_t l2_evict_last_policy() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+template <bool HINT>
+RDEV float4 gather4(const float* p, uint64_t pol) {
+  if constexpr (HINT) {
+    float4 r;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+        : "l"(p), "l"(pol));
+    return r;
+  } else {
+    return __ldg(reinterpret_cast<const float4*>(p));
+  }
+}
+
 // The same sweep with two lanes per row: lane h owns the right-hand sides 4h .. 4h+3 and
 // gathers them as one 16-byte load per entry, so a warp has 16 rows in flight instead of 4.
+// HINT: the gathers carry the evict-last L2 policy.  PIPE: the index and value loads of a
+// row's next trip of four entries are issued before this trip's gathers complete, so the
+// two dependent memory round trips of a trip overlap with the previous trip's.
+template <bool HINT, bool PIPE>
 __global__ void __launch_bounds__(BT) k_bsweep_q(ChainList L, const int64_t* __restrict__ rp,
                                                  const int32_t* __restrict__ ci, const float* __restrict__ ah,
                                                  const uint8_t* __restrict__ sq, const float* __restrict__ R,
@@ -341,6 +372,7 @@ __global__ void __launch_bounds__(BT) k_bsweep_q(ChainList L, const int64_t* __r
   const int64_t nw = (int64_t)gridDim.x * (BT / 32);
   const int32_t nl = (int32_t)L.hdr[0];
   const int64_t nch = L.hdr[1];
+  const uint64_t pol = HINT ? l2_evict_last_policy() : 0ull;
   ChunkWalk walk;
   for (int64_t q = (int64_t)blockIdx.x * (BT / 32) + (threadIdx.x >> 5); q < nch; q += nw) {
     int64_t r0, r1;
@@ -349,30 +381,38 @@ __global__ void __launch_bounds__(BT) k_bsweep_q(ChainList L, const int64_t* __r
     for (int64_t s = r0 + grp; s < r1; s += 16) {
       const int64_t hi = rp[s + 1];
       float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-      for (int64_t k = rp[s]; k < hi; k += 4) {
-        int32_t cc[4];
-        float v[4];
+      int32_t cc[4];
+      float v[4];
+      auto load = [&](int64_t k) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const bool ok = k + u < hi;
           cc[u] = ok ? __ldcs(ci + k + u) : 0;
           v[u] = ok ? __ldcs(ah + k + u) : 0.0f;
         }
+      };
+      int64_t k = rp[s];
+      if (PIPE) load(k);
+      for (; k < hi; k += 4) {
+        if (!PIPE) load(k);
         float4 g[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          g[u] = k + u < hi ? __ldg(reinterpret_cast<const float4*>(Din + (int64_t)cc[u] * 8 + 4 * h))
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
+          g[u] = k + u < hi ? gather4<HINT>(Din + (int64_t)cc[u] * 8 + 4 * h, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float vv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) vv[u] = v[u];
+        if (PIPE) load(k + 4);     // slots past the row end load nothing
 #pragma unroll
         for (int u = 0; u < 4; u += 2) {
-          a.x = fmaf(v[u], g[u].x, a.x);
-          a.y = fmaf(v[u], g[u].y, a.y);
-          a.z = fmaf(v[u], g[u].z, a.z);
-          a.w = fmaf(v[u], g[u].w, a.w);
-          b.x = fmaf(v[u + 1], g[u + 1].x, b.x);
-          b.y = fmaf(v[u + 1], g[u + 1].y, b.y);
-          b.z = fmaf(v[u + 1], g[u + 1].z, b.z);
-          b.w = fmaf(v[u + 1], g[u + 1].w, b.w);
+          a.x = fmaf(vv[u], g[u].x, a.x);
+          a.y = fmaf(vv[u], g[u].y, a.y);
+          a.z = fmaf(vv[u], g[u].z, a.z);
+          a.w = fmaf(vv[u], g[u].w, a.w);
+          b.x = fmaf(vv[u + 1], g[u + 1].x, b.x);
+          b.y = fmaf(vv[u + 1], g[u + 1].y, b.y);
+          b.z = fmaf(vv[u + 1], g[u + 1].z, b.z);
+          b.w = fmaf(vv[u + 1], g[u + 1].w, b.w);
         }
       }
       const unsigned m = sq[s] >> (4 * h);
@@ -586,15 +626,28 @@ static void l_bresid(reach_batch* b, bool report, cudaStream_t s) {
   }
 }
 
+template <bool HINT, bool PIPE>
+static void l_bsweep_q(reach_batch* b, const float* din, float* dout, cudaStream_t s) {
+  reach_ctx* c = b->base;
+  const void* fn = (const void*)k_bsweep_q<HINT, PIPE>;
+  k_bsweep_q<HINT, PIPE><<<chunk_grid(b, fn), BT, 0, s>>>(chain_list(b, 1), c->a_rowptr, c->a_col, c->a_hi, b->sq,
+                                                          b->R, din, dout, c->st);
+}
+
+// The FP32 sweep in the batch's variant (BSW_*): eight lanes per row, or two lanes per row
+// with or without the evict-last gathers and the pipelined trips.
 static void l_bsweep(reach_batch* b, const float* din, float* dout, cudaStream_t s) {
   reach_ctx* c = b->base;
-  if (b->quad_lanes) {
-    k_bsweep_q<<<chunk_grid(b, (const void*)k_bsweep_q), BT, 0, s>>>(chain_list(b, 1), c->a_rowptr, c->a_col,
-                                                                     c->a_hi, b->sq, b->R, din, dout, c->st);
-    return;
+  switch (b->sweep_variant) {
+    case BSW_LANES8:
+      k_bsweep<<<chunk_grid(b, (const void*)k_bsweep), BT, 0, s>>>(chain_list(b, 1), c->a_rowptr, c->a_col,
+                                                                   c->a_hi, b->sq, b->R, din, dout, c->st);
+      break;
+    case BSW_Q_HINT: l_bsweep_q<true, false>(b, din, dout, s); break;
+    case BSW_Q_PIPE: l_bsweep_q<false, true>(b, din, dout, s); break;
+    case BSW_Q_HINT_PIPE: l_bsweep_q<true, true>(b, din, dout, s); break;
+    default: l_bsweep_q<false, false>(b, din, dout, s); break;
   }
-  k_bsweep<<<chunk_grid(b, (const void*)k_bsweep), BT, 0, s>>>(chain_list(b, 1), c->a_rowptr, c->a_col, c->a_hi,
-                                                               b->sq, b->R, din, dout, c->st);
 }
 
 // Chain membership check: every positive entry of row s stays inside the chain of s.
@@ -812,8 +865,13 @@ reach_status reach_batch_create(reach_batch** out, int64_t n, int64_t m, const i
   reach_batch* b = new reach_batch();
   b->base = base;
   b->k = k;
-  // REACH_BSWEEP_LANES=8 selects the sweep with one lane per right-hand side
-  if (const char* v = std::getenv("REACH_BSWEEP_LANES")) b->quad_lanes = v[0] != '8';
+  // REACH_BSWEEP_LANES=8 selects the sweep with one lane per right-hand side;
+  // REACH_BSWEEP_VARIANT=0..4 any variant (BSW_*)
+  if (const char* v = std::getenv("REACH_BSWEEP_LANES")) b->sweep_variant = v[0] == '8' ? BSW_LANES8 : BSW_Q;
+  if (const char* v = std::getenv("REACH_BSWEEP_VARIANT")) {
+    const int x = std::atoi(v);
+    if (x >= 0 && x < BSW_COUNT) b->sweep_variant = x;
+  }
   cudaStream_t s = base->stream;
   cudaError_t e;
   uint8_t* gdev = nullptr;
@@ -974,6 +1032,67 @@ reach_status reach_batch_get_classes(reach_batch* b, uint8_t* cls, int32_t flags
   return e == cudaSuccess ? REACH_OK : bcuda(b, e, "reach_batch_get_classes");
 }
 
+reach_status reach_batch_autotune(reach_batch* b, int32_t* variant, double* sweep_ms, int32_t* refine_k) {
+  if (!b) return bfail(nullptr, REACH_EINVAL, "reach_batch_autotune: NULL batch");
+  if (!b->have_classes) return bfail(b, REACH_ESTATE, "reach_batch_autotune: call reach_batch_precompute first");
+  if (b->n_chains < 1 || !b->lid[0]) return bfail(b, REACH_ESTATE, "reach_batch_autotune: no chain lists");
+  reach_ctx* c = b->base;
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n;
+  const int32_t nc = b->n_chains;
+  // a fresh state: every chain active, nothing done, finite vectors
+  cudaError_t e = cudaMemsetAsync(c->st, 0, sizeof(SolveState), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->lid[1], b->lid[0], (size_t)nc * 4, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->lpre[1], b->lpre[0], (size_t)(nc + 1) * 8, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->lhdr + 2, b->lhdr, 2 * 8, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->R, 0, sizeof(float) * (size_t)n * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->D[0], 0, sizeof(float) * (size_t)n * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->D[1], 0, sizeof(float) * (size_t)n * 8, s);
+  if (e != cudaSuccess) return bcuda(b, e, "reach_batch_autotune");
+  k_batch_init_x<<<grid_for(c, (const void*)k_batch_init_x, BT, n * 8), BT, 0, s>>>(n, b->one, b->X);
+  auto time_it = [&](const std::function<void()>& launch, int reps, float* avg) -> cudaError_t {
+    launch();  // warm-up
+    cudaError_t te = cudaEventRecord(c->ev0, s);
+    for (int r = 0; r < reps && te == cudaSuccess; ++r) launch();
+    if (te == cudaSuccess) te = cudaEventRecord(c->ev1, s);
+    if (te == cudaSuccess) te = cudaEventSynchronize(c->ev1);
+    float ms = 0.f;
+    if (te == cudaSuccess) te = cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    if (te == cudaSuccess) te = cudaGetLastError();
+    *avg = ms / (float)reps;
+    return te;
+  };
+  int best = BSW_Q;
+  float best_ms = 0.f;
+  for (int v = 0; v < BSW_COUNT && e == cudaSuccess; ++v) {
+    b->sweep_variant = v;
+    float ms = 0.f;
+    e = time_it([&] { l_bsweep(b, b->D[0], b->D[1], s); }, 3, &ms);
+    if (e == cudaSuccess && (v == 0 || ms < best_ms)) {
+      best = v;
+      best_ms = ms;
+    }
+  }
+  b->sweep_variant = best;
+  // the FP64 residual step, for the refinement period
+  float resid_ms = 0.f;
+  if (e == cudaSuccess) e = time_it([&] { l_bresid(b, false, s); }, 2, &resid_ms);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->cmax, 0, (size_t)nc * 8, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bcuda(b, e, "reach_batch_autotune");
+  // N sweeps cost N t + (N / k) c for the residual steps plus about k / 2 sweeps that a
+  // chain runs past its stopping point (it stops only at a check): k = sqrt(2 N c / t),
+  // N = 500 (the sweep count of the batched chains here), even, in [8, 62]
+  const double k_opt = std::sqrt(2.0 * 500.0 * (double)resid_ms / std::max((double)best_ms, 1e-6));
+  int k = (int)std::lround(k_opt / 2.0) * 2;
+  k = std::min(62, std::max(8, k));
+  b->tuned_k = k;
+  if (variant) *variant = best;
+  if (sweep_ms) *sweep_ms = best_ms;
+  if (refine_k) *refine_k = k;
+  return REACH_OK;
+}
+
 reach_status reach_batch_solve(reach_batch* b, double eps, int64_t max_iter, int32_t refine_k,
                                double* x_out, int32_t flags, reach_info* info) {
   if (!b) return bfail(nullptr, REACH_EINVAL, "reach_batch_solve: NULL batch");
@@ -982,9 +1101,15 @@ reach_status reach_batch_solve(reach_batch* b, double eps, int64_t max_iter, int
   if (!(eps > 0.0) || max_iter < 1) return bfail(b, REACH_EINVAL, "reach_batch_solve: bad eps or max_iter");
   // default period 32: the FP64 residual costs about five FP32 sweeps here, and longer
   // periods barely change the sweep count
-  if (refine_k == 0) refine_k = 32;
+  if (refine_k == 0) refine_k = b->tuned_k > 0 ? b->tuned_k : 32;
   if (refine_k < 2 || refine_k > 62 || (refine_k & 1))
     return bfail(b, REACH_EINVAL, "reach_batch_solve: refine_k must be even in [2, 62]");
+  if (b->tuned_k == 0 && std::getenv("REACH_AUTOTUNE") && std::getenv("REACH_AUTOTUNE")[0] == '1') {
+    int32_t v = 0, kk = 0;
+    double ms = 0.0;
+    const reach_status ts = reach_batch_autotune(b, &v, &ms, &kk);
+    if (ts != REACH_OK) return ts;
+  }
   if (!x_out || (flags != REACH_HOST && flags != REACH_DEVICE))
     return bfail(b, REACH_EINVAL, "reach_batch_solve: bad output");
   reach_ctx* c = b->base;
@@ -1015,7 +1140,8 @@ reach_status reach_batch_solve(reach_batch* b, double eps, int64_t max_iter, int
   if (e == cudaSuccess) e = cudaEventRecord(c->ev0, s);
   if (e == cudaSuccess) {
     // the graph holds the chain-list pointers: set_chains drops it when they change
-    const int64_t key = ((n * 1000003LL + c->m_q) * 64 + kref) * 1000003LL + b->chunks_all * 31 + nc;
+    const int64_t key = (((n * 1000003LL + c->m_q) * 64 + kref) * 1000003LL + b->chunks_all * 31 + nc) * 8 +
+                        b->sweep_variant;
     e = run_loop(c, b->g_exec[2], b->g_key[2], key, [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
       l_bresid(b, false, cs);
       k_bchain_ctl<<<1, CTL_NT, 0, cs>>>(c->st, b->lhdr + 2, b->lid[1], b->lpre[1], b->coff, c->a_rowptr, b->cmax,
@@ -1063,6 +1189,7 @@ reach_status reach_batch_solve(reach_batch* b, double eps, int64_t max_iter, int
                         work[2] / (double)(kref - 1) * 160.0;
     info->status = hs.status;
     info->refinements = hs.refinements;
+    info->err_bound = INFINITY;   // no norm bound per goal set is computed for batches
   }
   if (hs.status != REACH_OK) bfail(b, REACH_ENOTCONV, "reach_batch_solve: max_iter reached before the stopping rule held");
   return (reach_status)hs.status;

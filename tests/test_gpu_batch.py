@@ -196,3 +196,34 @@ def test_set_chains_rejects_bad_offsets(mixed_speed):
         # the batch is unchanged: still one chain
         x1, i1 = bs.solve(eps=1e-9)
     assert np.array_equal(x0, x1) and i0["iters"] == i1["iters"]
+
+
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3", "4"])
+def test_every_sweep_variant_matches_oracle(batch, variant, monkeypatch):
+    """The five FP32 sweep variants (autotuner candidates); 0, 2, 3 and 4 run the same FMAs
+    in the same order, so their x is bit-identical."""
+    need_gpu()
+    n, rowptr, col, val, goals, offs = batch.concat()
+    cls_o, x_o = _oracle(batch, O.PROB01)
+    monkeypatch.setenv("REACH_BSWEEP_VARIANT", variant)
+    with R.BatchSolver(n, rowptr, col, val, goals, chains=offs) as bs:
+        x, info = bs.solve(eps=1e-9)
+    monkeypatch.setenv("REACH_BSWEEP_VARIANT", "0")
+    with R.BatchSolver(n, rowptr, col, val, goals, chains=offs) as bs:
+        x0, _ = bs.solve(eps=1e-9)
+    assert np.max(np.abs(x - x_o)) <= TOL_MIXED
+    if variant != "1":
+        assert np.array_equal(x, x0)
+
+
+def test_batch_autotune_picks_a_variant_and_period(batch):
+    need_gpu()
+    n, rowptr, col, val, goals, offs = batch.concat()
+    cls_o, x_o = _oracle(batch, O.PROB01)
+    with R.BatchSolver(n, rowptr, col, val, goals, chains=offs) as bs:
+        t = bs.autotune()
+        assert t["variant"] in range(5) and t["sweep_ms"] > 0
+        assert 8 <= t["refine_k"] <= 62 and t["refine_k"] % 2 == 0
+        x, info = bs.solve(eps=1e-9)
+    assert info["status"] == R.REACH_OK
+    assert np.max(np.abs(x - x_o)) <= TOL_MIXED
