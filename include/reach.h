@@ -161,7 +161,13 @@ reach_status reach_get_classes(reach_ctx* ctx, uint8_t* cls, int32_t flags);
  * refine_k (JACOBI_MIXED) >= 2 and even, 0 = default 16; x0: optional float64[n]
  * starting point (its S? entries are used; NULL = 0), same memory kind as x_out.
  * info may be NULL.  Returns REACH_ENOTCONV when max_iter ran out (x_out still
- * holds the last iterate).  Synchronises the stream. */
+ * holds the last iterate).  Synchronises the stream.
+ * Small systems (16-bit columns, fitting the shared memory of 16 SMs) run the mixed method,
+ * and FP64 Jacobi up to 10240 stored entries, as one launch on a thread-block cluster of
+ * 16 CTAs with the matrix in shared memory, the iterate exchanged through distributed
+ * shared memory and one cluster barrier per sweep; same iteration, stopping rule and
+ * iteration count.  REACH_SMALL=0 in the environment turns this off, REACH_SMALL=1 uses
+ * it for FP64 Jacobi whenever the system fits. */
 reach_status reach_solve(reach_ctx* ctx, int32_t method, double eps, int64_t max_iter,
                          int32_t refine_k, const double* x0, double* x_out, int32_t flags,
                          reach_info* info);

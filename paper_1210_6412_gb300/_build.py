@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I" + INCLUDE]
-SOURCES = ["graph.cu", "solve.cu", "api.cu", "param.cu", "batch.cu", "noalloc.cu", "segscan.cu", "scc.cu", "tma.cu", "block.cu"]
+SOURCES = ["graph.cu", "solve.cu", "api.cu", "param.cu", "batch.cu", "noalloc.cu", "segscan.cu", "scc.cu", "tma.cu", "block.cu", "small.cu"]
 
 
 def nvcc() -> str:

@@ -202,6 +202,9 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms);
 cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms);
 void launch_finalize_resid(cudaStream_t s, SolveState* st);
 
+// ---- small.cu
+bool small_system(const reach_ctx* c, int method);
+cudaError_t solve_small(reach_ctx* c, int method, int k);
 // ---- segscan.cu
 cudaError_t solve_jacobi_seg(reach_ctx* c, const double* x0q);
 cudaError_t seg_plan(reach_ctx* c);

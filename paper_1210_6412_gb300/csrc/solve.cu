@@ -1180,6 +1180,16 @@ cudaError_t solve_jacobi64(reach_ctx* c, const double* x0q, bool transposed) {
                       : Sys{nq, c->a_rowptr, c->a_col, c->a_val, c->b};
   const Lay L = transposed ? row_layout(c, -1) : layout(c, nq, c->m_q, REACH_JACOBI_FP64);
   const int k = c->tune.k;
+  if (!transposed && small_system(c, REACH_JACOBI_FP64)) {
+    // the whole iteration in one launch on a thread-block cluster (small.cu)
+    cudaError_t e = solve_small(c, REACH_JACOBI_FP64, k);
+    if (e == cudaSuccess) {
+      LAY_DISPATCH(L, l_resid, c, yr, xa, s);
+      k_finalize_resid<<<1, 1, 0, s>>>(c->st);
+      return cudaGetLastError();
+    }
+    if (e != cudaErrorNotSupported) return e;
+  }
   const int gs = transposed ? 3 : 0;
   cudaError_t e = run_loop(c, c->g_exec[gs], c->g_key[gs], shape_key(c, L, k),
                            [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
@@ -1207,6 +1217,18 @@ cudaError_t solve_mixed(reach_ctx* c, const double* x0q) {
   if (e != cudaSuccess) return e;
   if (x0q) cudaMemcpyAsync(c->x, x0q, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
   else cudaMemsetAsync(c->x, 0, sizeof(double) * nq, s);
+  if (small_system(c, REACH_JACOBI_MIXED)) {
+    // the whole iteration in one launch on a thread-block cluster (small.cu)
+    e = solve_small(c, REACH_JACOBI_MIXED, c->tune.k);
+    if (e == cudaSuccess) {
+      Sys y{nq, c->a_rowptr, c->a_col, c->a_val, c->b};
+      const Lay LR = row_layout(c, REACH_JACOBI_MIXED);
+      LAY_DISPATCH(LR, l_resid, c, y, c->x, s);
+      k_finalize_resid<<<1, 1, 0, s>>>(c->st);
+      return cudaGetLastError();
+    }
+    if (e != cudaErrorNotSupported) return e;
+  }
   k_apply<<<ew_grid(c, (const void*)k_apply, nq), NT, 0, s>>>(nq, c->x, c->xf, nullptr, c->st, 0);
   const Lay L = layout(c, nq, c->m_q, REACH_JACOBI_MIXED);
   if (L.seg && (e = seg_plan(c)) != cudaSuccess) return e;
