@@ -132,7 +132,12 @@ __global__ void k_validate(int64_t n, int64_t m, const int64_t* __restrict__ rp,
           double v = val[k];
           if (cc < 0 || (int64_t)cc >= n) e |= VERR_COL;
           // a chain needs probabilities; a general system only finite entries
-          if (general ? !(fabs(v) <= 1.7976931348623157e308) : !(v >= 0.0 && v <= 1.0)) e |= VERR_VAL;
+          // checked on the bits (integer units, not the narrow FP64 pipe): a finite value has
+          // an exponent below all ones; a probability is +-0 or a positive value up to 1.0
+          const unsigned long long ub = (unsigned long long)__double_as_longlong(v);
+          const bool bad = general ? ((ub >> 52) & 0x7ffull) == 0x7ffull
+                                   : !((ub & 0x7fffffffffffffffull) == 0ull || ub <= 0x3ff0000000000000ull);
+          if (bad) e |= VERR_VAL;
           sum += v;
         }
       }
@@ -277,21 +282,27 @@ RDEV uint32_t agg_inc(uint32_t* ctr) {
 
 RDEV bool bit_of(const uint32_t* v, int64_t s) { return (v[s >> 5] >> (s & 31)) & 1u; }
 
-// Sources: kind 0 = goal states; kind 1 = states NOT marked in `other` (S=0).
-__global__ void k_bfs_init(int64_t n, int kind, const uint8_t* __restrict__ goal,
+// Fetches the line holding *p into L2 without waiting for it.
+RDEV void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Sources: kind 0 = goal states; kind 1 = states NOT marked in `other` (S=0).  avoid_goal:
+// goal states are marked visited from the start without being sources, so the search never
+// enters them and no level has to read the goal mask (their bits mean nothing afterwards).
+__global__ void k_bfs_init(int64_t n, int kind, int avoid_goal, const uint8_t* __restrict__ goal,
                            const uint32_t* __restrict__ other, uint32_t* vis, int32_t* q0,
                            BfsState* st) {
   const int64_t words = (n + 31) >> 5;
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
        w += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t bits = 0;
+    uint32_t bits = 0, blocked = 0;
     for (int j = 0; j < 32; ++j) {
       int64_t s = w * 32 + j;
       if (s >= n) break;
       bool src = kind == 0 ? goal[s] != 0 : !bit_of(other, s);
       if (src) bits |= 1u << j;
+      else if (avoid_goal && goal[s]) blocked |= 1u << j;
     }
-    vis[w] = bits;
+    vis[w] = bits | blocked;
     int nb = __popc(bits);
     if (nb) {
       uint32_t base = atomicAdd(&st->count[0], (uint32_t)nb);
@@ -307,25 +318,30 @@ __global__ void k_bfs_level(const int64_t* __restrict__ trp, const int32_t* __re
                             int32_t* qa, int32_t* qb, BfsState* st, unsigned* ticket,
                             cudaGraphConditionalHandle h, int use_cond) {
   const int L = st->level;
-  const int cur = L & 1;
+  const int cur = L % 3, nxt = (L + 1) % 3;
   const uint32_t cnt = st->count[cur];
   if (cnt == 0) {  // the search already ended (in the cluster kernel of this body)
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
     return;
   }
-  const int32_t* qc = cur ? qb : qa;
-  int32_t* qn = cur ? qa : qb;
+  // the frontier count of level L - 1 becomes the push target of level L + 1 (the rule of
+  // the cluster kernel too, whichever kernel runs each level)
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->count[(L + 2) % 3] = 0u;
+  const int32_t* qc = (L & 1) ? qb : qa;
+  int32_t* qn = (L & 1) ? qa : qb;
   RowGroups rg = RowGroups::make<G>();
   for (int64_t i = rg.first; i < (int64_t)cnt; i += rg.stride) {
     const int32_t v = qc[i];
     const int64_t hi = trp[v + 1];
     for (int64_t k = trp[v] + rg.lane; k < hi; k += G) {
       const int32_t u = tcol[k];
-      if (avoid_goal && goal[u]) continue;
       const uint32_t bit = 1u << (u & 31);
       if (__ldcg(vis + (u >> 5)) & bit) continue;
       const uint32_t old = atomicOr(vis + (u >> 5), bit);
-      if (!(old & bit)) qn[agg_inc(&st->count[cur ^ 1])] = u;
+      if (!(old & bit)) {
+        qn[agg_inc(&st->count[nxt])] = u;
+        prefetch_l2(trp + u);   // the next level reads u's row of the reversed graph
+      }
     }
   }
   __shared__ bool last;
@@ -337,8 +353,7 @@ __global__ void k_bfs_level(const int64_t* __restrict__ trp, const int32_t* __re
   __syncthreads();
   if (last && threadIdx.x == 0) {
     __threadfence();
-    const uint32_t next = atomicAdd(&st->count[cur ^ 1], 0u);
-    st->count[cur] = 0;
+    const uint32_t next = atomicAdd(&st->count[nxt], 0u);
     st->level = L + 1;
     *ticket = 0u;
     if (use_cond) cudaGraphSetConditional(h, next > 0 ? 1u : 0u);
@@ -374,27 +389,29 @@ __global__ void __launch_bounds__(BFS_CL_NT, 1) k_bfs_cluster(const int64_t* __r
   const int lane = threadIdx.x & (G - 1);
   int L = *(volatile int32_t*)&st->level;
   for (int64_t it = 0; it < max_levels; ++it) {
-    const int cur = L & 1;
+    const int cur = L % 3, nxt = (L + 1) % 3;
     const uint32_t cnt = *(volatile uint32_t*)&st->count[cur];
     // the same values in every thread: written before the last barrier, not since
     if (cnt == 0 || (double)cnt * mean_deg > max_edges) break;
-    cl.sync();  // every thread has read cnt: count[cur] may be cleared for the level after next
-    if (tid == 0) st->count[cur] = 0u;
-    const int32_t* qc = cur ? qb : qa;
-    int32_t* qn = cur ? qa : qb;
+    // the frontier count of level L - 1, read by every thread before the last barrier
+    if (tid == 0) st->count[(L + 2) % 3] = 0u;
+    const int32_t* qc = (L & 1) ? qb : qa;
+    int32_t* qn = (L & 1) ? qa : qb;
     for (int64_t i = tid / G; i < (int64_t)cnt; i += groups) {
       const int32_t v = __ldcg(qc + i);
       const int64_t hi = trp[v + 1];
       for (int64_t k = trp[v] + lane; k < hi; k += G) {
         const int32_t u = tcol[k];
-        if (avoid_goal && goal[u]) continue;
         const uint32_t bit = 1u << (u & 31);
         // no read-before-atomic filter here: on a narrow level it would add a round trip
         const uint32_t old = atomicOr(vis + (u >> 5), bit);
-        if (!(old & bit)) __stcg(qn + agg_inc(&st->count[cur ^ 1]), u);
+        if (!(old & bit)) {
+          __stcg(qn + agg_inc(&st->count[nxt]), u);
+          prefetch_l2(trp + u);   // the next level reads u's row of the reversed graph
+        }
       }
     }
-    cl.sync();  // the next frontier is complete
+    cl.sync();  // the next frontier is complete (one barrier per level)
     ++L;
   }
   if (tid == 0) st->level = L;
@@ -503,7 +520,7 @@ cudaError_t bfs_backward(reach_ctx* c, int source_kind, bool avoid_goal) {
   cudaMemsetAsync(c->bfs, 0, sizeof(BfsState), s);
   cudaMemsetAsync(c->ticket, 0, sizeof(unsigned), s);
   int ig = grid_for(c, (const void*)k_bfs_init, 256, words);
-  k_bfs_init<<<ig, 256, 0, s>>>(n, source_kind, c->goal, other, vis, c->queue, c->bfs);
+  k_bfs_init<<<ig, 256, 0, s>>>(n, source_kind, avoid_goal ? 1 : 0, c->goal, other, vis, c->queue, c->bfs);
   const int g = pick_group(n, c->m);
   const int grid = c->sm_count * 4;
   // small frontiers run on one cluster (0: no cluster launch available, or disabled)
@@ -549,7 +566,7 @@ cudaError_t bfs_backward(reach_ctx* c, int source_kind, bool avoid_goal) {
     e = cudaMemcpyAsync(&hs, c->bfs, sizeof(hs), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
-    if (hs.count[hs.level & 1] == 0) break;
+    if (hs.count[hs.level % 3] == 0) break;
   }
   return cudaGetLastError();
 }
@@ -562,9 +579,11 @@ __global__ void k_classify(int64_t n, int mode, const uint8_t* __restrict__ goal
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
        s += (int64_t)gridDim.x * blockDim.x) {
     uint8_t k;
+    // (the S=1 search marks goal states visited without entering them: a goal is S=1)
     if (!bit_of(vis0, s)) k = CLS_S0;
+    else if (goal[s]) k = CLS_S1;
     else if (mode == REACH_PROB01) k = bit_of(vis1, s) ? CLS_SQ : CLS_S1;
-    else k = goal[s] ? CLS_S1 : CLS_SQ;
+    else k = CLS_SQ;
     cls[s] = k;
     qflag[s] = k == CLS_SQ;
   }
@@ -656,8 +675,15 @@ __global__ void k_jform(int64_t nq, const int64_t* __restrict__ rp, const double
   RowGroups rg = RowGroups::make<G>();
   for (int64_t i = rg.first; i < nq; i += rg.stride) {
     const double di = d[i];
-    for (int64_t k = rp[i] + rg.lane; k < rp[i + 1]; k += G) aj[k] = av[k] / di;
-    if (rg.lane == 0 && bj) bj[i] = b[i] / di;
+    // a row without a self-loop has d_i = 1 exactly and needs no division: on GB300 an FP64
+    // division is a long sequence on the narrow FP64 pipe (3.7x the sweep time on sparse rows)
+    if (di == 1.0) {
+      for (int64_t k = rp[i] + rg.lane; k < rp[i + 1]; k += G) aj[k] = av[k];
+      if (rg.lane == 0 && bj) bj[i] = b[i];
+    } else {
+      for (int64_t k = rp[i] + rg.lane; k < rp[i + 1]; k += G) aj[k] = av[k] / di;
+      if (rg.lane == 0 && bj) bj[i] = b[i] / di;
+    }
   }
 }
 

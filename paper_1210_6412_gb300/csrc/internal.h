@@ -47,10 +47,13 @@ struct BiState {
   int32_t skip;         // rest of this iteration is skipped (breakdown at q.v)
 };
 
+// Level-synchronous backward search: level L reads the frontier of count[L % 3] entries,
+// pushes into count[(L + 1) % 3] and may clear count[(L + 2) % 3] (the frontier of level
+// L - 1, read by everyone before the barrier that ended level L - 1), so a level needs
+// one barrier.
 struct BfsState {
   int32_t level;
-  uint32_t count[2];
-  uint32_t pad;
+  uint32_t count[3];
 };
 
 struct Tuning {

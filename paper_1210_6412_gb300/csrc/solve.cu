@@ -357,7 +357,8 @@ __global__ void __launch_bounds__(NT) k_jacobi64(int64_t nq, const int64_t* __re
 // S_i = |b_i| + |d_i x_i| + sum_j |A_ij x_j| (summed with upward rounding) and D the number
 // of roundings any term passes through in this kernel's fixed order (ceil(len / G)
 // sequential FMAs per lane, log2 G shuffle additions, then + b_i and - d_i x_i), with
-// gamma_D = D u / (1 - D u), u = 2^-53, evaluated with upward rounding.
+// gamma_D = D u / (1 - D u), u = 2^-53, bounded above by D u (1 + 2 D u) with upward
+// rounding (no division).
 
 template <int G>
 RDEV double group_sum_ru(double v) {
@@ -399,7 +400,8 @@ __global__ void __launch_bounds__(NT) k_resid_cert(int64_t nq, const int64_t* __
       const double sum_abs = __dadd_ru(__dadd_ru(a, fabs(bi)), __dmul_ru(fabs(di), fabs(xi)));
       const double depth = (double)((hi - lo + G - 1) / G + log2_of<G>() + 2);
       const double du = depth * 0x1p-53;   // exact: an integer times a power of two
-      const double gam = __ddiv_ru(du, __dadd_rd(1.0, -du));
+      // gamma = du / (1 - du) <= du (1 + 2 du) for du <= 1/2, without an FP64 division
+      const double gam = __fma_ru(2.0 * du, du, du);
       const double ub = __dadd_ru(fabs(r), __dmul_ru(gam, sum_abs));
       mr = umax64(mr, abs_bits(r));
       mu = umax64(mu, abs_bits(ub));
