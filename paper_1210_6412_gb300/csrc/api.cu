@@ -113,6 +113,7 @@ void free_system(reach_ctx* c) {
   dfree(c->x); dfree(c->x2); dfree(c->vr); dfree(c->vq); dfree(c->vp); dfree(c->vv);
   dfree(c->vs); dfree(c->vt); dfree(c->r32); dfree(c->xf); dfree(c->dl[0]); dfree(c->dl[1]);
   dfree(c->tau_save);
+  for (auto& e : c->small_ext) e[0] = e[1] = -1;
   c->kinv_varah = INFINITY;
   c->kinv_tau = INFINITY;
   c->kinv_varah_t = -1.0;

@@ -170,6 +170,9 @@ struct reach_ctx {
                                  nullptr, nullptr, nullptr, nullptr, nullptr};
   int64_t g_key[10] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
 
+  // rows and entries of the fullest CTA when the system is split over 1, 2, 4, 8, 16 CTAs
+  // (small.cu; -1 = not measured yet)
+  int64_t small_ext[5][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};
   void* seg = nullptr;      // tile plan of the entry-balanced Jacobi sweep (segscan.cu)
   void* scc = nullptr;      // components, levels and row order (scc.cu)
 };
@@ -206,7 +209,7 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms);
 void launch_finalize_resid(cudaStream_t s, SolveState* st);
 
 // ---- small.cu
-bool small_system(const reach_ctx* c, int method);
+bool small_system(reach_ctx* c, int method);
 cudaError_t solve_small(reach_ctx* c, int method, int k);
 // ---- segscan.cu
 cudaError_t solve_jacobi_seg(reach_ctx* c, const double* x0q);

@@ -34,7 +34,7 @@ namespace reach {
 namespace {
 
 constexpr int SM_NT = 512;          // threads per CTA
-constexpr int SM_CL = 16;           // CTAs of the cluster (non-portable size)
+constexpr int SM_CL = 16;           // most CTAs of the cluster (16 is a non-portable size)
 constexpr size_t SM_SMEM_MAX = 220 * 1024;   // dynamic part (the static part is below 1 KB)
 
 // Rows of CTA `rank` of `nc`: [first row whose cost reaches rank * C / nc, ...), cost(i) =
@@ -396,23 +396,33 @@ __global__ void __launch_bounds__(SM_NT, 1) k_small_mixed(int64_t nq, const int6
   cl.sync();
 }
 
-// Bytes of shared memory per CTA for a system of nq rows and m entries whose longest row
-// has L entries, split over nc CTAs by cost.
-size_t small_smem(bool mixed, int64_t nq, int64_t m, int64_t L, int nc) {
+// Largest rows and entries any CTA of an nc-CTA split gets (the kernels' own cost split).
+__global__ void k_small_extents(const int64_t* __restrict__ rp, int64_t nq, int nc, int64_t* out) {
+  if (threadIdx.x != 0) return;
+  int64_t rmax = 0, emax = 0;
+  for (int r = 0; r < nc; ++r) {
+    const int64_t a = cost_bound(rp, nq, r, nc), b = cost_bound(rp, nq, r + 1, nc);
+    rmax = b - a > rmax ? b - a : rmax;
+    emax = rp[b] - rp[a] > emax ? rp[b] - rp[a] : emax;
+  }
+  out[0] = rmax;
+  out[1] = emax;
+}
+
+// Bytes of shared memory per CTA for a system of nq rows when no CTA gets more than rcap
+// rows and ecap entries.
+size_t small_smem(bool mixed, int64_t nq, int64_t ecap, int64_t rcap) {
   auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
-  const int64_t ecap = (m + 2 * nq) / nc + L + 3;
-  const int64_t rcap = ecap / 2 + 2;
   if (mixed)
     return 2 * al(4 * nq) + al(8 * nq) + al(4 * nq) + 2 * al(4 * ecap) + al(2 * ecap) + al(4 * (rcap + 1)) +
            al(8 * rcap) + al(4 * rcap);
   return 2 * al(8 * nq) + al(8 * ecap) + al(2 * ecap) + al(4 * (rcap + 1)) + al(8 * rcap);
 }
 
-// Lanes per row: as many as let one pass of the CTA's thread groups cover its rows (about
-// nq / 16, with a margin for the uneven cost split), at most a lane per 4 entries of the
-// mean row (a lane's trip), at least 1.
-int small_lanes(int64_t nq, int64_t m) {
-  const double rows = 1.25 * (double)nq / SM_CL + 1.0;
+// Lanes per row: as many as let one pass of the CTA's thread groups cover the rows of the
+// fullest CTA, at most a lane per 4 entries of the mean row (a lane's trip), at least 1.
+int small_lanes(int64_t nq, int64_t m, int64_t max_rows) {
+  const double rows = (double)max_rows;
   const double mean = nq > 0 ? (double)m / (double)nq : 0.0;
   int g = 1;
   while (g < 32 && (double)(SM_NT / (2 * g)) >= rows && 4.0 * (2 * g) <= mean + 3.0) g *= 2;
@@ -420,19 +430,19 @@ int small_lanes(int64_t nq, int64_t m) {
 }
 
 template <typename K>
-cudaError_t launch_small(reach_ctx* c, K kernel, size_t smem, void** args) {
+cudaError_t launch_small(reach_ctx* c, K kernel, size_t smem, int nc, void** args) {
   const void* fn = (const void*)kernel;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(SM_CL);
+  cfg.gridDim = dim3(nc);
   cfg.blockDim = dim3(SM_NT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = c->stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = SM_CL;
+  at[0].val.clusterDim.x = nc;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
@@ -456,11 +466,46 @@ int small_mode() {
 }
 bool small_enabled() { return small_mode() != 0; }
 
-// Can one cluster of SM_CL CTAs hold this system (16-bit columns, shared memory)?
-bool small_fits(const reach_ctx* c, bool mixed) {
-  if (!small_enabled() || c->n_q < 1 || c->n_q > 65536) return false;
-  return small_smem(mixed, c->n_q, c->m_q, std::max<int64_t>(c->max_row, 1), SM_CL) <= SM_SMEM_MAX;
+// Rows and entries per CTA of every cluster size, measured once per system (c->small_ext,
+// cleared when the system changes).  Returns false when the measurement failed.
+bool small_extents(reach_ctx* c) {
+  if (c->small_ext[0][0] >= 0) return true;
+  int64_t* dev = reinterpret_cast<int64_t*>(c->part);
+  for (int i = 0, nc = 1; nc <= SM_CL; ++i, nc *= 2) {
+    k_small_extents<<<1, 32, 0, c->stream>>>(c->a_rowptr, c->n_q, nc, dev + 2 * i);
+  }
+  int64_t h[10];
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, dev, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  for (int i = 0; i < 5; ++i) {
+    c->small_ext[i][0] = h[2 * i];
+    c->small_ext[i][1] = h[2 * i + 1];
+  }
+  return true;
 }
+
+// CTAs of the cluster for this system: one CTA (only its own barrier) when a thread per row
+// covers the whole system, else 16, if the shared memory holds it; else 0 (no cluster:
+// 16-bit columns and 220 KB per CTA are the limits).  Measured per sweep of the mixed method:
+// 92 states 1.04 -> 0.74 us and 313 states 1.11 -> 0.91 us with one CTA instead of 16; with 2
+// to 8 CTAs the larger systems were slower than with 16 (667 states: 1.29 against 1.10 us on
+// 2 CTAs; 4096 states: 3.1 against 2.3 us on 8), the work per CTA outweighing the barrier.
+int small_cluster(reach_ctx* c, bool mixed) {
+  if (!small_enabled() || c->n_q < 1 || c->n_q > 65536) return 0;
+  if (!small_extents(c)) return 0;
+  if (c->small_ext[0][0] <= SM_NT && small_smem(mixed, c->n_q, c->small_ext[0][1], c->small_ext[0][0]) <= SM_SMEM_MAX)
+    return 1;
+  return small_smem(mixed, c->n_q, c->small_ext[4][1], c->small_ext[4][0]) <= SM_SMEM_MAX ? SM_CL : 0;
+}
+
+int small_index(int nc) { return nc >= 16 ? 4 : nc >= 8 ? 3 : nc >= 4 ? 2 : nc >= 2 ? 1 : 0; }
+
+bool small_fits(reach_ctx* c, bool mixed) { return small_cluster(c, mixed) > 0; }
 
 }  // namespace
 
@@ -472,7 +517,7 @@ bool small_fits(const reach_ctx* c, bool mixed) {
 // 2.3 against 3.3 us per sweep at 4096 / 64K, so it takes the cluster whenever it fits.
 constexpr int64_t SMALL_FP64_MAX_ENTRIES = 10240;
 
-bool small_system(const reach_ctx* c, int method) {
+bool small_system(reach_ctx* c, int method) {
   if (c->general || c->tune.g != 0) return false;   // a forced row mapping keeps the graph solvers
   if (method == REACH_JACOBI_FP64)
     return (small_mode() == 1 || c->m_q <= SMALL_FP64_MAX_ENTRIES) && small_fits(c, false);
@@ -491,20 +536,22 @@ bool small_system(const reach_ctx* c, int method) {
   }
 
 template <int G>
-static cudaError_t run_small_jacobi(reach_ctx* c, int k, cudaError_t* out) {
+static cudaError_t run_small_jacobi(reach_ctx* c, int k, int nc, cudaError_t* out) {
   int64_t nq = c->n_q;
-  const size_t smem = small_smem(false, c->n_q, c->m_q, std::max<int64_t>(c->max_row, 1), SM_CL);
+  const int i = small_index(nc);
+  const size_t smem = small_smem(false, c->n_q, c->small_ext[i][1], c->small_ext[i][0]);
   void* args[] = {&nq, &c->a_rowptr, &c->a_col, &c->a_jv, &c->bj, &c->x, &k, &c->st};
-  *out = launch_small(c, k_small_jacobi<G>, smem, args);
+  *out = launch_small(c, k_small_jacobi<G>, smem, nc, args);
   return *out;
 }
 
 template <int G>
-static cudaError_t run_small_mixed(reach_ctx* c, int k, cudaError_t* out) {
+static cudaError_t run_small_mixed(reach_ctx* c, int k, int nc, cudaError_t* out) {
   int64_t nq = c->n_q;
-  const size_t smem = small_smem(true, c->n_q, c->m_q, std::max<int64_t>(c->max_row, 1), SM_CL);
+  const int i = small_index(nc);
+  const size_t smem = small_smem(true, c->n_q, c->small_ext[i][1], c->small_ext[i][0]);
   void* args[] = {&nq, &c->a_rowptr, &c->a_col, &c->a_hi, &c->a_lo, &c->bj, &c->x, &k, &c->st};
-  *out = launch_small(c, k_small_mixed<G>, smem, args);
+  *out = launch_small(c, k_small_mixed<G>, smem, nc, args);
   return *out;
 }
 
@@ -514,11 +561,13 @@ static cudaError_t run_small_mixed(reach_ctx* c, int k, cudaError_t* out) {
 // cudaErrorNotSupported (nothing launched): the device cannot place the cluster.
 cudaError_t solve_small(reach_ctx* c, int method, int k) {
   cudaError_t e = cudaSuccess;
-  const int g = small_lanes(c->n_q, c->m_q);
+  const int nc = small_cluster(c, method == REACH_JACOBI_MIXED);
+  if (nc < 1) return cudaErrorNotSupported;
+  const int g = small_lanes(c->n_q, c->m_q, c->small_ext[small_index(nc)][0]);
   if (method == REACH_JACOBI_MIXED) {
-    SMALL_DISPATCH(g, run_small_mixed, c, k, &e);
+    SMALL_DISPATCH(g, run_small_mixed, c, k, nc, &e);
   } else {
-    SMALL_DISPATCH(g, run_small_jacobi, c, k, &e);
+    SMALL_DISPATCH(g, run_small_jacobi, c, k, nc, &e);
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   return e;
