@@ -44,8 +44,8 @@ EPS = {"jacobi": 5e-12, "mixed": 5e-12, "bicgstab": 5e-12}
 K_REFINE = 16
 # DRAM bytes (read + write) per launch of the current kernels on this workload, from one
 # ncu capture each; set back to None whenever the kernel changes, until it is captured again.
-NCU_TRAFFIC_BYTES = 1.271472e9 + 2.955776e6
-NCU_TRAFFIC_SWEEP32_BYTES = 0.633107e9 + 2.984192e6
+NCU_TRAFFIC_BYTES = 1271578368 + 3304448
+NCU_TRAFFIC_SWEEP32_BYTES = 633112320 + 2868224
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA per clock (ncu's
 # roofline reports 4 FP64 flop/clk/SM) x 2 flop x 2.07 GHz; matches the 1.25 TFLOP/s nominal.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
