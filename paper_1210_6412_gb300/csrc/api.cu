@@ -114,6 +114,7 @@ void free_system(reach_ctx* c) {
   dfree(c->vs); dfree(c->vt); dfree(c->r32); dfree(c->xf); dfree(c->dl[0]); dfree(c->dl[1]);
   dfree(c->tau_save);
   for (auto& e : c->small_ext) e[0] = e[1] = -1;
+  c->varah_key = false;
   c->kinv_varah = INFINITY;
   c->kinv_tau = INFINITY;
   c->kinv_varah_t = -1.0;
@@ -222,7 +223,7 @@ static reach_status create_common(reach_ctx** out, int64_t n, int64_t m, const i
       (e = dalloc(&c->st, 1)) != cudaSuccess || (e = dalloc(&c->bi, 1)) != cudaSuccess ||
       (e = dalloc(&c->part, part_n)) != cudaSuccess || (e = dalloc(&c->ticket, 1)) != cudaSuccess ||
       (e = dalloc(&c->verr, 1)) != cudaSuccess || (e = dalloc(&c->vrow, 1)) != cudaSuccess ||
-      (e = dalloc(&c->maxrow, 1)) != cudaSuccess || (e = dalloc(&c->keys, 2)) != cudaSuccess) {
+      (e = dalloc(&c->maxrow, 1)) != cudaSuccess || (e = dalloc(&c->keys, 3)) != cudaSuccess) {
     reach_status s = cuda_fail(nullptr, e, (w + ": allocation").c_str());
     reach_destroy(c);
     return s;
@@ -351,7 +352,7 @@ reach_status reach_precompute(reach_ctx* c, int32_t mode) {
   c->have_classes = false;
   c->have_x = false;
   cudaError_t e = cudaEventRecord(c->ev0, s);
-  if (e == cudaSuccess) e = build_reverse_pattern(c);
+  c->rev_ready = false;   // the reversed graph of P is built when a search first needs it
   if (e == cudaSuccess) e = bfs_backward(c, 0, false);
   if (e == cudaSuccess && mode == REACH_PROB01) e = bfs_backward(c, 1, true);
   if (e == cudaSuccess) e = classify_and_extract(c, mode);

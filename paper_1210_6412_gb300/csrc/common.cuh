@@ -28,6 +28,22 @@ RDEV T warp_max(T v) {
 template <typename T>
 RDEV T warp_sum(T v) { return group_sum<32>(v); }
 
+// Sum over a group of G lanes with every addition rounded upward: an upper bound of the
+// exact sum of the lanes' values.
+template <int G>
+RDEV double group_sum_ru(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = __dadd_ru(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+
+// Order-preserving map of doubles onto unsigned integers (for atomicMin / atomicMax of
+// values of either sign).
+RDEV unsigned long long ordered_key(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
 // Block-wide reduction of NV doubles (sum or max).  Result valid in thread 0.
 // `sh` needs NV * 32 doubles.  Fixed order, so the result is deterministic.
 template <int NV, bool MAX>

@@ -2,7 +2,10 @@
 // underlying digraph, backward breadth-first search for S=0 and S=1, the
 // partition, and extraction of A (off-diagonal), d = 1 - A_ii and b over S?.
 #include <algorithm>
+#include <climits>
+#include <cmath>
 #include <cstdlib>
+#include <utility>
 
 #include <cooperative_groups.h>
 
@@ -314,9 +317,8 @@ __global__ void k_bfs_init(int64_t n, int kind, int avoid_goal, const uint8_t* _
 
 template <int G>
 __global__ void k_bfs_level(const int64_t* __restrict__ trp, const int32_t* __restrict__ tcol,
-                            const uint8_t* __restrict__ goal, int avoid_goal, uint32_t* vis,
-                            int32_t* qa, int32_t* qb, BfsState* st, unsigned* ticket,
-                            cudaGraphConditionalHandle h, int use_cond) {
+                            uint32_t* vis, int32_t* qa, int32_t* qb, BfsState* st, unsigned* ticket,
+                            double mean_deg, double pull_edges, cudaGraphConditionalHandle h, int use_cond) {
   const int L = st->level;
   const int cur = L % 3, nxt = (L + 1) % 3;
   const uint32_t cnt = st->count[cur];
@@ -324,6 +326,7 @@ __global__ void k_bfs_level(const int64_t* __restrict__ trp, const int32_t* __re
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
     return;
   }
+  if ((double)cnt * mean_deg > pull_edges) return;   // a wide level: k_bfs_pull's
   // the frontier count of level L - 1 becomes the push target of level L + 1 (the rule of
   // the cluster kernel too, whichever kernel runs each level)
   if (blockIdx.x == 0 && threadIdx.x == 0) st->count[(L + 2) % 3] = 0u;
@@ -361,10 +364,173 @@ __global__ void k_bfs_level(const int64_t* __restrict__ trp, const int32_t* __re
 }
 
 template <int G>
-static void launch_level(reach_ctx* c, int grid, int avoid_goal, uint32_t* vis,
+static void launch_level(reach_ctx* c, int grid, uint32_t* vis, double pull_edges,
                          cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
-  k_bfs_level<G><<<grid, 256, 0, s>>>(c->t_rowptr, c->t_col, c->goal, avoid_goal, vis, c->queue,
-                                      c->queue + c->n, c->bfs, c->ticket, h, use_cond);
+  const double mean_deg = c->n > 0 ? std::max(1.0, (double)c->m / (double)c->n) : 1.0;
+  k_bfs_level<G><<<grid, 256, 0, s>>>(c->t_rowptr, c->t_col, vis, c->queue, c->queue + c->n, c->bfs,
+                                      c->ticket, mean_deg, pull_edges, h, use_cond);
+}
+
+// One level of the backward search computed from the other end (bottom-up): every state
+// not yet marked reads its own successors in P and is marked, and queued, if one of them
+// is marked (a blocked goal does not count).  A wide level costs one pass over the
+// unmarked states' rows, most of which stop at their first marked successor, against one
+// atomic per reversed edge of the frontier top-down; the reversed graph is not read.
+// Marks made during the pass may serve later states of the same pass: each is still a
+// path to the sources, so the search reaches the same set (§2.2), in fewer levels.
+template <int G>
+__global__ void k_bfs_pull(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, const uint8_t* __restrict__ goal, int avoid_goal,
+                           uint32_t* vis, int32_t* qa, int32_t* qb, BfsState* st, unsigned* ticket,
+                           double mean_deg, double pull_edges, int32_t level_cap,
+                           cudaGraphConditionalHandle h, int use_cond) {
+  const int L = st->level;
+  const int cur = L % 3, nxt = (L + 1) % 3;
+  const uint32_t cnt = st->count[cur];
+  if (cnt == 0) {   // no sources, or the search ended: the loop must stop here too
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
+  if (!((double)cnt * mean_deg > pull_edges)) return;   // k_bfs_level's
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->count[(L + 2) % 3] = 0u;
+  int32_t* qn = (L & 1) ? qa : qb;
+  RowGroups rg = RowGroups::make<G>();
+  const int wl = threadIdx.x & 31;
+  const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (wl & ~(G - 1)));
+  for (int64_t s = rg.first; warp_has_row<G>(s, n); s += rg.stride) {
+    bool done = true;
+    int64_t k = 0, hi = 0;
+    if (s < n && !((__ldcg(vis + (s >> 5)) >> (s & 31)) & 1u)) {
+      k = rp[s] + rg.lane;
+      hi = rp[s + 1];
+      done = false;
+    }
+    bool hit = false;
+    // G successors per trip; the group stops at its first marked one (flags equal in a group)
+    while (__any_sync(FULL, !done)) {
+      bool m = false;
+      if (!done && k < hi) {
+        const int32_t cc = col[k];
+        m = val[k] > 0.0 && ((__ldcg(vis + (cc >> 5)) >> (cc & 31)) & 1u) && !(avoid_goal && goal[cc]);
+      }
+      const unsigned b = __ballot_sync(FULL, m) & gmask;
+      const unsigned more = __ballot_sync(FULL, !done && k + G < hi) & gmask;
+      if (!done) {
+        if (b) hit = done = true;
+        else if (!more) done = true;
+      }
+      k += G;
+    }
+    if (hit && rg.lane == 0) {
+      atomicOr(vis + (s >> 5), 1u << (s & 31));
+      qn[agg_inc(&st->count[nxt])] = (int32_t)s;
+    }
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const uint32_t next = atomicAdd(&st->count[nxt], 0u);
+    st->level = L + 1;
+    *ticket = 0u;
+    if (use_cond) cudaGraphSetConditional(h, next > 0 && L + 1 < level_cap ? 1u : 0u);
+  }
+}
+
+// The same pass for short rows: each thread takes PULL_S consecutive states (one visited
+// word) and walks their rows in step, so the loads of its states go out together and a
+// warp keeps 32 * PULL_S rows in flight.
+constexpr int PULL_S = 4;
+
+__global__ void k_bfs_pull_thin(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, const uint8_t* __restrict__ goal,
+                                int avoid_goal, uint32_t* vis, int32_t* qa, int32_t* qb, BfsState* st,
+                                unsigned* ticket, double mean_deg, double pull_edges, int32_t level_cap,
+                                cudaGraphConditionalHandle h, int use_cond) {
+  const int L = st->level;
+  const int cur = L % 3, nxt = (L + 1) % 3;
+  const uint32_t cnt = st->count[cur];
+  if (cnt == 0) {   // no sources, or the search ended: the loop must stop here too
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
+  if (!((double)cnt * mean_deg > pull_edges)) return;   // k_bfs_level's
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->count[(L + 2) % 3] = 0u;
+  int32_t* qn = (L & 1) ? qa : qb;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x * PULL_S;
+  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * PULL_S; base < n; base += step) {
+    const uint32_t w = __ldcg(vis + (base >> 5));   // PULL_S divides 32: one word
+    int64_t k[PULL_S], hi[PULL_S];
+    bool live[PULL_S];
+#pragma unroll
+    for (int j = 0; j < PULL_S; ++j) {
+      const int64_t sj = base + j;
+      live[j] = sj < n && !((w >> (sj & 31)) & 1u);
+      k[j] = live[j] ? rp[sj] : 0;
+      hi[j] = live[j] ? rp[sj + 1] : 0;
+    }
+    uint32_t found = 0u;   // bits (s & 31) of the states marked by this thread
+    bool more = true;
+    while (more) {
+      int32_t cc[PULL_S];
+      bool pos[PULL_S];
+#pragma unroll
+      for (int j = 0; j < PULL_S; ++j) {
+        const bool go = live[j] && k[j] < hi[j];
+        cc[j] = go ? col[k[j]] : -1;
+        pos[j] = go && val[k[j]] > 0.0;
+      }
+      more = false;
+#pragma unroll
+      for (int j = 0; j < PULL_S; ++j) {
+        if (cc[j] >= 0) {
+          const uint32_t vw = __ldcg(vis + (cc[j] >> 5));
+          const bool blocked = avoid_goal && goal[cc[j]];
+          if (pos[j] && ((vw >> (cc[j] & 31)) & 1u) && !blocked) {
+            found |= 1u << ((base + j) & 31);
+            live[j] = false;
+          }
+          ++k[j];
+          more |= live[j] && k[j] < hi[j];
+        }
+      }
+    }
+    if (found) {
+      atomicOr(vis + (base >> 5), found);
+#pragma unroll
+      for (int j = 0; j < PULL_S; ++j)
+        if ((found >> ((base + j) & 31)) & 1u) qn[agg_inc(&st->count[nxt])] = (int32_t)(base + j);
+    }
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const uint32_t next = atomicAdd(&st->count[nxt], 0u);
+    st->level = L + 1;
+    *ticket = 0u;
+    if (use_cond) cudaGraphSetConditional(h, next > 0 && L + 1 < level_cap ? 1u : 0u);
+  }
+}
+
+template <int G>
+static void launch_pull(reach_ctx* c, int avoid_goal, uint32_t* vis, double pull_edges, int32_t level_cap,
+                        cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
+  const double mean_deg = c->n > 0 ? std::max(1.0, (double)c->m / (double)c->n) : 1.0;
+  const int grid = grid_for(c, (const void*)k_bfs_pull<G>, 256, c->n * G);
+  k_bfs_pull<G><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->col, c->val, c->goal, avoid_goal, vis, c->queue,
+                                     c->queue + c->n, c->bfs, c->ticket, mean_deg, pull_edges, level_cap,
+                                     h, use_cond);
 }
 
 // Levels with small frontiers on one thread-block cluster, many per launch: the
@@ -417,10 +583,149 @@ __global__ void __launch_bounds__(BFS_CL_NT, 1) k_bfs_cluster(const int64_t* __r
   if (tid == 0) st->level = L;
 }
 
-// Cluster size the device can host for k_bfs_cluster<G> (16, else 8, else 0 = none).
+// Entries of a reversed row that one lane of k_bfs_cluster_lq handles at a time.
+constexpr int BFS_ILP = 4;
+
+// The same level loop with the frontier held in the CTAs' shared memory.  A state found by
+// CTA r goes into r's own queue (a shared-memory counter, no atomics in global memory) and
+// r stores its queue length into a slot of every CTA before the level's barrier.  After it
+// every thread sums the same slots, and the groups of the whole cluster deal the states of
+// all queues among themselves, reading them from the owners' shared memory (a CTA that kept
+// its own states would soon hold most of the frontier: who finds a state first keeps it).
+// While a CTA waits at the barrier it loads the reversed-graph row bounds of the states it
+// found and fetches their rows into L2, so the next level mostly reads L2.  A full queue
+// spills to the global queue (the level's global counter, as in k_bfs_level), which all
+// CTAs expand next level.  On the way out to k_bfs_level the CTAs append their queues to
+// the global queue: the search state is the one k_bfs_level keeps.
 template <int G>
-static int bfs_cluster_size(reach_ctx* c) {
-  const void* fn = (const void*)k_bfs_cluster<G>;
+__global__ void __launch_bounds__(BFS_CL_NT, 1) k_bfs_cluster_lq(const int64_t* __restrict__ trp,
+                                                                 const int32_t* __restrict__ tcol, uint32_t* vis,
+                                                                 int32_t* qa, int32_t* qb, BfsState* st,
+                                                                 double mean_deg, double max_edges,
+                                                                 int64_t max_levels, uint32_t cap) {
+  extern __shared__ int32_t lq[];   // [2][cap]: the queues of even and odd levels
+  __shared__ uint32_t lcnt[2];
+  __shared__ uint32_t pub[2][16];   // [level parity][CTA]: queue lengths of every CTA
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), nb = (int)cl.num_blocks();
+  const int t = threadIdx.x, lane = t & (G - 1);
+  const int64_t ctid = (int64_t)rank * blockDim.x + t;
+  const int64_t cgroups = (int64_t)nb * blockDim.x / G;
+  if (t < 2) lcnt[t] = 0u;
+  if (t < 32) pub[t >> 4][t & 15] = 0u;
+  cl.sync();   // every slot is zero before any CTA publishes into it
+  int L = *(volatile int32_t*)&st->level;
+  uint32_t spill = 0, local_tot = 0;
+  bool wide = false;
+  for (int64_t it = 0;; ++it) {
+    const int cur = L % 3, nxt = (L + 1) % 3, p = L & 1;
+    // the same values in every thread: written before the last barrier, not since
+    spill = *(volatile uint32_t*)&st->count[cur];
+    local_tot = 0;
+    for (int r = 0; r < nb; ++r) local_tot += *(volatile uint32_t*)&pub[p][r];
+    const uint32_t tot = spill + local_tot;
+    if (tot == 0) break;
+    if (it >= max_levels || (double)tot * mean_deg > max_edges) {
+      wide = true;
+      break;
+    }
+    // the global count of level L - 1, read by every thread before the last barrier
+    if (ctid == 0) st->count[(L + 2) % 3] = 0u;
+    const int32_t* qc = (L & 1) ? qb : qa;
+    int32_t* qn = (L & 1) ? qa : qb;
+    int32_t* lc = lq + (size_t)p * cap;
+    int32_t* ln = lq + (size_t)(p ^ 1) * cap;
+    uint32_t* ncnt = &lcnt[p ^ 1];
+    for (int64_t i = ctid / G; i < (int64_t)tot; i += cgroups) {
+      int32_t v;
+      if (i < (int64_t)local_tot) {   // entry i of the CTAs' queues taken in rank order
+        uint32_t o = 0, acc = 0;
+        while ((uint32_t)i >= acc + *(volatile uint32_t*)&pub[p][o]) acc += *(volatile uint32_t*)&pub[p][o++];
+        v = *cl.map_shared_rank(lc + ((uint32_t)i - acc), o);
+      } else {
+        v = __ldcg(qc + (i - (int64_t)local_tot));
+      }
+      const int64_t lo = trp[v], hi = trp[v + 1];
+      // BFS_ILP entries per lane at a time: their loads, then their atomics, are issued
+      // together, so a long row costs about one round trip of each instead of one per entry
+      for (int64_t k0 = lo + lane; k0 < hi; k0 += (int64_t)G * BFS_ILP) {
+        int32_t u[BFS_ILP];
+        uint32_t old[BFS_ILP];
+#pragma unroll
+        for (int j = 0; j < BFS_ILP; ++j) u[j] = k0 + (int64_t)j * G < hi ? tcol[k0 + (int64_t)j * G] : -1;
+#pragma unroll
+        for (int j = 0; j < BFS_ILP; ++j) old[j] = u[j] >= 0 ? atomicOr(vis + (u[j] >> 5), 1u << (u[j] & 31)) : ~0u;
+#pragma unroll
+        for (int j = 0; j < BFS_ILP; ++j) {
+          if (!((old[j] >> (u[j] & 31)) & 1u)) {
+            cg::coalesced_group g = cg::coalesced_threads();
+            uint32_t base = 0;
+            if (g.thread_rank() == 0) base = atomicAdd(ncnt, (uint32_t)g.size());
+            const uint32_t slot = g.shfl(base, 0) + g.thread_rank();
+            if (slot < cap) ln[slot] = u[j];
+            else __stcg(qn + agg_inc(&st->count[nxt]), u[j]);
+            prefetch_l2(trp + u[j]);   // its row bounds are read before the next level
+          }
+        }
+      }
+    }
+    __syncthreads();   // this CTA's expansion is done: its next queue is final
+    const uint32_t nmine = min(*ncnt, cap);
+    if (t == 0) {
+      for (int r = 0; r < nb; ++r) *cl.map_shared_rank(&pub[p ^ 1][rank], r) = nmine;
+      lcnt[p] = 0u;   // the counter of the queue just expanded serves level L + 2
+    }
+    auto token = cl.barrier_arrive();   // the next frontier is complete, the lengths published
+    // meanwhile the rows of this CTA's next states into L2 (hints: nothing waits for them)
+    for (uint32_t i = t; i < nmine; i += blockDim.x) {
+      const int32_t u = ln[i];
+      const int64_t lo = trp[u], hi = trp[u + 1];
+      if (hi > lo) {
+        prefetch_l2(tcol + lo);
+        if (((lo ^ (hi - 1)) >> 5) != 0) prefetch_l2(tcol + hi - 1);   // a row across two lines
+      }
+    }
+    cl.barrier_wait(std::move(token));
+    ++L;
+  }
+  if (wide) {
+    const int p = L & 1;
+    cl.sync();   // every CTA has read the global count of level L before it changes
+    uint32_t off = spill;
+    for (int r = 0; r < rank; ++r) off += pub[p][r];
+    const uint32_t mine = pub[p][rank];
+    int32_t* qc = (L & 1) ? qb : qa;
+    for (uint32_t i = t; i < mine; i += blockDim.x) __stcg(qc + off + i, lq[(size_t)p * cap + i]);
+    if (ctid == 0) st->count[L % 3] = spill + local_tot;
+  }
+  if (ctid == 0) st->level = L;
+}
+
+// States per CTA queue of k_bfs_cluster_lq (two queues per CTA: 128 KB of shared memory).
+constexpr uint32_t BFS_LQ_CAP = 16384;
+
+// The level loop on the cluster keeps its frontier in shared memory unless REACH_BFS_LQ=0.
+static bool bfs_local_queues() {
+  const char* e = std::getenv("REACH_BFS_LQ");
+  return !(e && e[0] == '0');
+}
+
+template <int G>
+static const void* bfs_cluster_fn(bool lq) {
+  return lq ? (const void*)k_bfs_cluster_lq<G> : (const void*)k_bfs_cluster<G>;
+}
+
+static size_t bfs_cluster_smem(bool lq) { return lq ? 2 * sizeof(int32_t) * BFS_LQ_CAP : 0; }
+
+// Cluster size the device can host for the cluster level loop (16, else 8, else 0 = none).
+template <int G>
+static int bfs_cluster_size(reach_ctx* c, bool lq) {
+  const void* fn = bfs_cluster_fn<G>(lq);
+  if (lq && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bfs_cluster_smem(lq)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   for (int cs : {16, 8}) {
     if (cs > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
       cudaGetLastError();
@@ -429,6 +734,7 @@ static int bfs_cluster_size(reach_ctx* c) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs);
     cfg.blockDim = dim3(BFS_CL_NT);
+    cfg.dynamicSmemBytes = bfs_cluster_smem(lq);
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = cs;
@@ -450,11 +756,13 @@ static int bfs_cluster_size(reach_ctx* c) {
 constexpr double BFS_CLUSTER_EDGES = 24576.0;
 
 template <int G>
-static cudaError_t launch_cluster_levels(reach_ctx* c, int cs, int avoid_goal, uint32_t* vis, cudaStream_t s) {
-  const void* fn = (const void*)k_bfs_cluster<G>;
+static cudaError_t launch_cluster_levels(reach_ctx* c, int cs, bool lq, int avoid_goal, uint32_t* vis,
+                                         cudaStream_t s) {
+  const void* fn = bfs_cluster_fn<G>(lq);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cs);
   cfg.blockDim = dim3(BFS_CL_NT);
+  cfg.dynamicSmemBytes = bfs_cluster_smem(lq);
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -472,62 +780,77 @@ static cudaError_t launch_cluster_levels(reach_ctx* c, int cs, int avoid_goal, u
   double mean_deg = c->n > 0 ? std::max(1.0, (double)c->m / (double)c->n) : 1.0;
   double max_edges = BFS_CLUSTER_EDGES;
   int64_t max_levels = c->n + 2;
+  uint32_t cap = BFS_LQ_CAP;
+  if (lq) {
+    // the opt-in shared memory limit is an attribute of the device in use: set per launch
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bfs_cluster_smem(lq));
+    if (e != cudaSuccess) return e;
+    void* args[] = {&trp, &tcol, &vis, &qa, &qb, &st, &mean_deg, &max_edges, &max_levels, &cap};
+    return cudaLaunchKernelExC(&cfg, fn, args);
+  }
   void* args[] = {&trp, &tcol, &goal, &avoid_goal, &vis, &qa, &qb, &st, &mean_deg, &max_edges, &max_levels};
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-static int cluster_dispatch_size(reach_ctx* c, int g) {
+static int cluster_dispatch_size(reach_ctx* c, int g, bool lq) {
   switch (g) {
-    case 2: return bfs_cluster_size<2>(c);
-    case 4: return bfs_cluster_size<4>(c);
-    case 8: return bfs_cluster_size<8>(c);
-    case 16: return bfs_cluster_size<16>(c);
-    default: return bfs_cluster_size<32>(c);
+    case 2: return bfs_cluster_size<2>(c, lq);
+    case 4: return bfs_cluster_size<4>(c, lq);
+    case 8: return bfs_cluster_size<8>(c, lq);
+    case 16: return bfs_cluster_size<16>(c, lq);
+    default: return bfs_cluster_size<32>(c, lq);
   }
 }
 
-static cudaError_t cluster_dispatch(reach_ctx* c, int g, int cs, int avoid_goal, uint32_t* vis, cudaStream_t s) {
+static cudaError_t cluster_dispatch(reach_ctx* c, int g, int cs, bool lq, int avoid_goal, uint32_t* vis,
+                                    cudaStream_t s) {
   switch (g) {
-    case 2: return launch_cluster_levels<2>(c, cs, avoid_goal, vis, s);
-    case 4: return launch_cluster_levels<4>(c, cs, avoid_goal, vis, s);
-    case 8: return launch_cluster_levels<8>(c, cs, avoid_goal, vis, s);
-    case 16: return launch_cluster_levels<16>(c, cs, avoid_goal, vis, s);
-    default: return launch_cluster_levels<32>(c, cs, avoid_goal, vis, s);
+    case 2: return launch_cluster_levels<2>(c, cs, lq, avoid_goal, vis, s);
+    case 4: return launch_cluster_levels<4>(c, cs, lq, avoid_goal, vis, s);
+    case 8: return launch_cluster_levels<8>(c, cs, lq, avoid_goal, vis, s);
+    case 16: return launch_cluster_levels<16>(c, cs, lq, avoid_goal, vis, s);
+    default: return launch_cluster_levels<32>(c, cs, lq, avoid_goal, vis, s);
   }
 }
 
-static void level_dispatch(reach_ctx* c, int g, int grid, int avoid_goal, uint32_t* vis,
+static void level_dispatch(reach_ctx* c, int g, int grid, uint32_t* vis, double pull_edges,
                            cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
   switch (g) {
-    case 2: launch_level<2>(c, grid, avoid_goal, vis, h, use_cond, s); break;
-    case 4: launch_level<4>(c, grid, avoid_goal, vis, h, use_cond, s); break;
-    case 8: launch_level<8>(c, grid, avoid_goal, vis, h, use_cond, s); break;
-    case 16: launch_level<16>(c, grid, avoid_goal, vis, h, use_cond, s); break;
-    default: launch_level<32>(c, grid, avoid_goal, vis, h, use_cond, s); break;
+    case 2: launch_level<2>(c, grid, vis, pull_edges, h, use_cond, s); break;
+    case 4: launch_level<4>(c, grid, vis, pull_edges, h, use_cond, s); break;
+    case 8: launch_level<8>(c, grid, vis, pull_edges, h, use_cond, s); break;
+    case 16: launch_level<16>(c, grid, vis, pull_edges, h, use_cond, s); break;
+    default: launch_level<32>(c, grid, vis, pull_edges, h, use_cond, s); break;
   }
 }
 
-// Backward search from the sources over reversed edges (§2.2).  source_kind 0:
-// GS, marks vis[0..] = "can reach GS".  source_kind 1: S=0 (states not marked by
-// the first search), with predecessors that are goals skipped when avoid_goal;
-// marks vis[words..] = "reaches S=0 along a path avoiding GS".
-cudaError_t bfs_backward(reach_ctx* c, int source_kind, bool avoid_goal) {
-  const int64_t n = c->n;
-  const int64_t words = (n + 31) >> 5;
-  uint32_t* vis = c->vis + (source_kind == 0 ? 0 : words);
-  const uint32_t* other = c->vis;
+static void pull_dispatch(reach_ctx* c, int g, int avoid_goal, uint32_t* vis, double pull_edges,
+                          int32_t level_cap, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
+  if (g <= 4) {   // short rows: a thread per PULL_S states
+    const double mean_deg = c->n > 0 ? std::max(1.0, (double)c->m / (double)c->n) : 1.0;
+    const int grid = grid_for(c, (const void*)k_bfs_pull_thin, 256, (c->n + PULL_S - 1) / PULL_S);
+    k_bfs_pull_thin<<<grid, 256, 0, s>>>(c->n, c->rowptr, c->col, c->val, c->goal, avoid_goal, vis, c->queue,
+                                         c->queue + c->n, c->bfs, c->ticket, mean_deg, pull_edges, level_cap,
+                                         h, use_cond);
+    return;
+  }
+  switch (g) {
+    case 2: launch_pull<2>(c, avoid_goal, vis, pull_edges, level_cap, h, use_cond, s); break;
+    case 4: launch_pull<4>(c, avoid_goal, vis, pull_edges, level_cap, h, use_cond, s); break;
+    case 8: launch_pull<8>(c, avoid_goal, vis, pull_edges, level_cap, h, use_cond, s); break;
+    case 16: launch_pull<16>(c, avoid_goal, vis, pull_edges, level_cap, h, use_cond, s); break;
+    default: launch_pull<32>(c, avoid_goal, vis, pull_edges, level_cap, h, use_cond, s); break;
+  }
+}
+
+// Runs body(stream, handle, use_cond) until the frontier is empty or level_cap levels are
+// done: as a conditional-while graph (the kernels set the condition) or, with host loops,
+// with a read of the search state after each body.
+template <typename Body>
+static cudaError_t run_levels(reach_ctx* c, int64_t level_cap, Body body) {
   cudaStream_t s = c->stream;
-  cudaMemsetAsync(c->bfs, 0, sizeof(BfsState), s);
-  cudaMemsetAsync(c->ticket, 0, sizeof(unsigned), s);
-  int ig = grid_for(c, (const void*)k_bfs_init, 256, words);
-  k_bfs_init<<<ig, 256, 0, s>>>(n, source_kind, avoid_goal ? 1 : 0, c->goal, other, vis, c->queue, c->bfs);
-  const int g = pick_group(n, c->m);
-  const int grid = c->sm_count * 4;
-  // small frontiers run on one cluster (0: no cluster launch available, or disabled)
-  const char* ev = std::getenv("REACH_BFS_CLUSTER");
-  const int cs = (ev && ev[0] == '0') ? 0 : cluster_dispatch_size(c, g);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
   if (c->device_loops) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -542,13 +865,11 @@ cudaError_t bfs_backward(reach_ctx* c, int source_kind, bool avoid_goal) {
     cudaGraphNode_t node;
     if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
     if (e == cudaSuccess) {
-      cudaGraph_t body = np.conditional.phGraph_out[0];
-      e = cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0,
-                                        cudaStreamCaptureModeRelaxed);
+      cudaGraph_t g = np.conditional.phGraph_out[0];
+      e = cudaStreamBeginCaptureToGraph(c->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
       if (e == cudaSuccess) {
-        if (cs > 0) e = cluster_dispatch(c, g, cs, avoid_goal ? 1 : 0, vis, c->cap);
-        level_dispatch(c, g, grid, avoid_goal ? 1 : 0, vis, h, 1, c->cap);
-        const cudaError_t e2 = cudaStreamEndCapture(c->cap, &body);
+        e = body(c->cap, h, 1);
+        const cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
         if (e == cudaSuccess) e = e2;
       }
     }
@@ -558,17 +879,84 @@ cudaError_t bfs_backward(reach_ctx* c, int source_kind, bool avoid_goal) {
     if (graph) cudaGraphDestroy(graph);
     return e;
   }
-  // host-driven level loop
   BfsState hs;
-  for (int64_t level = 0; level <= n + 1; ++level) {
-    if (cs > 0 && (e = cluster_dispatch(c, g, cs, avoid_goal ? 1 : 0, vis, s)) != cudaSuccess) return e;
-    level_dispatch(c, g, grid, avoid_goal ? 1 : 0, vis, cudaGraphConditionalHandle(), 0, s);
+  for (int64_t it = 0; it <= c->n + 1; ++it) {
+    if ((e = body(s, cudaGraphConditionalHandle(), 0)) != cudaSuccess) return e;
     e = cudaMemcpyAsync(&hs, c->bfs, sizeof(hs), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
-    if (hs.count[hs.level % 3] == 0) break;
+    if (hs.count[hs.level % 3] == 0 || hs.level >= level_cap) break;
   }
   return cudaGetLastError();
+}
+
+// Rows of at least this mean length make the search start bottom-up and without the
+// reversed graph: every level is a pass over the unmarked states' rows, which mostly stop
+// at their first marked successor.  Such chains are a few levels deep; one still going
+// after BFS_DENSE_LEVELS levels starts again with the reversed graph.
+constexpr double BFS_DENSE_DEG = 32.0;
+constexpr int32_t BFS_DENSE_LEVELS = 8;
+
+// Levels whose frontier has more reversed edges than this run bottom-up (k_bfs_pull).
+static double bfs_pull_edges(reach_ctx* c) {
+  return std::max(4.0 * BFS_CLUSTER_EDGES, (double)c->m / 64.0);
+}
+
+// Backward search from the sources (§2.2).  source_kind 0: GS, marks vis[0..] = "can reach
+// GS".  source_kind 1: S=0 (states not marked by the first search), with goal states never
+// entered when avoid_goal; marks vis[words..] = "reaches S=0 along a path avoiding GS".
+// Narrow levels run on one thread-block cluster, others top-down on the whole GPU over the
+// reversed graph, wide ones bottom-up over P (REACH_BFS_PULL=0: never bottom-up).
+cudaError_t bfs_backward(reach_ctx* c, int source_kind, bool avoid_goal) {
+  const int64_t n = c->n;
+  const int64_t words = (n + 31) >> 5;
+  uint32_t* vis = c->vis + (source_kind == 0 ? 0 : words);
+  const uint32_t* other = c->vis;
+  cudaStream_t s = c->stream;
+  const int ag = avoid_goal ? 1 : 0;
+  const char* pv = std::getenv("REACH_BFS_PULL");
+  const bool pull_ok = !(pv && pv[0] == '0');
+  const double mean_deg = n > 0 ? std::max(1.0, (double)c->m / (double)n) : 1.0;
+  const int gp = graph_group(c, n, c->m);
+  auto init = [&]() {
+    cudaMemsetAsync(c->bfs, 0, sizeof(BfsState), s);
+    cudaMemsetAsync(c->ticket, 0, sizeof(unsigned), s);
+    const int ig = grid_for(c, (const void*)k_bfs_init, 256, words);
+    k_bfs_init<<<ig, 256, 0, s>>>(n, source_kind, ag, c->goal, other, vis, c->queue, c->bfs);
+  };
+  cudaError_t e;
+  if (pull_ok && mean_deg >= BFS_DENSE_DEG) {
+    init();
+    e = run_levels(c, BFS_DENSE_LEVELS, [&](cudaStream_t st, cudaGraphConditionalHandle h, int uc) {
+      pull_dispatch(c, gp, ag, vis, 0.0, BFS_DENSE_LEVELS, h, uc, st);
+      return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
+    BfsState hs;
+    e = cudaMemcpyAsync(&hs, c->bfs, sizeof(hs), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess || hs.count[hs.level % 3] == 0) return e;
+  }
+  // the reversed graph (its count pass borrows the queues: before the search starts)
+  if (!c->rev_ready) {
+    if ((e = build_reverse_pattern(c)) != cudaSuccess) return e;
+    c->rev_ready = true;
+  }
+  init();
+  const int g = pick_group(n, c->m);
+  const int grid = c->sm_count * 4;
+  // small frontiers run on one cluster (0: no cluster launch available, or disabled)
+  const char* ev = std::getenv("REACH_BFS_CLUSTER");
+  const bool lq = bfs_local_queues();
+  const int cs = (ev && ev[0] == '0') ? 0 : cluster_dispatch_size(c, g, lq);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const double pull_edges = pull_ok ? bfs_pull_edges(c) : INFINITY;
+  return run_levels(c, INT32_MAX, [&](cudaStream_t st, cudaGraphConditionalHandle h, int uc) {
+    cudaError_t le = cs > 0 ? cluster_dispatch(c, g, cs, lq, ag, vis, st) : cudaSuccess;
+    level_dispatch(c, g, grid, vis, pull_edges, h, uc, st);
+    if (pull_ok) pull_dispatch(c, gp, ag, vis, pull_edges, INT32_MAX, h, uc, st);
+    return le != cudaSuccess ? le : cudaGetLastError();
+  });
 }
 
 // ------------------------------------------------------------------ partition + extraction
@@ -593,7 +981,7 @@ template <int G>
 __global__ void k_extract_count(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                 const double* __restrict__ val, const uint8_t* __restrict__ cls,
                                 const int64_t* __restrict__ qidx, int64_t* __restrict__ acnt,
-                                double* __restrict__ d, double* __restrict__ b,
+                                double* __restrict__ d, double* __restrict__ b, double* __restrict__ bj,
                                 int64_t* __restrict__ qstate, int general) {
   RowGroups rg = RowGroups::make<G>();
   for (int64_t s = rg.first; warp_has_row<G>(s, n); s += rg.stride) {
@@ -620,29 +1008,45 @@ __global__ void k_extract_count(int64_t n, const int64_t* __restrict__ rp, const
       const int64_t i = qidx[s];
       acnt[i] = (int64_t)cnt;
       // chain: d = 1 - A_ii of I - A; general system M x = b: d = M_ii, b given
-      d[i] = general ? diag : 1.0 - diag;
-      if (!general) b[i] = bs;
+      const double di = general ? diag : 1.0 - diag;
+      d[i] = di;
+      if (!general) {
+        b[i] = bs;
+        // bj = b / d of the Jacobi form (§3.1); a row without a self-loop has d = 1 exactly
+        bj[i] = di == 1.0 ? bs : bs / di;
+      }
       qstate[i] = s;
     }
   }
 }
 
+// Also writes the Jacobi form Aj = A / d of each entry (§3.1; IEEE division once per
+// system, none where d = 1) and reduces Varah's row-dominance margin min_i (|d_i| -
+// sum_j |A_ij|) into *kmin as an ordered key, with the sum rounded upward and the
+// difference downward: a guaranteed lower bound of the exact margin.
 template <int G>
 __global__ void k_extract_fill(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                const double* __restrict__ val, const uint8_t* __restrict__ cls,
                                const int64_t* __restrict__ qidx, const int64_t* __restrict__ arp,
-                               int32_t* __restrict__ acol, double* __restrict__ aval, int general) {
+                               const double* __restrict__ d, int32_t* __restrict__ acol,
+                               double* __restrict__ aval, double* __restrict__ aj,
+                               unsigned long long* kmin, int general) {
   RowGroups rg = RowGroups::make<G>();
   const int wl = threadIdx.x & 31;
   const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (wl & ~(G - 1)));
   const unsigned lt = (1u << wl) - 1u;
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  double lo_min = inf;
   for (int64_t s = rg.first; warp_has_row<G>(s, n); s += rg.stride) {
     const bool act = s < n && cls[s] == CLS_SQ;
     int64_t lo = 0, hi = 0, out = 0;
+    double di = 1.0, sa = 0.0;
     if (act) {
       lo = rp[s];
       hi = rp[s + 1];
-      out = arp[qidx[s]];
+      const int64_t i = qidx[s];
+      out = arp[i];
+      di = d[i];
     }
     const unsigned trips = __reduce_max_sync(FULL, (unsigned)((hi - lo + G - 1) / G));
     for (unsigned t = 0; t < trips; ++t) {
@@ -659,12 +1063,22 @@ __global__ void k_extract_fill(int64_t n, const int64_t* __restrict__ rp, const 
       const unsigned mine = __ballot_sync(FULL, p) & gmask;
       if (p) {
         const int64_t pos = out + __popc(mine & lt);
+        const double a = general ? -v : v;   // general system: A = -(off-diagonal of M)
         acol[pos] = cq;
-        aval[pos] = general ? -v : v;   // general system: A = -(off-diagonal of M)
+        aval[pos] = a;
+        aj[pos] = di == 1.0 ? a : a / di;
+        sa = __dadd_ru(sa, fabs(a));
       }
       out += __popc(mine);
     }
+    sa = group_sum_ru<G>(sa);
+    if (act && rg.lane == 0) {
+      const double m = __dadd_rd(fabs(di), -sa);
+      lo_min = fmin(lo_min, m != m ? -inf : m);
+    }
   }
+  lo_min = -warp_max(-lo_min);
+  if ((threadIdx.x & 31) == 0) atomicMin(kmin, ordered_key(lo_min));
 }
 
 // Jacobi form: Aj_ij = A_ij / d_i, bj_i = b_i / d_i (IEEE division, once per system).
@@ -711,10 +1125,11 @@ static void extract_launch(reach_ctx* c, int64_t* acnt, int pass) {
                             256, c->n * G);
   if (pass == 0)
     k_extract_count<G><<<grid, 256, 0, c->stream>>>(c->n, c->rowptr, c->col, c->val, c->cls, c->qidx,
-                                                    acnt, c->d, c->b, c->qstate, c->general ? 1 : 0);
+                                                    acnt, c->d, c->b, c->bj, c->qstate, c->general ? 1 : 0);
   else
     k_extract_fill<G><<<grid, 256, 0, c->stream>>>(c->n, c->rowptr, c->col, c->val, c->cls, c->qidx,
-                                                   c->a_rowptr, c->a_col, c->a_val, c->general ? 1 : 0);
+                                                   c->a_rowptr, c->d, c->a_col, c->a_val, c->a_jv,
+                                                   c->keys + VARAH_KEY, c->general ? 1 : 0);
 }
 
 static void extract_dispatch(reach_ctx* c, int g, int64_t* acnt, int pass) {
@@ -779,6 +1194,9 @@ cudaError_t extract_rows(reach_ctx* c) {
   if ((e = dmalloc(&c->d, nq)) != cudaSuccess) return e;
   if ((e = dmalloc(&c->b, nq)) != cudaSuccess) return e;
   if ((e = dmalloc(&c->qstate, nq)) != cudaSuccess) return e;
+  // bj of a chain comes with b; a general system's b is given later (build_jacobi_form)
+  if (c->bj) { cudaFree(c->bj); c->bj = nullptr; }
+  if (!c->general && (e = dmalloc(&c->bj, nq)) != cudaSuccess) return e;
   int64_t* acnt = nullptr;
   if ((e = dmalloc(&acnt, nq)) != cudaSuccess) return e;
   const int g = graph_group(c, n, c->m);
@@ -794,12 +1212,14 @@ cudaError_t extract_rows(reach_ctx* c) {
   // +8 entries of slack so vector loads of the last row stay inside the allocation
   if ((e = dmalloc(&c->a_col, mq + 8)) != cudaSuccess) return e;
   if ((e = dmalloc(&c->a_val, mq + 8)) != cudaSuccess) return e;
+  if ((e = dmalloc(&c->a_jv, mq + 8)) != cudaSuccess) return e;
   cudaMemsetAsync(c->a_col + mq, 0, 8 * sizeof(int32_t), s);
   cudaMemsetAsync(c->a_val + mq, 0, 8 * sizeof(double), s);
+  cudaMemsetAsync(c->a_jv + mq, 0, 8 * sizeof(double), s);
+  cudaMemsetAsync(c->keys + VARAH_KEY, 0xff, sizeof(unsigned long long), s);
   if (nq > 0) extract_dispatch(c, g, nullptr, 1);
-  // the Jacobi form, the hi/lo split and the transposed system are rebuilt on demand
-  if (c->a_jv) { cudaFree(c->a_jv); c->a_jv = nullptr; }
-  if (c->bj) { cudaFree(c->bj); c->bj = nullptr; }
+  c->varah_key = true;
+  // the hi/lo split and the transposed system are rebuilt on demand
   if (c->at_jv) { cudaFree(c->at_jv); c->at_jv = nullptr; }
   if (c->a_hi) { cudaFree(c->a_hi); c->a_hi = nullptr; }
   if (c->a_lo) { cudaFree(c->a_lo); c->a_lo = nullptr; }
@@ -845,14 +1265,29 @@ cudaError_t split_hilo(reach_ctx* c) {
   return cudaGetLastError();
 }
 
+__global__ void k_bj(int64_t nq, const double* __restrict__ b, const double* __restrict__ d,
+                     double* __restrict__ bj) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+    const double di = d[i];
+    bj[i] = di == 1.0 ? b[i] : b[i] / di;
+  }
+}
+
+// The Jacobi form (§3.1).  The extraction writes Aj (and a chain's bj) with A itself; a
+// general system's bj follows here, once its b is in place.
 cudaError_t build_jacobi_form(reach_ctx* c) {
   if (c->a_jv && c->bj) return cudaSuccess;
   const int64_t nq = c->n_q, mq = c->m_q;
   cudaError_t e;
-  if ((e = dmalloc(&c->a_jv, mq + 8)) != cudaSuccess) return e;
+  if (!c->a_jv) {
+    if ((e = dmalloc(&c->a_jv, mq + 8)) != cudaSuccess) return e;
+    if ((e = dmalloc(&c->bj, nq)) != cudaSuccess) return e;
+    cudaMemsetAsync(c->a_jv + mq, 0, 8 * sizeof(double), c->stream);
+    if (nq > 0) jform_dispatch(c, graph_group(c, nq, mq), nq, c->a_rowptr, c->a_val, c->b, c->a_jv, c->bj);
+    return cudaGetLastError();
+  }
   if ((e = dmalloc(&c->bj, nq)) != cudaSuccess) return e;
-  cudaMemsetAsync(c->a_jv + mq, 0, 8 * sizeof(double), c->stream);
-  if (nq > 0) jform_dispatch(c, graph_group(c, nq, mq), nq, c->a_rowptr, c->a_val, c->b, c->a_jv, c->bj);
+  if (nq > 0) k_bj<<<grid_for(c, (const void*)k_bj, 256, nq), 256, 0, c->stream>>>(nq, c->b, c->d, c->bj);
   return cudaGetLastError();
 }
 

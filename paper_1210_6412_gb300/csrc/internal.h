@@ -51,6 +51,9 @@ struct BiState {
 // pushes into count[(L + 1) % 3] and may clear count[(L + 2) % 3] (the frontier of level
 // L - 1, read by everyone before the barrier that ended level L - 1), so a level needs
 // one barrier.
+// Slot of reach_ctx::keys that the extraction reduces Varah's margin into.
+constexpr int VARAH_KEY = 2;
+
 struct BfsState {
   int32_t level;
   uint32_t count[3];
@@ -157,11 +160,13 @@ struct reach_ctx {
   double kinv_varah = INFINITY;
   double kinv_tau = INFINITY;
   double kinv_varah_t = -1.0;           // < 0: not computed yet
-  unsigned long long* keys = nullptr;   // two ordered-key reduction words
+  unsigned long long* keys = nullptr;   // ordered-key reduction words (VARAH_KEY: the extraction's)
+  bool varah_key = false;               // keys[VARAH_KEY] holds the margin of the current system
   double* tau_save = nullptr;           // b and bj while the tau system is solved (2 n?)
 
   reach::Tuning tune;
   bool device_loops = true;   // conditional-while graphs (false: host-driven loops)
+  bool rev_ready = false;     // t_rowptr / t_col hold the reversed graph of the current P
   double ms_precompute = 0.0;
 
   // cached solve graphs, keyed by method and shape

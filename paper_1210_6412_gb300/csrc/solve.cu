@@ -360,12 +360,6 @@ __global__ void __launch_bounds__(NT) k_jacobi64(int64_t nq, const int64_t* __re
 // gamma_D = D u / (1 - D u), u = 2^-53, bounded above by D u (1 + 2 D u) with upward
 // rounding (no division).
 
-template <int G>
-RDEV double group_sum_ru(double v) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) v = __dadd_ru(v, __shfl_xor_sync(FULL, v, o));
-  return v;
-}
 
 template <int G>
 constexpr int log2_of() { return G <= 1 ? 0 : 1 + log2_of<G / 2>(); }
@@ -416,12 +410,6 @@ __global__ void __launch_bounds__(NT) k_resid_cert(int64_t nq, const int64_t* __
   }
 }
 
-// Order-preserving map of doubles onto unsigned integers (for atomicMin / atomicMax of
-// values of either sign), and back.
-RDEV unsigned long long ordered_key(double v) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
-}
 
 // Lower bound, per row, of (|M| w)_i in the sense needed by the norm bounds:
 //   ABS:  |d_i| - sum_j |A_ij|          (w = 1: Varah's row-dominance margin)
@@ -1328,8 +1316,17 @@ cudaError_t varah_norm_bound(reach_ctx* c, bool transposed, double* kinv) {
     return cudaSuccess;
   }
   double margin = 0.0;
-  const cudaError_t e = row_lower(c, transposed, nullptr, &margin, nullptr);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if (!transposed && c->varah_key) {   // reduced by the extraction
+    unsigned long long k = 0ull;
+    e = cudaMemcpyAsync(&k, c->keys + VARAH_KEY, sizeof(k), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return e;
+    const double lo = key_to_double(k);
+    margin = lo == lo ? lo : -INFINITY;
+  } else if ((e = row_lower(c, transposed, nullptr, &margin, nullptr)) != cudaSuccess) {
+    return e;
+  }
   *kinv = margin > 0.0 ? std::nextafter(1.0 / margin, INFINITY) : INFINITY;
   return cudaSuccess;
 }

@@ -15,6 +15,7 @@ import oracle as O
 import paper_1210_6412_gb300 as R
 from paper_1210_6412_gb300 import synth
 from tests.gpu_util import TOL_FP64, TOL_MIXED, need_gpu
+from tests.test_gpu_parity import BFS_VARIANTS
 
 pytestmark = pytest.mark.gpu
 
@@ -78,10 +79,11 @@ def test_layered_400k_classes_both_searches(layered, mode, monkeypatch):
     torch = need_gpu()
     c, _ = layered
     cls_o = O.partition(c.n, c.rowptr, c.col, c.val, c.goal, mode)
-    for cluster in ("1", "0"):
-        monkeypatch.setenv("REACH_BFS_CLUSTER", cluster)
+    for env in BFS_VARIANTS:
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
         with R.Solver(c.n, *_dev(torch, c.rowptr, c.col, c.val, c.goal), mode=mode) as s:
-            assert np.array_equal(s.classes(), cls_o), cluster
+            assert np.array_equal(s.classes(), cls_o), env
 
 
 def test_two_thousand_levels_on_the_cluster():

@@ -383,20 +383,78 @@ def test_bulk_copy_staged_sweep_matches_oracle(c1, name, monkeypatch):
     assert ms > 0.0
 
 
-@pytest.mark.parametrize("name", ["layered", "dense", "gambler", "random"])
+# the search's level kernels: narrow levels on the cluster with shared-memory queues or with
+# global ones, no cluster at all, no bottom-up levels
+BFS_VARIANTS = [
+    {"REACH_BFS_CLUSTER": "1", "REACH_BFS_LQ": "1", "REACH_BFS_PULL": "1"},
+    {"REACH_BFS_CLUSTER": "1", "REACH_BFS_LQ": "0", "REACH_BFS_PULL": "1"},
+    {"REACH_BFS_CLUSTER": "0", "REACH_BFS_LQ": "1", "REACH_BFS_PULL": "1"},
+    {"REACH_BFS_CLUSTER": "1", "REACH_BFS_LQ": "1", "REACH_BFS_PULL": "0"},
+]
+
+
+@pytest.mark.parametrize("name", ["layered", "dense", "gambler", "random", "dense_layered", "dense_no_sinks"])
 def test_partition_with_and_without_the_cluster_search(c1, name, monkeypatch):
-    """The backward searches of §2.2 run their narrow levels on one thread-block cluster and
-    wide levels on the whole GPU; with the cluster path switched off (REACH_BFS_CLUSTER=0)
-    every level runs on the GPU.  Both give the oracle's S=0 / S=1 / S? exactly, in both
-    partition modes."""
+    """The backward searches of §2.2 run their narrow levels on one thread-block cluster,
+    others top-down on the whole GPU and wide ones bottom-up; with each of these switched
+    off in turn they give the oracle's S=0 / S=1 / S? exactly, in both partition modes."""
     c = {"random": lambda: c1,
          "layered": lambda: synth.layered_chain(layers=300, width=200, seed=12),
          "dense": lambda: synth.dense_random_chain(n=3000, density=0.1, sink_frac=0.02, seed=7),
-         "gambler": lambda: synth.gamblers_ruin(500, 0.48)}[name]()
+         "gambler": lambda: synth.gamblers_ruin(500, 0.48),
+         # 40 successors per state, 30 layers: starts bottom-up and gives up after 8 levels
+         # every state reaches a goal: S=0 is empty and the S=1 search has no sources
+         "dense_no_sinks": lambda: synth.dense_random_chain(n=2000, density=0.05, sink_frac=0.0, seed=8),
+         "dense_layered": lambda: synth.layered_chain(layers=30, width=64, dmin=33, dmax=48, p_forward=1.0,
+                                                      goal_frac_last=0.05, seed=13)}[name]()
     need_gpu()
     for mode in MODES:
         cls_o = O.partition(c.n, c.rowptr, c.col, c.val, c.goal, mode)
-        for flag in ("1", "0"):
-            monkeypatch.setenv("REACH_BFS_CLUSTER", flag)
+        for env in BFS_VARIANTS:
+            for k, v in env.items():
+                monkeypatch.setenv(k, v)
             with R.Solver(c.n, c.rowptr, c.col, c.val, c.goal, mode=mode) as s:
-                assert np.array_equal(s.classes(), cls_o), (name, mode, flag)
+                assert np.array_equal(s.classes(), cls_o), (name, mode, env)
+
+
+def _fan_chain(fan, depth):
+    """State 0 is the goal; states 1..fan step into it (probability 1/2) and otherwise stay
+    (the first half) or fall into an absorbing sink (the second half); behind each of them a
+    path of `depth` states leads forward to it; the last fan/8 states of the paths lead only
+    to the sink instead.  The first backward level finds `fan` states in one go (one state's
+    reversed row), the next ones `fan` states per level."""
+    n = 2 + fan * (depth + 1)
+    sink = n - 1
+    rows = [[(0, 1.0)]]
+    for i in range(1, fan + 1):
+        rows.append([(0, 0.5), (i if i <= fan // 2 else sink, 0.5)])
+    for d in range(1, depth + 1):
+        for i in range(1, fan + 1):
+            s = d * fan + i
+            nxt = (d - 1) * fan + i
+            rows.append([(nxt, 1.0)] if i <= fan - fan // 8 or d < depth else [(sink, 1.0)])
+    rows.append([(sink, 1.0)])
+    assert len(rows) == n
+    rp = np.zeros(n + 1, np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    col = np.array([c for r in rows for c, _ in r], np.int32)
+    val = np.array([v for r in rows for _, v in r], np.float64)
+    goal = np.zeros(n, np.uint8)
+    goal[0] = 1
+    return synth.Chain(n=n, rowptr=rp, col=col, val=val, goal=goal)
+
+
+@pytest.mark.parametrize("fan,depth", [(40_000, 3), (12_000, 40), (200, 300)])
+def test_partition_through_full_local_queues(fan, depth, monkeypatch):
+    """A level that finds more states than a CTA's shared-memory queue holds (they spill to
+    the global queue), frontiers that leave the cluster for the whole GPU, and a long run of
+    narrow levels: classes against the oracle in both modes."""
+    need_gpu()
+    c = _fan_chain(fan, depth)
+    for mode in MODES:
+        cls_o = O.partition(c.n, c.rowptr, c.col, c.val, c.goal, mode)
+        for env in BFS_VARIANTS:
+            for k, v in env.items():
+                monkeypatch.setenv(k, v)
+            with R.Solver(c.n, c.rowptr, c.col, c.val, c.goal, mode=mode) as s:
+                assert np.array_equal(s.classes(), cls_o), (fan, depth, mode, env)
