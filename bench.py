@@ -291,8 +291,8 @@ def launches_per_step(infos, k, tau_iters=0):
     j, mx, b = infos["jacobi"], infos["mixed"], infos["bicgstab"]
     create = 1
     # search start, its bottom-up levels (no reversed graph on this dense chain), classes,
-    # scan, row counts (with b and bj), scan, rows (with Aj and Varah's margin)
-    precompute = 1 + j.get("bfs_levels", 3) + 1 + 3 + 1 + 3 + 1
+    # scan, row counts, scan, rows, Jacobi form (with Varah's margin)
+    precompute = 1 + j.get("bfs_levels", 3) + 1 + 3 + 1 + 3 + 1 + 1
     jac = j["iters"] + 2 * (j["iters"] // k) + 3
     mix = mx["refinements"] * (2 + (k - 1) + 2) + 3 + 1
     bic = 1 + 5 * b["iters"] + 3

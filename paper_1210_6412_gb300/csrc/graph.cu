@@ -288,6 +288,7 @@ RDEV bool bit_of(const uint32_t* v, int64_t s) { return (v[s >> 5] >> (s & 31)) 
 // Fetches the line holding *p into L2 without waiting for it.
 RDEV void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
+
 // Sources: kind 0 = goal states; kind 1 = states NOT marked in `other` (S=0).  avoid_goal:
 // goal states are marked visited from the start without being sources, so the search never
 // enters them and no level has to read the goal mask (their bits mean nothing afterwards).
@@ -442,87 +443,6 @@ __global__ void k_bfs_pull(int64_t n, const int64_t* __restrict__ rp, const int3
   }
 }
 
-// The same pass for short rows: each thread takes PULL_S consecutive states (one visited
-// word) and walks their rows in step, so the loads of its states go out together and a
-// warp keeps 32 * PULL_S rows in flight.
-constexpr int PULL_S = 4;
-
-__global__ void k_bfs_pull_thin(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                const double* __restrict__ val, const uint8_t* __restrict__ goal,
-                                int avoid_goal, uint32_t* vis, int32_t* qa, int32_t* qb, BfsState* st,
-                                unsigned* ticket, double mean_deg, double pull_edges, int32_t level_cap,
-                                cudaGraphConditionalHandle h, int use_cond) {
-  const int L = st->level;
-  const int cur = L % 3, nxt = (L + 1) % 3;
-  const uint32_t cnt = st->count[cur];
-  if (cnt == 0) {   // no sources, or the search ended: the loop must stop here too
-    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
-    return;
-  }
-  if (!((double)cnt * mean_deg > pull_edges)) return;   // k_bfs_level's
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->count[(L + 2) % 3] = 0u;
-  int32_t* qn = (L & 1) ? qa : qb;
-  const int64_t step = (int64_t)gridDim.x * blockDim.x * PULL_S;
-  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * PULL_S; base < n; base += step) {
-    const uint32_t w = __ldcg(vis + (base >> 5));   // PULL_S divides 32: one word
-    int64_t k[PULL_S], hi[PULL_S];
-    bool live[PULL_S];
-#pragma unroll
-    for (int j = 0; j < PULL_S; ++j) {
-      const int64_t sj = base + j;
-      live[j] = sj < n && !((w >> (sj & 31)) & 1u);
-      k[j] = live[j] ? rp[sj] : 0;
-      hi[j] = live[j] ? rp[sj + 1] : 0;
-    }
-    uint32_t found = 0u;   // bits (s & 31) of the states marked by this thread
-    bool more = true;
-    while (more) {
-      int32_t cc[PULL_S];
-      bool pos[PULL_S];
-#pragma unroll
-      for (int j = 0; j < PULL_S; ++j) {
-        const bool go = live[j] && k[j] < hi[j];
-        cc[j] = go ? col[k[j]] : -1;
-        pos[j] = go && val[k[j]] > 0.0;
-      }
-      more = false;
-#pragma unroll
-      for (int j = 0; j < PULL_S; ++j) {
-        if (cc[j] >= 0) {
-          const uint32_t vw = __ldcg(vis + (cc[j] >> 5));
-          const bool blocked = avoid_goal && goal[cc[j]];
-          if (pos[j] && ((vw >> (cc[j] & 31)) & 1u) && !blocked) {
-            found |= 1u << ((base + j) & 31);
-            live[j] = false;
-          }
-          ++k[j];
-          more |= live[j] && k[j] < hi[j];
-        }
-      }
-    }
-    if (found) {
-      atomicOr(vis + (base >> 5), found);
-#pragma unroll
-      for (int j = 0; j < PULL_S; ++j)
-        if ((found >> ((base + j) & 31)) & 1u) qn[agg_inc(&st->count[nxt])] = (int32_t)(base + j);
-    }
-  }
-  __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    const uint32_t next = atomicAdd(&st->count[nxt], 0u);
-    st->level = L + 1;
-    *ticket = 0u;
-    if (use_cond) cudaGraphSetConditional(h, next > 0 && L + 1 < level_cap ? 1u : 0u);
-  }
-}
-
 template <int G>
 static void launch_pull(reach_ctx* c, int avoid_goal, uint32_t* vis, double pull_edges, int32_t level_cap,
                         cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
@@ -604,25 +524,33 @@ __global__ void __launch_bounds__(BFS_CL_NT, 1) k_bfs_cluster_lq(const int64_t* 
                                                                  double mean_deg, double max_edges,
                                                                  int64_t max_levels, uint32_t cap) {
   extern __shared__ int32_t lq[];   // [2][cap]: the queues of even and odd levels
-  __shared__ uint32_t lcnt[2];
-  __shared__ uint32_t pub[2][16];   // [level parity][CTA]: queue lengths of every CTA
+  __shared__ uint32_t lcnt[2], lspill[2];
+  // [level parity][CTA]: every CTA's queue length (low word) and spilled states (high word)
+  __shared__ unsigned long long pub[2][16];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), nb = (int)cl.num_blocks();
   const int t = threadIdx.x, lane = t & (G - 1);
   const int64_t ctid = (int64_t)rank * blockDim.x + t;
   const int64_t cgroups = (int64_t)nb * blockDim.x / G;
-  if (t < 2) lcnt[t] = 0u;
-  if (t < 32) pub[t >> 4][t & 15] = 0u;
+  if (t < 2) lcnt[t] = lspill[t] = 0u;
+  if (t < 32) pub[t >> 4][t & 15] = 0ull;
   cl.sync();   // every slot is zero before any CTA publishes into it
   int L = *(volatile int32_t*)&st->level;
   uint32_t spill = 0, local_tot = 0;
   bool wide = false;
   for (int64_t it = 0;; ++it) {
     const int cur = L % 3, nxt = (L + 1) % 3, p = L & 1;
-    // the same values in every thread: written before the last barrier, not since
-    spill = *(volatile uint32_t*)&st->count[cur];
+    // the same values in every thread: written before the last barrier, not since.  The
+    // spilled states of a level are counted by the CTAs too; only the frontier this launch
+    // starts from is known from the global count alone.
     local_tot = 0;
-    for (int r = 0; r < nb; ++r) local_tot += *(volatile uint32_t*)&pub[p][r];
+    uint32_t pspill = 0;
+    for (int r = 0; r < nb; ++r) {
+      const unsigned long long w = *(volatile unsigned long long*)&pub[p][r];
+      local_tot += (uint32_t)w;
+      pspill += (uint32_t)(w >> 32);
+    }
+    spill = it == 0 ? *(volatile uint32_t*)&st->count[cur] : pspill;
     const uint32_t tot = spill + local_tot;
     if (tot == 0) break;
     if (it >= max_levels || (double)tot * mean_deg > max_edges) {
@@ -636,11 +564,13 @@ __global__ void __launch_bounds__(BFS_CL_NT, 1) k_bfs_cluster_lq(const int64_t* 
     int32_t* lc = lq + (size_t)p * cap;
     int32_t* ln = lq + (size_t)(p ^ 1) * cap;
     uint32_t* ncnt = &lcnt[p ^ 1];
+    uint32_t* nspill = &lspill[p ^ 1];
     for (int64_t i = ctid / G; i < (int64_t)tot; i += cgroups) {
       int32_t v;
       if (i < (int64_t)local_tot) {   // entry i of the CTAs' queues taken in rank order
         uint32_t o = 0, acc = 0;
-        while ((uint32_t)i >= acc + *(volatile uint32_t*)&pub[p][o]) acc += *(volatile uint32_t*)&pub[p][o++];
+        while ((uint32_t)i >= acc + (uint32_t)*(volatile unsigned long long*)&pub[p][o])
+          acc += (uint32_t)*(volatile unsigned long long*)&pub[p][o++];
         v = *cl.map_shared_rank(lc + ((uint32_t)i - acc), o);
       } else {
         v = __ldcg(qc + (i - (int64_t)local_tot));
@@ -663,7 +593,10 @@ __global__ void __launch_bounds__(BFS_CL_NT, 1) k_bfs_cluster_lq(const int64_t* 
             if (g.thread_rank() == 0) base = atomicAdd(ncnt, (uint32_t)g.size());
             const uint32_t slot = g.shfl(base, 0) + g.thread_rank();
             if (slot < cap) ln[slot] = u[j];
-            else __stcg(qn + agg_inc(&st->count[nxt]), u[j]);
+            else {
+              __stcg(qn + agg_inc(&st->count[nxt]), u[j]);
+              atomicAdd(nspill, 1u);
+            }
             prefetch_l2(trp + u[j]);   // its row bounds are read before the next level
           }
         }
@@ -672,8 +605,9 @@ __global__ void __launch_bounds__(BFS_CL_NT, 1) k_bfs_cluster_lq(const int64_t* 
     __syncthreads();   // this CTA's expansion is done: its next queue is final
     const uint32_t nmine = min(*ncnt, cap);
     if (t == 0) {
-      for (int r = 0; r < nb; ++r) *cl.map_shared_rank(&pub[p ^ 1][rank], r) = nmine;
-      lcnt[p] = 0u;   // the counter of the queue just expanded serves level L + 2
+      const unsigned long long w = ((unsigned long long)*nspill << 32) | nmine;
+      for (int r = 0; r < nb; ++r) *cl.map_shared_rank(&pub[p ^ 1][rank], r) = w;
+      lcnt[p] = lspill[p] = 0u;   // the counters of the level just expanded serve level L + 2
     }
     auto token = cl.barrier_arrive();   // the next frontier is complete, the lengths published
     // meanwhile the rows of this CTA's next states into L2 (hints: nothing waits for them)
@@ -692,8 +626,8 @@ __global__ void __launch_bounds__(BFS_CL_NT, 1) k_bfs_cluster_lq(const int64_t* 
     const int p = L & 1;
     cl.sync();   // every CTA has read the global count of level L before it changes
     uint32_t off = spill;
-    for (int r = 0; r < rank; ++r) off += pub[p][r];
-    const uint32_t mine = pub[p][rank];
+    for (int r = 0; r < rank; ++r) off += (uint32_t)pub[p][r];
+    const uint32_t mine = (uint32_t)pub[p][rank];
     int32_t* qc = (L & 1) ? qb : qa;
     for (uint32_t i = t; i < mine; i += blockDim.x) __stcg(qc + off + i, lq[(size_t)p * cap + i]);
     if (ctid == 0) st->count[L % 3] = spill + local_tot;
@@ -827,14 +761,6 @@ static void level_dispatch(reach_ctx* c, int g, int grid, uint32_t* vis, double 
 
 static void pull_dispatch(reach_ctx* c, int g, int avoid_goal, uint32_t* vis, double pull_edges,
                           int32_t level_cap, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
-  if (g <= 4) {   // short rows: a thread per PULL_S states
-    const double mean_deg = c->n > 0 ? std::max(1.0, (double)c->m / (double)c->n) : 1.0;
-    const int grid = grid_for(c, (const void*)k_bfs_pull_thin, 256, (c->n + PULL_S - 1) / PULL_S);
-    k_bfs_pull_thin<<<grid, 256, 0, s>>>(c->n, c->rowptr, c->col, c->val, c->goal, avoid_goal, vis, c->queue,
-                                         c->queue + c->n, c->bfs, c->ticket, mean_deg, pull_edges, level_cap,
-                                         h, use_cond);
-    return;
-  }
   switch (g) {
     case 2: launch_pull<2>(c, avoid_goal, vis, pull_edges, level_cap, h, use_cond, s); break;
     case 4: launch_pull<4>(c, avoid_goal, vis, pull_edges, level_cap, h, use_cond, s); break;
@@ -981,7 +907,7 @@ template <int G>
 __global__ void k_extract_count(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                 const double* __restrict__ val, const uint8_t* __restrict__ cls,
                                 const int64_t* __restrict__ qidx, int64_t* __restrict__ acnt,
-                                double* __restrict__ d, double* __restrict__ b, double* __restrict__ bj,
+                                double* __restrict__ d, double* __restrict__ b,
                                 int64_t* __restrict__ qstate, int general) {
   RowGroups rg = RowGroups::make<G>();
   for (int64_t s = rg.first; warp_has_row<G>(s, n); s += rg.stride) {
@@ -1008,45 +934,29 @@ __global__ void k_extract_count(int64_t n, const int64_t* __restrict__ rp, const
       const int64_t i = qidx[s];
       acnt[i] = (int64_t)cnt;
       // chain: d = 1 - A_ii of I - A; general system M x = b: d = M_ii, b given
-      const double di = general ? diag : 1.0 - diag;
-      d[i] = di;
-      if (!general) {
-        b[i] = bs;
-        // bj = b / d of the Jacobi form (§3.1); a row without a self-loop has d = 1 exactly
-        bj[i] = di == 1.0 ? bs : bs / di;
-      }
+      d[i] = general ? diag : 1.0 - diag;
+      if (!general) b[i] = bs;
       qstate[i] = s;
     }
   }
 }
 
-// Also writes the Jacobi form Aj = A / d of each entry (§3.1; IEEE division once per
-// system, none where d = 1) and reduces Varah's row-dominance margin min_i (|d_i| -
-// sum_j |A_ij|) into *kmin as an ordered key, with the sum rounded upward and the
-// difference downward: a guaranteed lower bound of the exact margin.
 template <int G>
 __global__ void k_extract_fill(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                const double* __restrict__ val, const uint8_t* __restrict__ cls,
                                const int64_t* __restrict__ qidx, const int64_t* __restrict__ arp,
-                               const double* __restrict__ d, int32_t* __restrict__ acol,
-                               double* __restrict__ aval, double* __restrict__ aj,
-                               unsigned long long* kmin, int general) {
+                               int32_t* __restrict__ acol, double* __restrict__ aval, int general) {
   RowGroups rg = RowGroups::make<G>();
   const int wl = threadIdx.x & 31;
   const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (wl & ~(G - 1)));
   const unsigned lt = (1u << wl) - 1u;
-  const double inf = __longlong_as_double(0x7ff0000000000000LL);
-  double lo_min = inf;
   for (int64_t s = rg.first; warp_has_row<G>(s, n); s += rg.stride) {
     const bool act = s < n && cls[s] == CLS_SQ;
     int64_t lo = 0, hi = 0, out = 0;
-    double di = 1.0, sa = 0.0;
     if (act) {
       lo = rp[s];
       hi = rp[s + 1];
-      const int64_t i = qidx[s];
-      out = arp[i];
-      di = d[i];
+      out = arp[qidx[s]];
     }
     const unsigned trips = __reduce_max_sync(FULL, (unsigned)((hi - lo + G - 1) / G));
     for (unsigned t = 0; t < trips; ++t) {
@@ -1063,58 +973,76 @@ __global__ void k_extract_fill(int64_t n, const int64_t* __restrict__ rp, const 
       const unsigned mine = __ballot_sync(FULL, p) & gmask;
       if (p) {
         const int64_t pos = out + __popc(mine & lt);
-        const double a = general ? -v : v;   // general system: A = -(off-diagonal of M)
         acol[pos] = cq;
-        aval[pos] = a;
-        aj[pos] = di == 1.0 ? a : a / di;
-        sa = __dadd_ru(sa, fabs(a));
+        aval[pos] = general ? -v : v;   // general system: A = -(off-diagonal of M)
       }
       out += __popc(mine);
     }
-    sa = group_sum_ru<G>(sa);
-    if (act && rg.lane == 0) {
-      const double m = __dadd_rd(fabs(di), -sa);
-      lo_min = fmin(lo_min, m != m ? -inf : m);
-    }
   }
-  lo_min = -warp_max(-lo_min);
-  if ((threadIdx.x & 31) == 0) atomicMin(kmin, ordered_key(lo_min));
 }
 
-// Jacobi form: Aj_ij = A_ij / d_i, bj_i = b_i / d_i (IEEE division, once per system).
+// Jacobi form: Aj_ij = A_ij / d_i, bj_i = b_i / d_i (IEEE division, once per system).  With
+// kmin it also reduces Varah's row-dominance margin min_i (|d_i| - sum_j |A_ij|) into *kmin
+// as an ordered key, the sum rounded upward and the difference downward: a guaranteed lower
+// bound of the exact margin, from the same pass over A.
 template <int G>
 __global__ void k_jform(int64_t nq, const int64_t* __restrict__ rp, const double* __restrict__ av,
                         const double* __restrict__ b, const double* __restrict__ d, double* __restrict__ aj,
-                        double* __restrict__ bj) {
+                        double* __restrict__ bj, unsigned long long* kmin) {
   RowGroups rg = RowGroups::make<G>();
-  for (int64_t i = rg.first; i < nq; i += rg.stride) {
-    const double di = d[i];
-    // a row without a self-loop has d_i = 1 exactly and needs no division: on GB300 an FP64
-    // division is a long sequence on the narrow FP64 pipe (3.7x the sweep time on sparse rows)
-    if (di == 1.0) {
-      for (int64_t k = rp[i] + rg.lane; k < rp[i + 1]; k += G) aj[k] = av[k];
-      if (rg.lane == 0 && bj) bj[i] = b[i];
-    } else {
-      for (int64_t k = rp[i] + rg.lane; k < rp[i + 1]; k += G) aj[k] = av[k] / di;
-      if (rg.lane == 0 && bj) bj[i] = b[i] / di;
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  double lo_min = inf;
+  for (int64_t i = rg.first; warp_has_row<G>(i, nq); i += rg.stride) {
+    double sa = 0.0, di = 1.0;
+    if (i < nq) {
+      di = d[i];
+      // a row without a self-loop has d_i = 1 exactly and needs no division: on GB300 an FP64
+      // division is a long sequence on the narrow FP64 pipe (3.7x the sweep time on sparse rows)
+      if (di == 1.0) {
+        for (int64_t k = rp[i] + rg.lane; k < rp[i + 1]; k += G) {
+          const double a = av[k];
+          aj[k] = a;
+          sa = __dadd_ru(sa, fabs(a));
+        }
+        if (rg.lane == 0 && bj) bj[i] = b[i];
+      } else {
+        for (int64_t k = rp[i] + rg.lane; k < rp[i + 1]; k += G) {
+          const double a = av[k];
+          aj[k] = a / di;
+          sa = __dadd_ru(sa, fabs(a));
+        }
+        if (rg.lane == 0 && bj) bj[i] = b[i] / di;
+      }
     }
+    if (kmin) {
+      sa = group_sum_ru<G>(sa);
+      if (i < nq && rg.lane == 0) {
+        const double m = __dadd_rd(fabs(di), -sa);
+        lo_min = fmin(lo_min, m != m ? -inf : m);
+      }
+    }
+  }
+  if (kmin) {
+    lo_min = -warp_max(-lo_min);
+    if ((threadIdx.x & 31) == 0) atomicMin(kmin, ordered_key(lo_min));
   }
 }
 
 template <int G>
 static void jform_launch(reach_ctx* c, int64_t nq, const int64_t* rp, const double* av, const double* b,
-                         double* aj, double* bj) {
-  k_jform<G><<<grid_for(c, (const void*)k_jform<G>, 256, nq * G), 256, 0, c->stream>>>(nq, rp, av, b, c->d, aj, bj);
+                         double* aj, double* bj, unsigned long long* kmin) {
+  k_jform<G><<<grid_for(c, (const void*)k_jform<G>, 256, nq * G), 256, 0, c->stream>>>(nq, rp, av, b, c->d, aj,
+                                                                                      bj, kmin);
 }
 
 static void jform_dispatch(reach_ctx* c, int g, int64_t nq, const int64_t* rp, const double* av,
-                           const double* b, double* aj, double* bj) {
+                           const double* b, double* aj, double* bj, unsigned long long* kmin = nullptr) {
   switch (g) {
-    case 2: jform_launch<2>(c, nq, rp, av, b, aj, bj); break;
-    case 4: jform_launch<4>(c, nq, rp, av, b, aj, bj); break;
-    case 8: jform_launch<8>(c, nq, rp, av, b, aj, bj); break;
-    case 16: jform_launch<16>(c, nq, rp, av, b, aj, bj); break;
-    default: jform_launch<32>(c, nq, rp, av, b, aj, bj); break;
+    case 2: jform_launch<2>(c, nq, rp, av, b, aj, bj, kmin); break;
+    case 4: jform_launch<4>(c, nq, rp, av, b, aj, bj, kmin); break;
+    case 8: jform_launch<8>(c, nq, rp, av, b, aj, bj, kmin); break;
+    case 16: jform_launch<16>(c, nq, rp, av, b, aj, bj, kmin); break;
+    default: jform_launch<32>(c, nq, rp, av, b, aj, bj, kmin); break;
   }
 }
 
@@ -1125,11 +1053,10 @@ static void extract_launch(reach_ctx* c, int64_t* acnt, int pass) {
                             256, c->n * G);
   if (pass == 0)
     k_extract_count<G><<<grid, 256, 0, c->stream>>>(c->n, c->rowptr, c->col, c->val, c->cls, c->qidx,
-                                                    acnt, c->d, c->b, c->bj, c->qstate, c->general ? 1 : 0);
+                                                    acnt, c->d, c->b, c->qstate, c->general ? 1 : 0);
   else
     k_extract_fill<G><<<grid, 256, 0, c->stream>>>(c->n, c->rowptr, c->col, c->val, c->cls, c->qidx,
-                                                   c->a_rowptr, c->d, c->a_col, c->a_val, c->a_jv,
-                                                   c->keys + VARAH_KEY, c->general ? 1 : 0);
+                                                   c->a_rowptr, c->a_col, c->a_val, c->general ? 1 : 0);
 }
 
 static void extract_dispatch(reach_ctx* c, int g, int64_t* acnt, int pass) {
@@ -1194,9 +1121,6 @@ cudaError_t extract_rows(reach_ctx* c) {
   if ((e = dmalloc(&c->d, nq)) != cudaSuccess) return e;
   if ((e = dmalloc(&c->b, nq)) != cudaSuccess) return e;
   if ((e = dmalloc(&c->qstate, nq)) != cudaSuccess) return e;
-  // bj of a chain comes with b; a general system's b is given later (build_jacobi_form)
-  if (c->bj) { cudaFree(c->bj); c->bj = nullptr; }
-  if (!c->general && (e = dmalloc(&c->bj, nq)) != cudaSuccess) return e;
   int64_t* acnt = nullptr;
   if ((e = dmalloc(&acnt, nq)) != cudaSuccess) return e;
   const int g = graph_group(c, n, c->m);
@@ -1212,14 +1136,13 @@ cudaError_t extract_rows(reach_ctx* c) {
   // +8 entries of slack so vector loads of the last row stay inside the allocation
   if ((e = dmalloc(&c->a_col, mq + 8)) != cudaSuccess) return e;
   if ((e = dmalloc(&c->a_val, mq + 8)) != cudaSuccess) return e;
-  if ((e = dmalloc(&c->a_jv, mq + 8)) != cudaSuccess) return e;
   cudaMemsetAsync(c->a_col + mq, 0, 8 * sizeof(int32_t), s);
   cudaMemsetAsync(c->a_val + mq, 0, 8 * sizeof(double), s);
-  cudaMemsetAsync(c->a_jv + mq, 0, 8 * sizeof(double), s);
-  cudaMemsetAsync(c->keys + VARAH_KEY, 0xff, sizeof(unsigned long long), s);
   if (nq > 0) extract_dispatch(c, g, nullptr, 1);
-  c->varah_key = true;
-  // the hi/lo split and the transposed system are rebuilt on demand
+  // the Jacobi form, the hi/lo split and the transposed system are rebuilt on demand
+  if (c->a_jv) { cudaFree(c->a_jv); c->a_jv = nullptr; }
+  if (c->bj) { cudaFree(c->bj); c->bj = nullptr; }
+  c->varah_key = false;
   if (c->at_jv) { cudaFree(c->at_jv); c->at_jv = nullptr; }
   if (c->a_hi) { cudaFree(c->a_hi); c->a_hi = nullptr; }
   if (c->a_lo) { cudaFree(c->a_lo); c->a_lo = nullptr; }
@@ -1265,29 +1188,18 @@ cudaError_t split_hilo(reach_ctx* c) {
   return cudaGetLastError();
 }
 
-__global__ void k_bj(int64_t nq, const double* __restrict__ b, const double* __restrict__ d,
-                     double* __restrict__ bj) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
-    const double di = d[i];
-    bj[i] = di == 1.0 ? b[i] : b[i] / di;
-  }
-}
-
-// The Jacobi form (§3.1).  The extraction writes Aj (and a chain's bj) with A itself; a
-// general system's bj follows here, once its b is in place.
+// The Jacobi form of the system (§3.1), with Varah's margin of its rows from the same pass.
 cudaError_t build_jacobi_form(reach_ctx* c) {
   if (c->a_jv && c->bj) return cudaSuccess;
   const int64_t nq = c->n_q, mq = c->m_q;
   cudaError_t e;
-  if (!c->a_jv) {
-    if ((e = dmalloc(&c->a_jv, mq + 8)) != cudaSuccess) return e;
-    if ((e = dmalloc(&c->bj, nq)) != cudaSuccess) return e;
-    cudaMemsetAsync(c->a_jv + mq, 0, 8 * sizeof(double), c->stream);
-    if (nq > 0) jform_dispatch(c, graph_group(c, nq, mq), nq, c->a_rowptr, c->a_val, c->b, c->a_jv, c->bj);
-    return cudaGetLastError();
-  }
+  if ((e = dmalloc(&c->a_jv, mq + 8)) != cudaSuccess) return e;
   if ((e = dmalloc(&c->bj, nq)) != cudaSuccess) return e;
-  if (nq > 0) k_bj<<<grid_for(c, (const void*)k_bj, 256, nq), 256, 0, c->stream>>>(nq, c->b, c->d, c->bj);
+  cudaMemsetAsync(c->a_jv + mq, 0, 8 * sizeof(double), c->stream);
+  cudaMemsetAsync(c->keys + VARAH_KEY, 0xff, sizeof(unsigned long long), c->stream);
+  if (nq > 0)
+    jform_dispatch(c, graph_group(c, nq, mq), nq, c->a_rowptr, c->a_val, c->b, c->a_jv, c->bj, c->keys + VARAH_KEY);
+  c->varah_key = true;
   return cudaGetLastError();
 }
 
