@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(BFS_CL_NT, 1) k_bfs_cluster(const int64_t* __r
 }
 
 // Entries of a reversed row that one lane of k_bfs_cluster_lq handles at a time.
-constexpr int BFS_ILP = 4;
+constexpr int BFS_ILP = 8;
 
 // The same level loop with the frontier held in the CTAs' shared memory.  A state found by
 // CTA r goes into r's own queue (a shared-memory counter, no atomics in global memory) and
