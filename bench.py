@@ -536,7 +536,11 @@ def run_workload(args):
                 shapes.append(row)
         line.update({"shapes": shapes, "oracle_cores": 1})
     elif args.workload == "batched":
-        bt = synth.batched_chains(n_chains=args.chains, sink_frac=0.02)
+        if args.chain_states:   # every chain of this many states (the L2 study of the sweep)
+            bt = synth.batched_chains(n_chains=args.chains, n_min=args.chain_states,
+                                      n_max=args.chain_states + 1, sink_frac=0.02)
+        else:
+            bt = synth.batched_chains(n_chains=args.chains, sink_frac=0.02)
         n, rowptr, col, val, goals, offs = bt.concat()
         d_in = dev(rowptr, col, val, goals)
         # each chain stops on its own unless --global-stop (one rule over the whole union)
@@ -650,6 +654,8 @@ def main():
                                            "table1", "batched", "parametric"],
                     default="dense", help="dense = the benchmark; the others print their own line")
     ap.add_argument("--chains", type=int, default=64, help="--workload batched: number of chains")
+    ap.add_argument("--chain-states", type=int, default=0,
+                    help="--workload batched: every chain with this many states (default: sizes log-uniform in [1e3, 2e6])")
     ap.add_argument("--global-stop", action="store_true",
                     help="--workload batched: one stopping rule over the whole union instead of one per chain")
     ap.add_argument("--batch-autotune", type=int, default=1,
