@@ -296,23 +296,34 @@ __global__ void k_bfs_init(int64_t n, int kind, int avoid_goal, const uint8_t* _
                            const uint32_t* __restrict__ other, uint32_t* vis, int32_t* q0,
                            BfsState* st) {
   const int64_t words = (n + 31) >> 5;
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
-       w += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  // a warp takes 32 consecutive words and reserves its queue slots with one atomic
+  for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; w0 < words;
+       w0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = w0 + lane;
     uint32_t bits = 0, blocked = 0;
-    for (int j = 0; j < 32; ++j) {
-      int64_t s = w * 32 + j;
-      if (s >= n) break;
-      bool src = kind == 0 ? goal[s] != 0 : !bit_of(other, s);
-      if (src) bits |= 1u << j;
-      else if (avoid_goal && goal[s]) blocked |= 1u << j;
+    if (w < words) {
+      for (int j = 0; j < 32; ++j) {
+        int64_t s = w * 32 + j;
+        if (s >= n) break;
+        bool src = kind == 0 ? goal[s] != 0 : !bit_of(other, s);
+        if (src) bits |= 1u << j;
+        else if (avoid_goal && goal[s]) blocked |= 1u << j;
+      }
+      vis[w] = bits | blocked;
     }
-    vis[w] = bits | blocked;
-    int nb = __popc(bits);
-    if (nb) {
-      uint32_t base = atomicAdd(&st->count[0], (uint32_t)nb);
-      for (int j = 0; j < 32; ++j)
-        if (bits & (1u << j)) q0[base++] = (int32_t)(w * 32 + j);
+    const uint32_t nb = (uint32_t)__popc(bits);
+    uint32_t inc = nb;   // inclusive scan of the warp's source counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += y;
     }
+    uint32_t base = 0;
+    if (lane == 31 && inc) base = atomicAdd(&st->count[0], inc);
+    base = __shfl_sync(FULL, base, 31) + inc - nb;
+    for (int j = 0; j < 32; ++j)
+      if (bits & (1u << j)) q0[base++] = (int32_t)(w * 32 + j);
   }
 }
 
@@ -379,8 +390,11 @@ static void launch_level(reach_ctx* c, int grid, uint32_t* vis, double pull_edge
 // atomic per reversed edge of the frontier top-down; the reversed graph is not read.
 // Marks made during the pass may serve later states of the same pass: each is still a
 // path to the sources, so the search reaches the same set (§2.2), in fewer levels.
+constexpr int PULL_NT = 256;     // threads of a k_bfs_pull block
+constexpr int PULL_BUF = 2048;   // marked states a block collects before one queue reservation
+
 template <int G>
-__global__ void k_bfs_pull(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+__global__ void __launch_bounds__(PULL_NT) k_bfs_pull(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                            const double* __restrict__ val, const uint8_t* __restrict__ goal, int avoid_goal,
                            uint32_t* vis, int32_t* qa, int32_t* qb, BfsState* st, unsigned* ticket,
                            double mean_deg, double pull_edges, int32_t level_cap,
@@ -395,14 +409,31 @@ __global__ void k_bfs_pull(int64_t n, const int64_t* __restrict__ rp, const int3
   if (!((double)cnt * mean_deg > pull_edges)) return;   // k_bfs_level's
   if (blockIdx.x == 0 && threadIdx.x == 0) st->count[(L + 2) % 3] = 0u;
   int32_t* qn = (L & 1) ? qa : qb;
-  RowGroups rg = RowGroups::make<G>();
+  // marked states collect in shared memory and reach the queue a buffer at a time: one
+  // global atomic per flush instead of one per warp step (a same-address atomic per warp
+  // serialised in L2 and bounded the pass)
+  constexpr int ROWS = PULL_NT / G;
+  __shared__ int32_t sbuf[PULL_BUF];
+  __shared__ uint32_t scnt, sbase;
+  if (threadIdx.x == 0) scnt = 0u;
+  __syncthreads();
+  auto flush = [&]() {
+    if (threadIdx.x == 0) sbase = scnt ? atomicAdd(&st->count[nxt], scnt) : 0u;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < scnt; i += PULL_NT) qn[sbase + i] = sbuf[i];
+    __syncthreads();
+    if (threadIdx.x == 0) scnt = 0u;
+    __syncthreads();
+  };
+  const int lane = threadIdx.x & (G - 1);
   const int wl = threadIdx.x & 31;
   const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (wl & ~(G - 1)));
-  for (int64_t s = rg.first; warp_has_row<G>(s, n); s += rg.stride) {
+  for (int64_t s0 = (int64_t)blockIdx.x * ROWS; s0 < n; s0 += (int64_t)gridDim.x * ROWS) {
+    const int64_t s = s0 + threadIdx.x / G;
     bool done = true;
     int64_t k = 0, hi = 0;
     if (s < n && !((__ldcg(vis + (s >> 5)) >> (s & 31)) & 1u)) {
-      k = rp[s] + rg.lane;
+      k = rp[s] + lane;
       hi = rp[s + 1];
       done = false;
     }
@@ -422,11 +453,14 @@ __global__ void k_bfs_pull(int64_t n, const int64_t* __restrict__ rp, const int3
       }
       k += G;
     }
-    if (hit && rg.lane == 0) {
+    if (hit && lane == 0) {
       atomicOr(vis + (s >> 5), 1u << (s & 31));
-      qn[agg_inc(&st->count[nxt])] = (int32_t)s;
+      sbuf[atomicAdd(&scnt, 1u)] = (int32_t)s;
     }
+    __syncthreads();
+    if (scnt > PULL_BUF - ROWS) flush();   // room for one more step's marks
   }
+  flush();
   __shared__ bool last;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -447,8 +481,8 @@ template <int G>
 static void launch_pull(reach_ctx* c, int avoid_goal, uint32_t* vis, double pull_edges, int32_t level_cap,
                         cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
   const double mean_deg = c->n > 0 ? std::max(1.0, (double)c->m / (double)c->n) : 1.0;
-  const int grid = grid_for(c, (const void*)k_bfs_pull<G>, 256, c->n * G);
-  k_bfs_pull<G><<<grid, 256, 0, s>>>(c->n, c->rowptr, c->col, c->val, c->goal, avoid_goal, vis, c->queue,
+  const int grid = grid_for(c, (const void*)k_bfs_pull<G>, PULL_NT, c->n * G);
+  k_bfs_pull<G><<<grid, PULL_NT, 0, s>>>(c->n, c->rowptr, c->col, c->val, c->goal, avoid_goal, vis, c->queue,
                                      c->queue + c->n, c->bfs, c->ticket, mean_deg, pull_edges, level_cap,
                                      h, use_cond);
 }
