@@ -324,20 +324,33 @@ def run_ours(args):
     lanes = {}
     bound = {}
 
-    def step(inputs, outputs):
+    def step(inputs, outputs, parts=None):
+        """One step; `parts` (a dict) gets the wall time of each call, in ms."""
         infos = {}
+        t = [time.perf_counter()]
+
+        def mark(name):
+            if parts is not None:
+                t.append(time.perf_counter())
+                parts[name] = (t[-1] - t[-2]) * 1e3
+
         ctx = R.reach_create(n, *inputs, stream=stream.cuda_stream)
+        mark("create")
         try:
             R.reach_precompute(ctx, R.REACH_PROB0_ONLY)
+            mark("precompute")
             # certified ||(I - A)^-1|| from tau = (I - A)^-1 1, for every solve's error bound
             bound["kinv"], bound["info"] = R.reach_norm_bound(ctx, "bicgstab", eps=1e-8)
+            mark("norm_bound")
             for meth in ("jacobi", "mixed", "bicgstab"):
                 # row mapping from the autotuner (measured once per system shape, then cached)
                 lanes[meth] = R.reach_autotune(ctx, meth)["lanes"]
                 _, infos[meth] = R.reach_solve(ctx, n, meth, eps=EPS[meth], max_iter=200_000,
                                                refine_k=K_REFINE, out=outputs[meth])
+                mark(meth)
         finally:
             R.reach_destroy(ctx)
+            mark("destroy")
         return infos
 
     for _ in range(args.warmup):
@@ -346,13 +359,15 @@ def run_ours(args):
     # end to end through the public API: host (pinned) inputs copied in, x copied out.  Run
     # right after the warm-up, like the timed region below, so both see the same thermal and
     # power state (after seconds of FP64 load the Jacobi sweeps run a few % slower)
-    e_ms = []
+    e_ms, e_parts = [], []
     with Clocks(local) as e2e_clk:
         for _ in range(max(1, min(args.steps, 3))):
             torch.cuda.synchronize(dev)
+            parts = {}
             t0 = time.perf_counter()
-            step(h_in, h_outs)
+            step(h_in, h_outs, parts)
             e_ms.append((time.perf_counter() - t0) * 1e3)
+            e_parts.append(parts)
     e2e_clocks = e2e_clk.summary()
     h2d = sum(int(a.numel() * a.element_size()) for a in h_in)
     d2h = 3 * n * 8
@@ -427,7 +442,9 @@ def run_ours(args):
         "kernels": kernels,
         "e2e": {"value": statistics.median(e_ms), "unit": "ms", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": len(e_ms),
-                "when": "after the warm-up, before the timed region", "clocks": e2e_clocks},
+                "when": "after the warm-up, before the timed region", "clocks": e2e_clocks,
+                "samples_ms": [round(v, 2) for v in e_ms],
+                "parts_ms": {k: round(statistics.median(p[k] for p in e_parts), 2) for k in e_parts[0]}},
         "gpu_launches": launches_per_step(infos, K_REFINE, bound["info"]["iters"]) * args.steps,
         "clocks": clocks,
     }
