@@ -279,7 +279,7 @@ def kernel_times(R, n, d_in, stream, launches=20):
         R.reach_precompute(ctx, R.REACH_PROB0_ONLY)
         for meth in ("jacobi", "mixed", "bicgstab"):
             R.reach_autotune(ctx, meth)        # the mappings the timed solves used
-        for k in ("jacobi64", "sweep32", "resid_hilo", "bicgstab_spmv"):
+        for k in ("jacobi64", "sweep32", "resid_mixed", "bicgstab_spmv"):
             out[k] = R.reach_time_kernel(ctx, k, launches)
     finally:
         R.reach_destroy(ctx)
@@ -398,7 +398,7 @@ def run_ours(args):
     # per-kernel device times, measured live on the context stream with CUDA events
     kern = kernel_times(R, n, d_in, stream)
     kbytes = {"jacobi64": mq * 12 + nq * 32, "sweep32": mq * (6 if nq <= 65536 else 8) + nq * 16,
-              "resid_hilo": mq * (10 if nq <= 65536 else 12) + nq * 36, "bicgstab_spmv": mq * 12 + nq * 40}
+              "resid_mixed": mq * (10 if nq <= 65536 else 12) + nq * 32, "bicgstab_spmv": mq * 12 + nq * 40}
     kernels = {}
     for k, t in kern.items():
         gbs = kbytes[k] / (t * 1e-3) / 1e9

@@ -340,7 +340,7 @@ def reach_scc(ctx, labels=True, max_rounds=0, out_label=None, out_level=None):
     return out_label, out_level, info.as_dict()
 
 
-KERNELS = {"jacobi64": 0, "sweep32": 1, "resid_hilo": 2, "bicgstab_spmv": 3}
+KERNELS = {"jacobi64": 0, "sweep32": 1, "resid_mixed": 2, "bicgstab_spmv": 3}
 
 
 def reach_time_kernel(ctx, kernel, launches=20):

@@ -83,6 +83,48 @@ RDEV double dot64(int64_t lo, int64_t hi, int lane, const int32_t* __restrict__ 
   return s;
 }
 
+// The FP64 dot of dot64 over either index width (16-bit columns when every column fits).
+template <int G, bool V, typename IT>
+RDEV double dot_jv(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
+                   const double* __restrict__ av, const double* __restrict__ x, double init = 0.0) {
+  double s = init;
+  if constexpr (V) {
+    int64_t a = (lo + 3) & ~int64_t(3);
+    if (a > hi) a = hi;
+    const int64_t e = a + ((hi - a) & ~int64_t(3));
+    if (lo + lane < a) s = fma(__ldcs(av + lo + lane), __ldg(x + ld_idx(ci + lo + lane)), s);
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0;   // independent FP64 chains (see dot64)
+    for (int64_t k = a + 4 * lane; k < e; k += 4 * G) {
+      const int4 c4 = ld_idx4(ci + k);
+      const double2 v0 = __ldcs(reinterpret_cast<const double2*>(av + k));
+      const double2 v1 = __ldcs(reinterpret_cast<const double2*>(av + k + 2));
+      s = fma(v0.x, __ldg(x + c4.x), s);
+      s1 = fma(v0.y, __ldg(x + c4.y), s1);
+      s2 = fma(v1.x, __ldg(x + c4.z), s2);
+      s3 = fma(v1.y, __ldg(x + c4.w), s3);
+    }
+    s = (s + s1) + (s2 + s3);
+    if (e + lane < hi) s = fma(__ldcs(av + e + lane), __ldg(x + ld_idx(ci + e + lane)), s);
+  } else {
+    constexpr int B = G == 1 ? 4 : 2;   // loads of a trip first, one accumulator (see dot64)
+    for (int64_t k = lo + lane; k < hi; k += B * G) {
+      int c[B];
+      double v[B], xg[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        const bool ok = k + u * G < hi;
+        c[u] = ok ? ld_idx(ci + k + u * G) : 0;
+        v[u] = ok ? __ldcs(av + k + u * G) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < B; ++u) xg[u] = k + u * G < hi ? __ldg(x + c[u]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < B; ++u) s = fma(v[u], xg[u], s);
+    }
+  }
+  return s;
+}
+
 // FP32 values, FP32 accumulation (inner sweeps of the mixed method).  XS: x lives in
 // shared memory (plain loads) instead of global memory (read-only path).
 template <int G, bool V, typename IT = int32_t, int U = 2, bool XS = false>
@@ -157,76 +199,6 @@ RDEV float dot32(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
       s1 = fmaf(v[3], xg[3], s1);
     }
     s += s1;
-  }
-  return s;
-}
-
-// Residual step with values v = hi + lo (FP32 pair, v to about 2^-48 relative):
-// sum hi * x in FP64 (one FP64 FMA per entry) and sum lo * x in FP32 against an FP32
-// copy of x (lo is 2^-24 of hi, so FP32 keeps that term to about 2^-48 of the total).
-template <int G, bool V, typename IT = int32_t>
-RDEV double dot_hilo(int64_t lo, int64_t hi, int lane, const IT* __restrict__ ci,
-                     const float* __restrict__ ah, const float* __restrict__ al,
-                     const double* __restrict__ x, const float* __restrict__ xf, float& sl,
-                     double init = 0.0) {
-  double s = init;
-  if constexpr (V) {
-    int64_t a = (lo + 3) & ~int64_t(3);
-    if (a > hi) a = hi;
-    const int64_t e = a + ((hi - a) & ~int64_t(3));
-    if (lo + lane < a) {
-      const int64_t k = lo + lane;
-      const int c = ld_idx(ci + k);
-      s = fma(widen(__ldcs(ah + k)), __ldg(x + c), s);
-      sl = fmaf(__ldcs(al + k), __ldg(xf + c), sl);
-    }
-    double s1 = 0.0, s2 = 0.0, s3 = 0.0;   // independent FP64 chains (see dot64)
-    for (int64_t k = a + 4 * lane; k < e; k += 4 * G) {
-      const int4 c4 = ld_idx4(ci + k);
-      const float4 h = __ldcs(reinterpret_cast<const float4*>(ah + k));
-      const float4 l = __ldcs(reinterpret_cast<const float4*>(al + k));
-      s = fma(widen(h.x), __ldg(x + c4.x), s);
-      s1 = fma(widen(h.y), __ldg(x + c4.y), s1);
-      s2 = fma(widen(h.z), __ldg(x + c4.z), s2);
-      s3 = fma(widen(h.w), __ldg(x + c4.w), s3);
-      sl = fmaf(l.x, __ldg(xf + c4.x), sl);
-      sl = fmaf(l.y, __ldg(xf + c4.y), sl);
-      sl = fmaf(l.z, __ldg(xf + c4.z), sl);
-      sl = fmaf(l.w, __ldg(xf + c4.w), sl);
-    }
-    s = (s + s1) + (s2 + s3);
-    if (e + lane < hi) {
-      const int64_t k = e + lane;
-      const int c = ld_idx(ci + k);
-      s = fma(widen(__ldcs(ah + k)), __ldg(x + c), s);
-      sl = fmaf(__ldcs(al + k), __ldg(xf + c), sl);
-    }
-  } else {
-    // B entries per lane per trip, loads first, one FP64 accumulator (see dot64)
-    constexpr int B = G == 1 ? 4 : 2;
-    for (int64_t k = lo + lane; k < hi; k += B * G) {
-      int c[B];
-      float h[B], l[B], xl[B];
-      double xg[B];
-#pragma unroll
-      for (int u = 0; u < B; ++u) {
-        const bool ok = k + u * G < hi;
-        c[u] = ok ? ld_idx(ci + k + u * G) : 0;
-        h[u] = ok ? __ldcs(ah + k + u * G) : 0.0f;
-        l[u] = ok ? __ldcs(al + k + u * G) : 0.0f;
-      }
-#pragma unroll
-      for (int u = 0; u < B; ++u) {
-        const bool ok = k + u * G < hi;
-        xg[u] = ok ? __ldg(x + c[u]) : 0.0;
-        xl[u] = ok ? __ldg(xf + c[u]) : 0.0f;
-      }
-#pragma unroll
-      for (int u = 0; u < B; ++u) {
-        s = fma(widen(h[u]), xg[u], s);
-        sl = fmaf(l[u], xl[u], sl);
-      }
-    }
   }
   return s;
 }
@@ -501,37 +473,33 @@ __global__ void k_finalize_resid(SolveState* st) {
 // then x += d in FP64.  max|r_i| is exactly the max|x' - x| of an FP64 Jacobi sweep
 // from x, so the stopping rule matches.
 
+// The FP64 residual step reads the FP64 Jacobi-form values: one FP64 FMA and one gather of x
+// per entry, 10 (16-bit columns) or 12 bytes per entry.  Reading the FP32 pair hi + lo
+// instead moves the same bytes but adds an FP32 product against an FP32 copy of x and the
+// widening of hi, and was 1.31x slower on the dense benchmark system.
 template <int G, bool V, typename IT>
-__global__ void __launch_bounds__(NT) k_resid_hilo(int64_t nq, const int64_t* __restrict__ rp,
-                                                   const IT* __restrict__ ci,
-                                                   const float* __restrict__ ah,
-                                                   const float* __restrict__ al,
-                                                   const double* __restrict__ bj,
-                                                   const double* __restrict__ x,
-                                                   const float* __restrict__ xf,
-                                                   float* __restrict__ r32, float* __restrict__ dl0,
-                                                   SolveState* st, int slot_idx, unsigned* ctr) {
+__global__ void __launch_bounds__(NT) k_resid_jv(int64_t nq, const int64_t* __restrict__ rp,
+                                                 const IT* __restrict__ ci, const double* __restrict__ av,
+                                                 const double* __restrict__ bj, const double* __restrict__ x,
+                                                 float* __restrict__ r32, float* __restrict__ dl0,
+                                                 SolveState* st, int slot_idx, unsigned* ctr) {
   if (st->done) return;
   RowGroups rg = RowGroups::make<G>();
   unsigned long long mx = 0ull;
   for (int64_t i = row_begin<G>(rg, ctr); warp_has_row<G>(i, nq); i = row_next<G>(rg, ctr, i)) {
     double s = 0.0, bv = 0.0, xo = 0.0;
-    float sl = 0.0f;
     if (!V && i < nq && rg.lane == 0) {  // short rows: row-side loads issued early
       bv = bj[i];
       xo = x[i];
     }
-    if (i < nq) s = dot_hilo<G, V, IT>(rp[i], rp[i + 1], rg.lane, ci, ah, al, x, xf, sl, V ? 0.0 : bv);
+    if (i < nq) s = dot_jv<G, V, IT>(rp[i], rp[i + 1], rg.lane, ci, av, x, V ? 0.0 : bv);
     s = group_sum<G>(s);
-    sl = group_sum<G>(sl);
     if (i < nq && rg.lane == 0) {
       if (V) {
         bv = bj[i];
         xo = x[i];
       }
-      // residual of the Jacobi form: r_i / d_i = bj_i + (Aj x)_i - x_i (short rows: bj_i is
-      // already in s)
-      const double r = ((V ? bv + s : s) + (double)sl) - xo;
+      const double r = (V ? bv + s : s) - xo;   // bj_i + (Aj x)_i - x_i
       const float rf = __double2float_rn(r);
       r32[i] = rf;
       dl0[i] = rf;
@@ -1027,17 +995,19 @@ static void l_resid(reach_ctx* c, const Sys& y, const double* x, cudaStream_t s)
   k_resid_cert<G><<<grid, NT, 0, s>>>(y.nq, y.rp, y.ci, y.av, y.b, c->d, x, &c->st->slot[63], &c->st->slot[61]);
 }
 
+// The mixed method's FP64 residual on the Jacobi form (16-bit column indices whenever every
+// column fits).
 template <int G, bool V>
-static void l_resid_hilo(reach_ctx* c, int slot, cudaStream_t s, unsigned* ctr = nullptr) {
+static void l_resid_mixed(reach_ctx* c, int slot, cudaStream_t s, unsigned* ctr = nullptr) {
   unsigned* cr = G == 32 ? ctr : nullptr;
-  if (c->a_col16) {   // 16-bit column indices whenever every column fits
-    const int grid = grid_rows(c, (const void*)k_resid_hilo<G, V, uint16_t>, NT, G, c->n_q, cr != nullptr);
-    k_resid_hilo<G, V, uint16_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col16, c->a_hi, c->a_lo, c->bj,
-                                                     c->x, c->xf, c->r32, c->dl[1], c->st, slot, cr);
+  if (c->a_col16) {
+    const int grid = grid_rows(c, (const void*)k_resid_jv<G, V, uint16_t>, NT, G, c->n_q, cr != nullptr);
+    k_resid_jv<G, V, uint16_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col16, c->a_jv, c->bj, c->x,
+                                                   c->r32, c->dl[1], c->st, slot, cr);
   } else {
-    const int grid = grid_rows(c, (const void*)k_resid_hilo<G, V, int32_t>, NT, G, c->n_q, cr != nullptr);
-    k_resid_hilo<G, V, int32_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_hi, c->a_lo, c->bj,
-                                                    c->x, c->xf, c->r32, c->dl[1], c->st, slot, cr);
+    const int grid = grid_rows(c, (const void*)k_resid_jv<G, V, int32_t>, NT, G, c->n_q, cr != nullptr);
+    k_resid_jv<G, V, int32_t><<<grid, NT, 0, s>>>(c->n_q, c->a_rowptr, c->a_col, c->a_jv, c->bj, c->x,
+                                                  c->r32, c->dl[1], c->st, slot, cr);
   }
 }
 
@@ -1225,7 +1195,7 @@ cudaError_t solve_mixed(reach_ctx* c, const double* x0q) {
   const int k = c->tune.k;
   e = run_loop(c, c->g_exec[1], c->g_key[1], shape_key(c, L, k), [&](cudaStream_t cs, cudaGraphConditionalHandle, int) {
     if (L.seg) seg_resid_hilo(c, &c->st->slot[0], cs);
-    else LAY_DISPATCH(L, l_resid_hilo, c, 0, cs, &c->st->rowctr[0]);
+    else LAY_DISPATCH(L, l_resid_mixed, c, 0, cs, &c->st->rowctr[0]);
     k_check_mixed<<<1, 1, 0, cs>>>(c->st, 0, k);
     // k - 1 FP32 sweeps: dl[1] -> dl[0] -> dl[1] ... ; k even, so the last lands in dl[0]
     for (int j = 1; j < k; ++j) {
@@ -1574,7 +1544,7 @@ cudaError_t autotune(reach_ctx* c, int method, int* chosen, float* best_ms) {
         if (part == 1 && L.seg) {
           seg_resid_hilo(c, &c->st->slot[62], s);
         } else if (part == 1) {
-          LAY_DISPATCH(L, l_resid_hilo, c, 62, s, ctr);
+          LAY_DISPATCH(L, l_resid_mixed, c, 62, s, ctr);
         } else if (L.tma) {
           e = sweep32_tma(c, c->dl[0], c->dl[1], s, ctr);
           if (e != cudaSuccess) return e;
@@ -1677,7 +1647,7 @@ cudaError_t time_kernel(reach_ctx* c, int kernel, int launches, float* avg_ms) {
     }
     else if (kernel == 0) LAY_DISPATCH(L, l_jacobi, c, y, c->x, c->x2, &c->st->slot[0], s, ctr);
     else if (kernel == 1) LAY_DISPATCH(L, l_sweep32, c, c->dl[0], c->dl[1], s, ctr);
-    else if (kernel == 2) LAY_DISPATCH(L, l_resid_hilo, c, 0, s, ctr);
+    else if (kernel == 2) LAY_DISPATCH(L, l_resid_mixed, c, 0, s, ctr);
     else LAY_DISPATCH(L, l_bi_v, c, ya, s);
   };
   one(0);  // warm-up

@@ -194,7 +194,7 @@ def test_autotune_then_solve(c1, method, tol):
         assert t["lanes"] in (1, 2, 4, 8, 16, 32, 48, 64, 66, 128) and t["sweep_ms"] > 0
         x, info = s.solve(method, eps=_eps(method))
         assert np.max(np.abs(x - x_o)) <= tol
-        for k in ("jacobi64", "sweep32", "resid_hilo", "bicgstab_spmv"):
+        for k in ("jacobi64", "sweep32", "resid_mixed", "bicgstab_spmv"):
             assert R.reach_time_kernel(s.ctx, k, 3) > 0.0
 
 
