@@ -147,9 +147,13 @@ reach_status reach_system_create(reach_ctx** out, int64_t n, int64_t m, const in
                                  const int32_t* col, const double* val, const double* b,
                                  int32_t flags, void* stream);
 
-/* Partition S into S=0 / S=1 / S? by backward breadth-first search over the
- * reversed underlying digraph (§2.2), then build A (off-diagonal, CSR over S? in
- * ascending state order), d = 1 - diag(A) and b (§2.3).  mode: reach_precomp_mode. */
+/* Partition S into S=0 / S=1 / S? by backward search over the underlying digraph
+ * (§2.2), then build A (off-diagonal, CSR over S? in ascending state order),
+ * d = 1 - diag(A) and b (§2.3).  mode: reach_precomp_mode.  Narrow search levels run on
+ * one thread-block cluster, medium ones top-down over the reversed digraph (built on the
+ * first such level), wide ones bottom-up over P itself; the resulting classes are the
+ * same.  REACH_BFS_CLUSTER=0, REACH_BFS_LQ=0 and REACH_BFS_PULL=0 in the environment
+ * switch off the cluster, its shared-memory queues and the bottom-up levels. */
 reach_status reach_precompute(reach_ctx* ctx, int32_t mode);
 
 /* Class of every state after reach_precompute: 0 = S=0, 1 = S=1, 2 = S?.
