@@ -11,3 +11,17 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: full-size workloads (minutes)")
+
+
+# A GPU test that does not finish in this many seconds fails and ends the process, where
+# the timeout plugin is installed.  Its thread method also ends a process blocked inside a
+# CUDA call: a device loop that never ends fails its test instead of stalling the suite.
+GPU_TEST_TIMEOUT_S = 1200
+
+
+def pytest_collection_modifyitems(config, items):
+    if not config.pluginmanager.hasplugin("timeout"):
+        return
+    for item in items:
+        if item.get_closest_marker("gpu") and not item.get_closest_marker("timeout"):
+            item.add_marker(pytest.mark.timeout(GPU_TEST_TIMEOUT_S, method="thread"))
